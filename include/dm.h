@@ -1,0 +1,204 @@
+/*
+ * dm.h - C ABI of the GB300 (sm_103a) Delta-Motif embedding-enumeration library.
+ *
+ * Problem (Sec. 3.1 of "Delta-Motif: Parallel Subgraph Isomorphism via Tabular Operations
+ * for Scalable Layout Selection", arXiv 2508.21287): given an undirected, simple, connected
+ * data graph G_d and pattern graph G_p, enumerate every injective map f : V_p -> V_d such
+ * that each pattern edge {u, v} maps onto a data edge {f(u), f(v)}. The library follows the
+ * method's reading of that statement (Alg. 1 with the overlap filter of Sec. 3.2): edges
+ * must be preserved, non-edges need not be (monomorphisms). Induced matching is future work.
+ *
+ * Method (Sec. 3.2-3.3, Alg. 1, Alg. 2): the pattern is decomposed into motif slices (paths,
+ * cycles, stars, ...); the embeddings Res(M) of each motif in G_d are tables of vertex-id
+ * tuples, built once per data graph; the result is assembled by joining the tables on the
+ * pattern vertices that slices share and filtering rows whose mapped vertices repeat.
+ * All of it runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions for every call:
+ *   - Return value: DM_OK (0) or a negative DM_E_* code; dm_strerror() names it. On error
+ *     no output argument is written unless stated.
+ *   - Vertex ids are int32, 0-based. CSR: row_ptr has n+1 entries, row_ptr[0] = 0,
+ *     col_idx[row_ptr[u] .. row_ptr[u+1]) lists the neighbours of u, sorted ascending,
+ *     no duplicates; every edge appears in both directions. Self-loops are dropped on load
+ *     (Res(M2) excludes them, Sec. 3.3).
+ *   - Input arrays are host memory owned by the caller; the library copies what it keeps.
+ *   - Calls on one dm_ctx must not run concurrently from several host threads.
+ *   - All device work of a context runs on its stream (dm_set_stream), in order.
+ */
+#ifndef DM_H
+#define DM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes ---- */
+#define DM_OK 0
+#define DM_E_INVAL (-1)        /* bad argument or malformed CSR (asymmetric, unsorted, duplicate, out of range) */
+#define DM_E_DISCONNECTED (-2) /* pattern or data graph not connected (Sec. 3.1 assumes connected graphs) */
+#define DM_E_NOMEM (-3)        /* device or host allocation failed, or the memory budget is too small */
+#define DM_E_CAPACITY (-4)     /* projected work or rows exceed the plan's cap (dm_plan_opts.max_rows) */
+#define DM_E_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define DM_E_CUDA (-6)         /* a CUDA runtime call failed */
+#define DM_E_CANCELLED (-7)    /* the chunk callback returned non-zero */
+#define DM_E_NOTFOUND (-8)     /* unknown graph handle or motif id */
+
+/* ------------------------------------------------------------------ handles --------- */
+typedef struct dm_ctx dm_ctx;
+typedef struct dm_plan_s dm_plan_t; /* plan handle (the call that makes one is dm_plan) */
+typedef int32_t dm_graph;
+
+/* ------------------------------------------------------------------ motifs ---------- */
+/* Motif ids (naming of Sec. 3.1: M_k is a path on k vertices, "-O" a cycle, "-1" one
+ * branch). Vertex order of each motif is fixed: paths 0-1-...-(k-1); cycles 0-1-...-(k-1)-0;
+ * M4-1 has centre 0 and leaves 1, 2, 3; M6-2O is the 2 x 3 grid 0-1-2 / 3-4-5 with rungs
+ * 0-3, 1-4, 2-5; M18-O-6 is the 12-cycle 0..11 plus pendant vertex 12 + i/2 on each even
+ * cycle vertex i. */
+#define DM_MOTIF_PATH(k) (k)           /* k = 2..16: M_k, M2 is a single edge */
+#define DM_MOTIF_CYCLE(k) (100 + (k))  /* k = 3..16: M_{k-O} */
+#define DM_MOTIF_M4_1 201              /* claw K_{1,3} */
+#define DM_MOTIF_M6_2O 202             /* two 4-cycles sharing an edge (2 x 3 grid) */
+#define DM_MOTIF_M18_O_6 203           /* 12-cycle with a pendant on every other vertex */
+
+/* ------------------------------------------------------------------ plan options ---- */
+#define DM_ORDER_PAPER 0      /* Sec. 3.2: largest motif first, first match found */
+#define DM_ORDER_HEURISTIC 1  /* greedy: smallest estimated intermediate table next */
+#define DM_ORDER_LEARNED 2    /* greedy on the trained cardinality model (falls back to heuristic if none) */
+
+#define DM_JOIN_AUTO 0
+#define DM_JOIN_HASH 1        /* probe a per-key index of the motif table (direct or hashed packed key) */
+#define DM_JOIN_SORTMERGE 2   /* sort the intermediate table by key, then merge with the sorted motif table */
+
+typedef struct dm_plan_opts {
+    const int32_t *motifs; /* motif ids to decompose with (M2 is always added); NULL = preset by data-graph degree */
+    int32_t n_motifs;
+    int32_t order;          /* DM_ORDER_* */
+    int32_t join_algo;      /* DM_JOIN_* */
+    int32_t induced;        /* must be 0 (reserved) */
+    int64_t chunk_rows;     /* 0 = from the memory budget; else the row cap of one intermediate chunk */
+    int64_t max_rows;       /* 0 = unlimited; else DM_E_CAPACITY once a step's candidate rows exceed it */
+} dm_plan_opts;
+
+/* ------------------------------------------------------------------ context --------- */
+
+/* Create a context on CUDA device `device`. mem_budget_bytes bounds the device memory the
+ * intermediate tables of one dm_match may hold (0 = half of the free memory at creation);
+ * larger results are streamed in chunks (depth-first over the join steps). */
+int dm_create(dm_ctx **out, int device, uint64_t mem_budget_bytes);
+
+/* Release every graph, motif table and buffer of the context. */
+int dm_destroy(dm_ctx *ctx);
+
+/* Run subsequent device work on `stream` (a cudaStream_t; NULL = the context's own stream). */
+int dm_set_stream(dm_ctx *ctx, void *stream);
+
+/* Change the memory budget of later calls (bytes; 0 = half of the free memory now). */
+int dm_set_budget(dm_ctx *ctx, uint64_t mem_budget_bytes);
+
+/* ------------------------------------------------------------------ data graph ------ */
+
+/* Load a data graph (Sec. 3.1). edge_err (nullable) is aligned with col_idx: the error of
+ * the directed slot, equal on both directions of an edge. qubit_err (nullable) has n
+ * entries. The graph, its adjacency bitmap and its Res(M2) table (Sec. 3.3) stay resident
+ * on the device until dm_destroy. Errors: DM_E_INVAL for malformed CSR,
+ * DM_E_DISCONNECTED if G_d is not connected. */
+int dm_load_data_graph(dm_ctx *ctx, int32_t n_vertices, const int32_t *row_ptr,
+                       const int32_t *col_idx, const float *edge_err, const float *qubit_err,
+                       dm_graph *out);
+
+/* Res(M) of one motif on a loaded graph (Alg. 2 builds it by the same join-and-filter
+ * loop). Writes min(cap, count) rows of k = motif size ints (row-major, host memory, in
+ * canonical ascending order) to out_rows (nullable) and the count and k to out_n / out_k. */
+int dm_motif_table(dm_ctx *ctx, dm_graph g, int32_t motif_id, int32_t *out_rows, int64_t cap,
+                   int64_t *out_n, int32_t *out_k);
+
+/* ------------------------------------------------------------------ plans ----------- */
+
+/* Decompose a pattern into motif slices (Sec. 3.2) against a loaded data graph and fix the
+ * join order. opts may be NULL. Errors: DM_E_INVAL (malformed CSR, n_p outside 1..64),
+ * DM_E_DISCONNECTED (pattern not connected). The plan owns copies of the pattern. */
+int dm_plan(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
+            const int32_t *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out);
+
+void dm_plan_free(dm_plan_t *plan);
+
+/* Flat description of a plan, for inspection and tests. Writes up to buf_len int32 words:
+ *   [n_steps, then per step: motif_id, k, slice[0..k-1] (pattern vertex of each motif
+ *    position), n_keys, n_backedges, backedge pairs (2 words each, pattern vertex ids)]
+ * and returns the number of words needed (or a negative error). */
+int32_t dm_plan_describe(const dm_plan_t *plan, int32_t *buf, int32_t buf_len);
+
+/* Host-only decomposition (Sec. 3.2) of a pattern with a motif set, without a data graph
+ * or a GPU: same output format as dm_plan_describe. order DM_ORDER_PAPER is the paper's
+ * rule; the estimate-driven orders see unit table sizes here. Returns the words needed, or
+ * DM_E_INVAL / DM_E_DISCONNECTED / DM_E_NOTFOUND (unknown motif id). */
+int32_t dm_decompose(int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
+                     const int32_t *motifs, int32_t n_motifs, int32_t order, int32_t *buf,
+                     int32_t buf_len);
+
+/* ------------------------------------------------------------------ matching -------- */
+#define DM_ALL 0            /* materialise every embedding */
+#define DM_COUNT 1          /* count + checksum only */
+#define DM_DEVICE_ROWS 0x10 /* flag: the callback gets device pointers instead of host copies */
+
+/* Chunk callback of DM_ALL. rows: nrows x n_cols int32, row-major, row r = (f(0), ...,
+ * f(n_p - 1)) indexed by pattern vertex; scores: nrows FP32 layout scores, or NULL when the
+ * graph has no error weights. Buffers belong to the library and are valid only during the
+ * call. Returning non-zero stops the match with DM_E_CANCELLED. */
+typedef int (*dm_chunk_cb)(void *user, const int32_t *rows, const float *scores, int64_t nrows,
+                           int32_t n_cols);
+
+/* Enumerate Emb(G_p, G_d) with the plan (Alg. 1).
+ *   DM_ALL: rows are delivered through cb in ascending canonical (lexicographic) order when
+ *     the whole result fits the memory budget; otherwise each delivered chunk is sorted and
+ *     chunks follow the depth-first order of the streamed join.
+ *   DM_COUNT: nothing is delivered; cb may be NULL.
+ * out_count / out_checksum (nullable) receive |Emb| and the checksum: the sum mod 2^64 over
+ * rows of H(row), H = fold of the SplitMix64 finaliser over (n_p, f(0), ..., f(n_p - 1)).
+ * Scores (when the graph has error weights) are the sum of edge errors over pattern edges
+ * plus vertex errors, FP32 (Sec. 5.4, log-domain form of the fidelity product). */
+int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void *user,
+             uint64_t *out_count, uint64_t *out_checksum);
+
+/* Count + checksum for n_plans plans on the same data graph in one persistent launch
+ * (captured in a CUDA graph). out_counts / out_checksums have n_plans entries. Results are
+ * identical to dm_match(DM_COUNT) on each plan alone. */
+int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, int mode,
+                   uint64_t *out_counts, uint64_t *out_checksums);
+
+/* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,
+ * row) key, in that order. out_rows: k x n_p int32 host buffer; out_scores: k floats
+ * (nullable); out_n receives the number written. Needs edge weights (DM_E_INVAL if none). */
+int dm_score_topk(dm_ctx *ctx, const dm_plan_t *plan, int32_t k, int32_t *out_rows,
+                  float *out_scores, int32_t *out_n);
+
+/* ------------------------------------------------------------------ statistics ------ */
+#define DM_MAX_STEPS 128
+typedef struct dm_stats {
+    int32_t n_steps;                  /* join steps of the last dm_match / dm_score_topk */
+    int64_t rows[DM_MAX_STEPS];       /* rows of the intermediate table after each step */
+    int64_t candidates[DM_MAX_STEPS]; /* joined rows before filtering, per step */
+    int64_t chunks;                   /* join launches (> n_steps when streaming) */
+    int64_t max_rows;                 /* largest intermediate table held at once */
+    double join_ms;                   /* device time of the join kernels (CUDA events) */
+    int64_t join_launches;
+    double join_bytes;                /* algorithmic bytes of the join launches */
+    double total_ms;                  /* host wall time of the call */
+} dm_stats;
+
+/* Statistics of the last dm_match / dm_score_topk on this context. Device timings are
+ * collected only after dm_enable_timing(ctx, 1). */
+int dm_get_stats(dm_ctx *ctx, dm_stats *out);
+int dm_enable_timing(dm_ctx *ctx, int on);
+
+const char *dm_strerror(int code);
+
+/* Text of the last CUDA failure seen by the context (empty if none); owned by the context. */
+const char *dm_last_error(dm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DM_H */

@@ -1,0 +1,345 @@
+"""Thin Python binding of include/dm.h (ctypes). Argument marshalling only: every step of the
+enumeration runs in libdmotif.so's CUDA kernels. Functions keep the C names; failures raise
+DMError with the library's status code.
+
+The library must have been built (``python -m paper_2508_21287_gb300.build`` or
+``__graft_entry__.build()``); importing this module without it raises immediately. There is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdmotif.so")
+
+DM_OK = 0
+DM_E_INVAL, DM_E_DISCONNECTED, DM_E_NOMEM, DM_E_CAPACITY = -1, -2, -3, -4
+DM_E_TIMEOUT, DM_E_CUDA, DM_E_CANCELLED, DM_E_NOTFOUND = -5, -6, -7, -8
+DM_ALL, DM_COUNT, DM_DEVICE_ROWS = 0, 1, 0x10
+DM_ORDER_PAPER, DM_ORDER_HEURISTIC, DM_ORDER_LEARNED = 0, 1, 2
+DM_JOIN_AUTO, DM_JOIN_HASH, DM_JOIN_SORTMERGE = 0, 1, 2
+DM_MAX_STEPS = 128
+
+
+def DM_MOTIF_PATH(k: int) -> int:
+    return k
+
+
+def DM_MOTIF_CYCLE(k: int) -> int:
+    return 100 + k
+
+
+DM_MOTIF_M4_1, DM_MOTIF_M6_2O, DM_MOTIF_M18_O_6 = 201, 202, 203
+
+
+class DMError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {dm_strerror(code)} ({code})" + (f" [{detail}]" if detail else ""))
+
+
+class dm_plan_opts(ctypes.Structure):
+    _fields_ = [("motifs", ctypes.POINTER(ctypes.c_int32)), ("n_motifs", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("join_algo", ctypes.c_int32), ("induced", ctypes.c_int32),
+                ("chunk_rows", ctypes.c_int64), ("max_rows", ctypes.c_int64)]
+
+
+class dm_stats(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int32), ("rows", ctypes.c_int64 * DM_MAX_STEPS),
+                ("candidates", ctypes.c_int64 * DM_MAX_STEPS), ("chunks", ctypes.c_int64),
+                ("max_rows", ctypes.c_int64), ("join_ms", ctypes.c_double),
+                ("join_launches", ctypes.c_int64), ("join_bytes", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+DM_CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int32)
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(the library has no CPU fallback)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp, _i32, _i64, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_fp = ctypes.POINTER(ctypes.c_float)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+_SIGS = {
+    "dm_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _u64]),
+    "dm_destroy": (ctypes.c_int, [_vp]),
+    "dm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "dm_set_budget": (ctypes.c_int, [_vp, _u64]),
+    "dm_load_data_graph": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32p]),
+    "dm_motif_table": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i64, ctypes.POINTER(_i64), _i32p]),
+    "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
+    "dm_plan_free": (None, [_vp]),
+    "dm_plan_describe": (_i32, [_vp, _i32p, _i32]),
+    "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
+    "dm_match_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _u64p, _u64p]),
+    "dm_score_topk": (ctypes.c_int, [_vp, _vp, _i32, _i32p, _fp, _i32p]),
+    "dm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dm_stats)]),
+    "dm_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "dm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "dm_last_error": (ctypes.c_char_p, [_vp]),
+    "dm_decompose": (_i32, [_i32, _i32p, _i32p, _i32p, _i32, _i32, _i32p, _i32]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def dm_strerror(code: int) -> str:
+    return _lib.dm_strerror(int(code)).decode()
+
+
+def dm_last_error(ctx) -> str:
+    return _lib.dm_last_error(ctx).decode()
+
+
+def _check(rc: int, what: str, ctx=None):
+    if rc != DM_OK:
+        raise DMError(rc, what, dm_last_error(ctx) if ctx else "")
+
+
+def _arr_i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(_i32p)
+
+
+def dm_create(device: int = 0, mem_budget_bytes: int = 0):
+    h = _vp()
+    _check(_lib.dm_create(ctypes.byref(h), int(device), int(mem_budget_bytes)), "dm_create")
+    return h
+
+
+def dm_destroy(ctx) -> None:
+    _check(_lib.dm_destroy(ctx), "dm_destroy")
+
+
+def dm_set_stream(ctx, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None for the context's own."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(_lib.dm_set_stream(ctx, _vp(raw) if raw else None), "dm_set_stream", ctx)
+
+
+def dm_set_budget(ctx, mem_budget_bytes: int) -> None:
+    _check(_lib.dm_set_budget(ctx, int(mem_budget_bytes)), "dm_set_budget", ctx)
+
+
+def dm_load_data_graph(ctx, n_vertices: int, row_ptr, col_idx, edge_err=None, qubit_err=None) -> int:
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    ee = None if edge_err is None else np.ascontiguousarray(edge_err, dtype=np.float32)
+    qe = None if qubit_err is None else np.ascontiguousarray(qubit_err, dtype=np.float32)
+    out = _i32()
+    rc = _lib.dm_load_data_graph(ctx, int(n_vertices), _p32(rp), _p32(ci),
+                                 None if ee is None else ee.ctypes.data_as(_fp),
+                                 None if qe is None else qe.ctypes.data_as(_fp), ctypes.byref(out))
+    _check(rc, "dm_load_data_graph", ctx)
+    return out.value
+
+
+def dm_motif_table(ctx, graph: int, motif_id: int) -> np.ndarray:
+    n, k = _i64(), _i32()
+    _check(_lib.dm_motif_table(ctx, int(graph), int(motif_id), None, 0, ctypes.byref(n), ctypes.byref(k)),
+           "dm_motif_table", ctx)
+    rows = np.empty((n.value, k.value), dtype=np.int32)
+    if n.value:
+        _check(_lib.dm_motif_table(ctx, int(graph), int(motif_id), _p32(rows), n.value, ctypes.byref(n),
+                                   ctypes.byref(k)), "dm_motif_table", ctx)
+    return rows
+
+
+def dm_plan(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, order: int = DM_ORDER_PAPER,
+            join_algo: int = DM_JOIN_AUTO, chunk_rows: int = 0, max_rows: int = 0):
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    opts = dm_plan_opts()
+    keep = None
+    if motifs:
+        keep = _arr_i32(list(motifs))
+        opts.motifs = _p32(keep)
+        opts.n_motifs = len(keep)
+    opts.order, opts.join_algo = int(order), int(join_algo)
+    opts.chunk_rows, opts.max_rows = int(chunk_rows), int(max_rows)
+    h = _vp()
+    _check(_lib.dm_plan(ctx, int(graph), int(n_p), _p32(rp), _p32(ci), ctypes.byref(opts), ctypes.byref(h)),
+           "dm_plan", ctx)
+    return h
+
+
+def dm_plan_free(plan) -> None:
+    _lib.dm_plan_free(plan)
+
+
+def _parse_description(words: list[int]) -> list[dict]:
+    steps, i = [], 1
+    for _ in range(words[0]):
+        motif, k = words[i], words[i + 1]
+        sl = words[i + 2:i + 2 + k]
+        i += 2 + k
+        n_keys, n_be = words[i], words[i + 1]
+        i += 2
+        be = [(words[i + 2 * j], words[i + 2 * j + 1]) for j in range(n_be)]
+        i += 2 * n_be
+        steps.append({"motif": motif, "slice": sl, "n_keys": n_keys, "backedges": be})
+    return steps
+
+
+def dm_plan_describe(plan) -> list[dict]:
+    n = _lib.dm_plan_describe(plan, None, 0)
+    if n < 0:
+        raise DMError(n, "dm_plan_describe")
+    buf = np.zeros(n, dtype=np.int32)
+    _lib.dm_plan_describe(plan, _p32(buf), n)
+    return _parse_description(buf.tolist())
+
+
+def dm_decompose(n_p: int, row_ptr, col_idx, motifs, order: int = DM_ORDER_PAPER) -> list[dict]:
+    """Host-only decomposition (no data graph): the plan's slice list, as dm_plan_describe."""
+    rp, ci, ms = _arr_i32(row_ptr), _arr_i32(col_idx), _arr_i32(list(motifs))
+    n = _lib.dm_decompose(int(n_p), _p32(rp), _p32(ci), _p32(ms), len(ms), int(order), None, 0)
+    if n < 0:
+        raise DMError(n, "dm_decompose")
+    buf = np.zeros(n, dtype=np.int32)
+    _lib.dm_decompose(int(n_p), _p32(rp), _p32(ci), _p32(ms), len(ms), int(order), _p32(buf), n)
+    return _parse_description(buf.tolist())
+
+
+def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):
+    """Run the plan. cb(rows ndarray [m, n] int32, scores ndarray [m] or None) receives host
+    copies (DM_ALL); with DM_DEVICE_ROWS in mode it receives (rows_ptr, scores_ptr, m, n) raw
+    device pointers instead. Returns (count, checksum)."""
+    err = []
+
+    def _tramp(user, rows, scores, nrows, ncols):
+        try:
+            if mode & DM_DEVICE_ROWS:
+                r = cb(ctypes.cast(rows, ctypes.c_void_p).value, ctypes.cast(scores, ctypes.c_void_p).value,
+                       nrows, ncols)
+            else:
+                a = np.ctypeslib.as_array(rows, shape=(nrows * ncols,)).reshape(nrows, ncols).copy()
+                s = np.ctypeslib.as_array(scores, shape=(nrows,)).copy() if scores else None
+                r = cb(a, s)
+            return int(bool(r))
+        except BaseException as e:  # noqa: BLE001 - re-raised after the C call returns
+            err.append(e)
+            return 1
+
+    c_cb = DM_CHUNK_CB(_tramp) if cb is not None else DM_CHUNK_CB()
+    cnt, cs = _u64(), _u64()
+    rc = _lib.dm_match(ctx, plan, int(mode), c_cb, None, ctypes.byref(cnt), ctypes.byref(cs))
+    if err:
+        raise err[0]
+    _check(rc, "dm_match", ctx)
+    return cnt.value, cs.value
+
+
+def dm_match_batch(ctx, plans, mode: int = DM_COUNT):
+    arr = (_vp * len(plans))(*[p.value if isinstance(p, _vp) else p for p in plans])
+    counts = np.zeros(len(plans), dtype=np.uint64)
+    sums = np.zeros(len(plans), dtype=np.uint64)
+    rc = _lib.dm_match_batch(ctx, arr, len(plans), int(mode), counts.ctypes.data_as(_u64p),
+                             sums.ctypes.data_as(_u64p))
+    _check(rc, "dm_match_batch", ctx)
+    return counts, sums
+
+
+def dm_score_topk(ctx, plan, k: int, n_p: int):
+    rows = np.zeros((k, n_p), dtype=np.int32)
+    scores = np.zeros(k, dtype=np.float32)
+    n = _i32()
+    _check(_lib.dm_score_topk(ctx, plan, int(k), _p32(rows), scores.ctypes.data_as(_fp), ctypes.byref(n)),
+           "dm_score_topk", ctx)
+    return rows[:n.value], scores[:n.value]
+
+
+def dm_get_stats(ctx) -> dict:
+    s = dm_stats()
+    _check(_lib.dm_get_stats(ctx, ctypes.byref(s)), "dm_get_stats", ctx)
+    n = s.n_steps
+    return {"n_steps": n, "rows": list(s.rows[:n]), "candidates": list(s.candidates[:n]),
+            "chunks": s.chunks, "max_rows": s.max_rows, "join_ms": s.join_ms,
+            "join_launches": s.join_launches, "join_bytes": s.join_bytes, "total_ms": s.total_ms}
+
+
+def dm_enable_timing(ctx, on: bool = True) -> None:
+    _check(_lib.dm_enable_timing(ctx, int(bool(on))), "dm_enable_timing", ctx)
+
+
+# ------------------------------------------------------------------- convenience ----------
+class Context:
+    """Owns a dm_ctx; graphs are objects with n, row_ptr, col_idx[, edge_err, qubit_err]."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.h = dm_create(device, mem_budget_bytes)
+
+    def close(self):
+        if self.h:
+            dm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load(self, g, weights: bool = True) -> int:
+        return dm_load_data_graph(self.h, g.n, g.row_ptr, g.col_idx,
+                                  getattr(g, "edge_err", None) if weights else None,
+                                  getattr(g, "qubit_err", None) if weights else None)
+
+    def plan(self, graph: int, pattern, **kw):
+        return Plan(self, dm_plan(self.h, graph, pattern.n, pattern.row_ptr, pattern.col_idx, **kw), pattern.n)
+
+    def motif_table(self, graph: int, motif_id: int) -> np.ndarray:
+        return dm_motif_table(self.h, graph, motif_id)
+
+    def stats(self) -> dict:
+        return dm_get_stats(self.h)
+
+
+class Plan:
+    def __init__(self, ctx: Context, h, n_p: int):
+        self.ctx, self.h, self.n_p = ctx, h, n_p
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            dm_plan_free(self.h)
+            self.h = None
+
+    def describe(self) -> list[dict]:
+        return dm_plan_describe(self.h)
+
+    def all(self):
+        """All embeddings: (rows [count, n_p] int32 in canonical order, scores or None, count, checksum)."""
+        rows, scores = [], []
+
+        def cb(r, s):
+            rows.append(r)
+            if s is not None:
+                scores.append(s)
+            return 0
+
+        cnt, cs = dm_match(self.ctx.h, self.h, DM_ALL, cb)
+        R = np.concatenate(rows) if rows else np.zeros((0, self.n_p), dtype=np.int32)
+        S = np.concatenate(scores) if scores else None
+        return R, S, cnt, cs
+
+    def count(self):
+        return dm_match(self.ctx.h, self.h, DM_COUNT, None)
+
+    def topk(self, k: int):
+        return dm_score_topk(self.ctx.h, self.h, k, self.n_p)

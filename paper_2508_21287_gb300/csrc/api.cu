@@ -1,0 +1,1239 @@
+// C ABI of the Delta-Motif library: context, data-graph store, motif database (Alg. 2),
+// plans (Sec. 3.2), the chunked join executor (Alg. 1), canonical output, top-k scoring.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/dm.h"
+#include "dm_internal.h"
+#include "kernels.h"
+
+using namespace dmi;
+
+namespace {
+
+struct DevTable {
+  int32_t *rows = nullptr;
+  float *score = nullptr;
+  int64_t n = 0;
+  int32_t w = 0;
+};
+
+struct Index {
+  IndexView v{};
+  int32_t *rows = nullptr;
+  float *score = nullptr;
+  int32_t *offsets = nullptr;
+  HashSlot *slots = nullptr;
+  int64_t distinct = 0;
+  int64_t max_group = 0;
+  int64_t bytes = 0;
+};
+
+struct DevGraph {
+  int32_t V = 0;
+  int64_t nnz = 0;
+  int32_t *row_ptr = nullptr, *col_idx = nullptr;
+  float *eerr = nullptr, *qerr = nullptr;
+  unsigned long long *adj = nullptr;
+  int32_t adj_words = 0;
+  double avg_deg = 0;
+  int32_t max_deg = 0;
+  std::map<int, DevTable> motifs;
+  std::map<std::tuple<int, int, int>, Index> indices;
+};
+
+}  // namespace
+
+struct dm_ctx {
+  int device = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  int num_sms = 1;
+  uint64_t budget = 0;
+  std::vector<DevGraph *> graphs;
+  unsigned long long *d_ctr = nullptr, *h_ctr = nullptr;
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  dm_stats stats{};
+  int64_t inflight = 0;
+  std::string last_error;
+  void *h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+};
+
+struct dm_plan_s {
+  Plan p;
+};
+
+namespace {
+
+#define CK(x)                                              \
+  do {                                                     \
+    cudaError_t e_ = (x);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #x);    \
+  } while (0)
+#define RET(x)                     \
+  do {                             \
+    int r_ = (x);                  \
+    if (r_ != DM_OK) return r_;    \
+  } while (0)
+
+int cuda_fail(dm_ctx *c, cudaError_t e, const char *what) {
+  if (c) c->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return DM_E_NOMEM;
+  }
+  return DM_E_CUDA;
+}
+
+int dalloc(dm_ctx *c, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    c->last_error = "cudaMallocAsync failed";
+    return DM_E_NOMEM;
+  }
+  return DM_OK;
+}
+template <class T>
+int dalloc_t(dm_ctx *c, T **p, size_t count) {
+  return dalloc(c, (void **)p, count * sizeof(T));
+}
+void dfree(dm_ctx *c, void *p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+void free_table(dm_ctx *c, DevTable &t) {
+  dfree(c, t.rows);
+  dfree(c, t.score);
+  t.rows = nullptr;
+  t.score = nullptr;
+  t.n = 0;
+}
+
+int bit_length(int64_t x) {
+  int b = 0;
+  while (x > 0) {
+    b++;
+    x >>= 1;
+  }
+  return b;
+}
+
+// ------------------------------------------------------------------ host CSR checks ----
+struct HostCSR {
+  std::vector<int32_t> rp, ci;
+  std::vector<float> ee;
+};
+
+int validate_csr(int32_t n, const int32_t *rp, const int32_t *ci, const float *ee, HostCSR *out) {
+  if (n < 0 || !rp || (n > 0 && !ci && rp[n] > 0)) return DM_E_INVAL;
+  if (rp[0] != 0) return DM_E_INVAL;
+  out->rp.assign(n + 1, 0);
+  for (int32_t u = 0; u < n; u++) {
+    if (rp[u + 1] < rp[u]) return DM_E_INVAL;
+    int32_t prev = -1;
+    for (int32_t k = rp[u]; k < rp[u + 1]; k++) {
+      int32_t v = ci[k];
+      if (v < 0 || v >= n) return DM_E_INVAL;
+      if (v <= prev) return DM_E_INVAL;  // unsorted or duplicate
+      prev = v;
+      if (v == u) continue;              // self-loops are dropped (Res(M2) excludes them)
+      out->ci.push_back(v);
+      if (ee) out->ee.push_back(ee[k]);
+    }
+    out->rp[u + 1] = (int32_t)out->ci.size();
+  }
+  // symmetry (and equal weights on both directions)
+  for (int32_t u = 0; u < n; u++)
+    for (int32_t k = out->rp[u]; k < out->rp[u + 1]; k++) {
+      int32_t v = out->ci[k];
+      auto b = out->ci.begin() + out->rp[v], e = out->ci.begin() + out->rp[v + 1];
+      auto it = std::lower_bound(b, e, u);
+      if (it == e || *it != u) return DM_E_INVAL;
+      if (ee && out->ee[it - out->ci.begin()] != out->ee[k]) return DM_E_INVAL;
+    }
+  return DM_OK;
+}
+
+bool connected(const HostCSR &g, int32_t n) {
+  if (n <= 1) return true;
+  std::vector<char> seen(n, 0);
+  std::vector<int32_t> st{0};
+  seen[0] = 1;
+  int32_t cnt = 1;
+  while (!st.empty()) {
+    int32_t u = st.back();
+    st.pop_back();
+    for (int32_t k = g.rp[u]; k < g.rp[u + 1]; k++)
+      if (!seen[g.ci[k]]) {
+        seen[g.ci[k]] = 1;
+        cnt++;
+        st.push_back(g.ci[k]);
+      }
+  }
+  return cnt == n;
+}
+
+// ------------------------------------------------------------------ sorting ------------
+// Sort a table's rows lexicographically (column 0 most significant); ids < 2^bits.
+int sort_perm_by_columns(dm_ctx *c, const DevTable &t, const std::vector<int> &cols_msb_first, int bits,
+                         int32_t **perm_out) {
+  int64_t n = t.n;
+  int32_t *A = nullptr, *B = nullptr;
+  int64_t *hist = nullptr, *hscan = nullptr, *tmp = nullptr;
+  int64_t he = dmk::radix_hist_elems(n);
+  RET(dalloc_t(c, &A, n));
+  RET(dalloc_t(c, &B, n));
+  RET(dalloc_t(c, &hist, he));
+  RET(dalloc_t(c, &hscan, he + 1));
+  RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(he)));
+  CK(dmk::launch_iota(A, n, c->stream));
+  if (bits < 1) bits = 1;
+  for (int ci = (int)cols_msb_first.size() - 1; ci >= 0; ci--) {
+    int col = cols_msb_first[ci];
+    for (int shift = 0; shift < bits; shift += 8) {
+      CK(dmk::radix_pass((const uint32_t *)t.rows + col, t.w, A, B, n, shift, hist, hscan, tmp, c->stream));
+      std::swap(A, B);
+    }
+  }
+  dfree(c, B);
+  dfree(c, hist);
+  dfree(c, hscan);
+  dfree(c, tmp);
+  *perm_out = A;
+  return DM_OK;
+}
+
+int stable_sort_perm_by_score(dm_ctx *c, const DevTable &t, int32_t *&perm) {
+  int64_t n = t.n;
+  int32_t *B = nullptr;
+  int64_t *hist = nullptr, *hscan = nullptr, *tmp = nullptr;
+  int64_t he = dmk::radix_hist_elems(n);
+  RET(dalloc_t(c, &B, n));
+  RET(dalloc_t(c, &hist, he));
+  RET(dalloc_t(c, &hscan, he + 1));
+  RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(he)));
+  for (int shift = 0; shift < 32; shift += 8) {
+    CK(dmk::radix_pass((const uint32_t *)t.score, 1, perm, B, n, shift, hist, hscan, tmp, c->stream));
+    std::swap(perm, B);
+  }
+  dfree(c, B);
+  dfree(c, hist);
+  dfree(c, hscan);
+  dfree(c, tmp);
+  return DM_OK;
+}
+
+int gather_table(dm_ctx *c, const DevTable &t, const int32_t *perm, int64_t n, DevTable *out) {
+  DevTable o;
+  o.n = n;
+  o.w = t.w;
+  RET(dalloc_t(c, &o.rows, (size_t)n * t.w));
+  if (t.score) RET(dalloc_t(c, &o.score, n));
+  CK(dmk::launch_gather_rows(t.rows, t.score, perm, n, t.w, o.rows, o.score, c->stream));
+  *out = o;
+  return DM_OK;
+}
+
+// Replace t by its rows in canonical (lexicographic) order.
+int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
+  if (t.n <= 1) return DM_OK;
+  std::vector<int> cols(t.w);
+  for (int i = 0; i < t.w; i++) cols[i] = i;
+  int32_t *perm = nullptr;
+  RET(sort_perm_by_columns(c, t, cols, bits, &perm));
+  DevTable o;
+  RET(gather_table(c, t, perm, t.n, &o));
+  dfree(c, perm);
+  free_table(c, t);
+  t = o;
+  return DM_OK;
+}
+
+// ------------------------------------------------------------------ motif database -----
+int graph_bits(const DevGraph *g) { return std::max(1, bit_length((int64_t)g->V - 1)); }
+
+int read_ctr(dm_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(unsigned long long) * CTR_N, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DM_OK;
+}
+
+int ensure_index(dm_ctx *c, DevGraph *g, int motif, int kp0, int kp1, Index **out) {
+  auto key = std::make_tuple(motif, kp0, kp1);
+  auto it = g->indices.find(key);
+  if (it != g->indices.end()) {
+    *out = &it->second;
+    return DM_OK;
+  }
+  DevTable &T = g->motifs.at(motif);
+  Index ix;
+  ix.v.nkeys = kp1 >= 0 ? 2 : 1;
+  ix.v.kpos[0] = kp0;
+  ix.v.kpos[1] = kp1;
+  ix.v.mw = T.w;
+  ix.v.n = T.n;
+  DevTable sorted = T;
+  int32_t *perm = nullptr;
+  std::vector<int> cols{kp0};
+  if (kp1 >= 0) cols.push_back(kp1);
+  if (T.n > 0) {
+    RET(sort_perm_by_columns(c, T, cols, graph_bits(g), &perm));
+    RET(gather_table(c, T, perm, T.n, &sorted));
+    dfree(c, perm);
+  } else {
+    RET(dalloc_t(c, &sorted.rows, 1));
+    sorted.score = nullptr;
+  }
+  ix.rows = sorted.rows;
+  ix.score = sorted.score;
+  ix.v.rows = sorted.rows;
+  ix.v.score = sorted.score;
+  ix.bytes = T.n * (4 * T.w + (sorted.score ? 4 : 0));
+  if (kp1 < 0) {
+    RET(dalloc_t(c, &ix.offsets, (size_t)g->V + 1));
+    CK(dmk::launch_offsets_direct(sorted.rows, T.w, kp0, T.n, g->V, ix.offsets, c->stream));
+    std::vector<int32_t> off(g->V + 1);
+    CK(cudaMemcpyAsync(off.data(), ix.offsets, sizeof(int32_t) * (g->V + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int32_t v = 0; v < g->V; v++) {
+      int64_t l = off[v + 1] - off[v];
+      ix.distinct += l > 0;
+      ix.max_group = std::max(ix.max_group, l);
+    }
+    ix.v.offsets = ix.offsets;
+    ix.bytes += 4 * ((int64_t)g->V + 1);
+  } else {
+    uint32_t lg = 1;
+    while ((1ll << lg) < 2 * std::max<int64_t>(1, T.n)) lg++;
+    RET(dalloc_t(c, &ix.slots, (size_t)1 << lg));
+    CK(cudaMemsetAsync(ix.slots, 0xFF, sizeof(HashSlot) << lg, c->stream));
+    CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
+    CK(dmk::launch_hash_build(sorted.rows, T.w, kp0, kp1, T.n, ix.slots, lg, c->d_ctr, c->stream));
+    RET(read_ctr(c));
+    ix.distinct = (int64_t)c->h_ctr[0];
+    ix.max_group = (int64_t)c->h_ctr[1];
+    ix.v.slots = ix.slots;
+    ix.v.log2cap = lg;
+    ix.bytes += (int64_t)sizeof(HashSlot) << lg;
+  }
+  auto res = g->indices.emplace(key, ix);
+  *out = &res.first->second;
+  return DM_OK;
+}
+
+// ------------------------------------------------------------------ executor -----------
+struct Sink {
+  virtual ~Sink() {}
+  // Takes ownership of a table of final rows (pattern-vertex order, unsorted).
+  virtual int take(dm_ctx *c, DevTable t) = 0;
+};
+
+struct StepRT {
+  JoinArgs base{};
+  Index *ix = nullptr;
+  DevTable *seed_table = nullptr;
+  int tile_rows = 32;
+  int64_t max_group = 1;
+  int64_t motif_bytes = 0;
+};
+
+struct Exec {
+  dm_ctx *c;
+  DevGraph *g;
+  const Plan *p;
+  int mode;          // DM_ALL / DM_COUNT
+  bool use_qerr;
+  float prune = INFINITY;
+  Sink *sink = nullptr;
+  int64_t chunk_rows = 0, max_rows = 0;
+  std::vector<StepRT> st;
+  uint64_t count = 0, checksum = 0;
+
+  int setup() {
+    const int S = (int)p->steps.size();
+    st.assign(S, StepRT());
+    for (int j = 0; j < S; j++) {
+      const StepSpec &s = p->steps[j];
+      StepRT &r = st[j];
+      JoinArgs &a = r.base;
+      memset(&a, 0, sizeof(a));
+      if (j == 0) {
+        auto it = g->motifs.find(s.motif);
+        if (it == g->motifs.end()) return DM_E_NOTFOUND;
+        r.seed_table = &it->second;
+        a.ix.nkeys = 0;
+        a.ix.rows = it->second.rows;
+        a.ix.score = it->second.score;
+        a.ix.n = it->second.n;
+        a.ix.mw = it->second.w;
+        r.motif_bytes = it->second.n * (4 * it->second.w + (it->second.score ? 4 : 0));
+      } else {
+        if (s.n_keys < 1) return DM_E_INVAL;
+        RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1, &r.ix));
+        a.ix = r.ix->v;
+        r.max_group = std::max<int64_t>(1, r.ix->max_group);
+        r.motif_bytes = r.ix->bytes;
+      }
+      a.key_col[0] = s.n_keys > 0 ? s.key_col[0] : 0;
+      a.key_col[1] = s.n_keys > 1 ? s.key_col[1] : 0;
+      a.n_chk = std::max(0, s.n_keys - 2);
+      for (int i = 2; i < s.n_keys; i++) {
+        a.chk_mpos[i - 2] = (int8_t)s.key_mpos[i];
+        a.chk_col[i - 2] = (int8_t)s.key_col[i];
+      }
+      a.n_new = s.n_new;
+      for (int i = 0; i < s.n_new; i++) a.new_mpos[i] = (int8_t)s.new_mpos[i];
+      a.n_be = s.n_be;
+      for (int i = 0; i < s.n_be; i++) {
+        a.be_a[i] = (int8_t)s.be_col[i][0];
+        a.be_b[i] = (int8_t)s.be_col[i][1];
+      }
+      a.w = s.w_in;
+      a.wo = s.w_out;
+      for (int cc = 0; cc < a.wo; cc++) a.out_pos[cc] = (int8_t)(j == S - 1 ? p->col_vertex[cc] : cc);
+      a.adj = g->adj;
+      a.adj_words = g->adj_words;
+      a.row_ptr = g->row_ptr;
+      a.col_idx = g->col_idx;
+      a.eerr = g->eerr;
+      a.qerr = use_qerr ? g->qerr : nullptr;
+      a.scored = g->eerr != nullptr;
+      a.prune = prune;
+      a.mode = (j == S - 1 && mode == DM_COUNT) ? 1 : 0;
+      a.nx.nkeys = -1;
+      r.tile_rows = dmk::join_tile_rows(a.w);
+    }
+    for (int j = 0; j + 1 < S; j++) {
+      st[j].base.nx = st[j + 1].base.ix;
+      st[j].base.nx_key_col[0] = st[j + 1].base.key_col[0];
+      st[j].base.nx_key_col[1] = st[j + 1].base.key_col[1];
+    }
+    return DM_OK;
+  }
+
+  int64_t row_bytes(int j) const {
+    const JoinArgs &a = st[j].base;
+    return 4ll * a.wo + (a.scored ? 4 : 0) + (j + 1 < (int)st.size() ? 4 : 0);
+  }
+
+  // One join launch over `in` (or over seed rows [lo, hi) of the motif table at step 0).
+  int launch(int j, const DevTable &in, int64_t lo, int64_t hi, int64_t cap, DevTable *out, int32_t **out_next,
+             int64_t *next_total) {
+    const int S = (int)st.size();
+    JoinArgs a = st[j].base;
+    a.prune = prune;
+    DevTable o;
+    o.w = a.wo;
+    int32_t *nxt = nullptr;
+    if (a.mode == 0) {
+      RET(dalloc_t(c, &o.rows, (size_t)std::max<int64_t>(1, cap) * a.wo));
+      if (a.scored) RET(dalloc_t(c, &o.score, std::max<int64_t>(1, cap)));
+      if (j + 1 < S) RET(dalloc_t(c, &nxt, std::max<int64_t>(1, cap)));
+    }
+    a.out = o.rows;
+    a.outs = o.score;
+    a.out_next = nxt;
+    a.out_cap = cap;
+    a.ctr = c->d_ctr;
+    if (j == 0) {
+      a.R = nullptr;
+      a.Rs = nullptr;
+      a.N = 0;
+      a.seed_lo = lo;
+      a.seed_hi = hi;
+    } else {
+      a.R = in.rows;
+      a.Rs = in.score;
+      a.N = in.n;
+    }
+    CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
+    int grid = dmk::join_grid(a, st[j].tile_rows, c->num_sms);
+    if (c->timing) CK(cudaEventRecord(c->ev0, c->stream));
+    CK(dmk::launch_join(a, grid, st[j].tile_rows, c->stream));
+    if (c->timing) CK(cudaEventRecord(c->ev1, c->stream));
+    RET(read_ctr(c));
+    if (c->h_ctr[CTR_OVF]) {
+      c->last_error = "join output overflow";
+      free_table(c, o);
+      dfree(c, nxt);
+      return DM_E_CAPACITY;
+    }
+    int64_t rows = (int64_t)c->h_ctr[CTR_ROWS];
+    int64_t nin = j == 0 ? hi - lo : in.n;
+    if (c->timing) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      c->stats.join_ms += ms;
+    }
+    c->stats.join_launches++;
+    c->stats.chunks++;
+    double bytes = (double)st[j].motif_bytes + (double)nin * (4.0 * a.w + (a.Rs ? 4 : 0));
+    if (a.mode == 0) bytes += (double)rows * row_bytes(j);
+    c->stats.join_bytes += bytes;
+    if (j < DM_MAX_STEPS) {
+      c->stats.rows[j] += rows;
+      c->stats.candidates[j] += (int64_t)c->h_ctr[CTR_CAND];
+    }
+    if (a.mode == 1) {
+      count += (uint64_t)rows;
+      checksum += c->h_ctr[CTR_SUM];
+    }
+    o.n = rows;
+    *out = o;
+    if (out_next) *out_next = nxt;
+    if (next_total) *next_total = (int64_t)c->h_ctr[CTR_NEXT];
+    return DM_OK;
+  }
+
+  int64_t limit_rows(int j) const {
+    int64_t avail = (int64_t)c->budget - c->inflight;
+    int64_t lim = std::max<int64_t>(1, avail / row_bytes(j));
+    if (chunk_rows > 0) lim = std::min(lim, chunk_rows);
+    return lim;
+  }
+
+  // After a step-j output (or the seed) exists: run steps j+1.. on it.
+  int descend(int j, DevTable &t, int32_t *t_next, int64_t next_total) {
+    const int S = (int)st.size();
+    if (j == S - 1) {
+      if (mode == DM_COUNT) {  // counted inside the last launch
+        free_table(c, t);
+        dfree(c, t_next);
+        return DM_OK;
+      }
+      c->inflight -= t.n * row_bytes(j);
+      int r = sink->take(c, t);
+      dfree(c, t_next);
+      return r;
+    }
+    c->stats.max_rows = std::max(c->stats.max_rows, t.n);
+    int r = process(j + 1, t, t_next, next_total);
+    c->inflight -= t.n * row_bytes(j);
+    free_table(c, t);
+    dfree(c, t_next);
+    return r;
+  }
+
+  int run_one(int j, const DevTable &in, int64_t lo, int64_t hi, int64_t cap) {
+    DevTable o;
+    int32_t *onext = nullptr;
+    int64_t ntot = 0;
+    RET(launch(j, in, lo, hi, cap, &o, &onext, &ntot));
+    if (st[j].base.mode == 1) return DM_OK;
+    c->inflight += o.n * row_bytes(j);
+    return descend(j, o, onext, ntot);
+  }
+
+  // Process step j over the rows of `in`; in_next[i] is the candidate count of row i.
+  int process(int j, const DevTable &in, const int32_t *in_next, int64_t cand_total) {
+    if (in.n == 0) return DM_OK;
+    if (max_rows > 0 && cand_total > max_rows) return DM_E_CAPACITY;
+    const bool count_last = st[j].base.mode == 1;
+    int64_t lim = limit_rows(j);
+    if (count_last || cand_total <= lim || in.n == 1) return run_one(j, in, 0, 0, std::max<int64_t>(1, cand_total));
+    // chunked streaming: split the input so that each chunk's candidates fit the budget
+    int64_t *pre = nullptr, *tmp = nullptr;
+    RET(dalloc_t(c, &pre, in.n + 1));
+    RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(in.n)));
+    CK(dmk::scan_i32(in_next, pre, in.n, tmp, c->stream));
+    int64_t step = std::max<int64_t>(1, lim - st[j].max_group);
+    int64_t nch = (cand_total + step - 1) / step;
+    std::vector<int64_t> hpre(in.n + 1);
+    // boundaries: the last row index whose prefix is <= i * step
+    CK(cudaMemcpyAsync(hpre.data(), pre, sizeof(int64_t) * (in.n + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, pre);
+    dfree(c, tmp);
+    std::vector<int64_t> b{0};
+    for (int64_t i = 1; i < nch; i++) {
+      int64_t target = i * step;
+      int64_t idx = (int64_t)(std::upper_bound(hpre.begin(), hpre.end(), target) - hpre.begin()) - 1;
+      if (idx > b.back()) b.push_back(idx);
+    }
+    if (b.size() == 1 && in.n > 1) b.push_back(in.n / 2);  // always make progress
+    b.push_back(in.n);
+    for (size_t i = 0; i + 1 < b.size(); i++) {
+      int64_t lo = b[i], hi = b[i + 1];
+      if (hi <= lo) continue;
+      DevTable sub;
+      sub.rows = in.rows + lo * in.w;
+      sub.score = in.score ? in.score + lo : nullptr;
+      sub.n = hi - lo;
+      sub.w = in.w;
+      int64_t sc = hpre[hi] - hpre[lo];
+      if (sc == 0) continue;
+      if (sc <= limit_rows(j) || sub.n == 1) RET(run_one(j, sub, 0, 0, sc));
+      else RET(process(j, sub, in_next + lo, sc));
+    }
+    return DM_OK;
+  }
+
+  int run() {
+    RET(setup());
+    const int S = (int)st.size();
+    c->stats.n_steps = S;
+    DevTable *T = st[0].seed_table;
+    int64_t n0 = T->n;
+    if (n0 == 0) return DM_OK;
+    // the seed step: candidates are the motif-table rows, chunked like any other step
+    int64_t lim = st[0].base.mode == 1 ? n0 : limit_rows(0);
+    for (int64_t lo = 0; lo < n0; lo += lim) {
+      int64_t hi = std::min(n0, lo + lim);
+      DevTable none;
+      RET(run_one(0, none, lo, hi, hi - lo));
+    }
+    return DM_OK;
+  }
+};
+
+struct CollectSink : Sink {
+  std::vector<DevTable> parts;
+  int take(dm_ctx *, DevTable t) override {
+    parts.push_back(t);
+    return DM_OK;
+  }
+  int concat(dm_ctx *c, int32_t w, bool scored, DevTable *out) {
+    int64_t n = 0;
+    for (auto &p : parts) n += p.n;
+    DevTable o;
+    o.n = n;
+    o.w = w;
+    RET(dalloc_t(c, &o.rows, (size_t)std::max<int64_t>(1, n) * w));
+    if (scored) RET(dalloc_t(c, &o.score, std::max<int64_t>(1, n)));
+    int64_t off = 0;
+    for (auto &p : parts) {
+      if (p.n) {
+        CK(cudaMemcpyAsync(o.rows + off * w, p.rows, sizeof(int32_t) * p.n * w, cudaMemcpyDeviceToDevice, c->stream));
+        if (scored && p.score)
+          CK(cudaMemcpyAsync(o.score + off, p.score, sizeof(float) * p.n, cudaMemcpyDeviceToDevice, c->stream));
+      }
+      off += p.n;
+      free_table(c, p);
+    }
+    parts.clear();
+    *out = o;
+    return DM_OK;
+  }
+};
+
+int deliver(dm_ctx *c, const DevTable &t, int flags, dm_chunk_cb cb, void *user) {
+  if (!cb || t.n == 0) return DM_OK;
+  if (flags & DM_DEVICE_ROWS) {
+    CK(cudaStreamSynchronize(c->stream));
+    return cb(user, t.rows, t.score, t.n, t.w) ? DM_E_CANCELLED : DM_OK;
+  }
+  const int64_t rb = 4ll * t.w + (t.score ? 4 : 0);
+  int64_t per = std::max<int64_t>(1, (int64_t)c->h_stage_bytes / rb);
+  for (int64_t lo = 0; lo < t.n; lo += per) {
+    int64_t m = std::min(per, t.n - lo);
+    int32_t *hr = (int32_t *)c->h_stage;
+    float *hs = t.score ? (float *)(hr + m * t.w) : nullptr;
+    CK(cudaMemcpyAsync(hr, t.rows + lo * t.w, sizeof(int32_t) * m * t.w, cudaMemcpyDeviceToHost, c->stream));
+    if (hs) CK(cudaMemcpyAsync(hs, t.score + lo, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (cb(user, hr, hs, m, t.w)) return DM_E_CANCELLED;
+  }
+  return DM_OK;
+}
+
+struct AllSink : Sink {
+  int flags;
+  dm_chunk_cb cb;
+  void *user;
+  int bits;
+  std::vector<DevTable> held;
+  int64_t held_bytes = 0;
+  bool streaming = false;
+  uint64_t count = 0, checksum = 0;
+  int flush_one(dm_ctx *c, DevTable &t) {
+    RET(sort_canonical(c, t, bits));
+    CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
+    CK(dmk::launch_hash_rows(t.rows, t.n, t.w, c->d_ctr, c->stream));
+    RET(read_ctr(c));
+    count += (uint64_t)t.n;
+    checksum += c->h_ctr[CTR_SUM];
+    int r = deliver(c, t, flags, cb, user);
+    free_table(c, t);
+    return r;
+  }
+  int take(dm_ctx *c, DevTable t) override {
+    int64_t tb = t.n * (4ll * t.w + (t.score ? 4 : 0));
+    if (!streaming && held_bytes + tb <= (int64_t)c->budget / 2) {
+      held.push_back(t);
+      held_bytes += tb;
+      return DM_OK;
+    }
+    streaming = true;
+    for (auto &h : held) RET(flush_one(c, h));
+    held.clear();
+    held_bytes = 0;
+    return flush_one(c, t);
+  }
+  int finish(dm_ctx *c, int32_t w, bool scored) {
+    if (held.empty()) return DM_OK;
+    CollectSink cs;
+    cs.parts = held;
+    held.clear();
+    DevTable all;
+    RET(cs.concat(c, w, scored, &all));
+    return flush_one(c, all);
+  }
+};
+
+// Top-k of a table (rows in pattern order + scores) by (score, row): a new table of
+// min(k, n) rows in that order.
+int topk_table(dm_ctx *c, DevGraph *g, const DevTable &t, int64_t k, DevTable *out) {
+  int64_t n = t.n;
+  int32_t *idx = nullptr;
+  int64_t m = n;
+  if (n > k) {
+    uint32_t prefix = 0, pmask = 0;
+    int64_t kk = k;
+    unsigned long long *hist = nullptr;
+    RET(dalloc_t(c, &hist, 256));
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), c->stream));
+      CK(dmk::launch_score_hist(t.score, n, prefix, pmask, shift, hist, c->stream));
+      unsigned long long h[256];
+      CK(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      int64_t cum = 0;
+      int d = 0;
+      for (; d < 256; d++) {
+        if (cum + (int64_t)h[d] >= kk) break;
+        cum += (int64_t)h[d];
+      }
+      kk -= cum;
+      prefix |= (uint32_t)d << shift;
+      pmask |= 255u << shift;
+    }
+    dfree(c, hist);
+    RET(dalloc_t(c, &idx, n));
+    CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
+    CK(dmk::launch_select_le(t.score, n, prefix, idx, c->d_ctr, c->stream));
+    RET(read_ctr(c));
+    m = (int64_t)c->h_ctr[0];
+  } else {
+    RET(dalloc_t(c, &idx, std::max<int64_t>(1, n)));
+    CK(dmk::launch_iota(idx, n, c->stream));
+  }
+  DevTable cand;
+  RET(gather_table(c, t, idx, m, &cand));
+  dfree(c, idx);
+  // (score, row) order: canonical sort by row, then a stable sort by score
+  RET(sort_canonical(c, cand, graph_bits(g)));
+  int32_t *perm = nullptr;
+  RET(dalloc_t(c, &perm, std::max<int64_t>(1, m)));
+  CK(dmk::launch_iota(perm, m, c->stream));
+  RET(stable_sort_perm_by_score(c, cand, perm));
+  DevTable o;
+  RET(gather_table(c, cand, perm, std::min(k, m), &o));
+  dfree(c, perm);
+  free_table(c, cand);
+  *out = o;
+  return DM_OK;
+}
+
+struct TopkSink : Sink {
+  DevGraph *g;
+  int64_t k;
+  DevTable best;  // current best min(k, seen) rows
+  bool have = false;
+  float *prune_ptr = nullptr;
+  int take(dm_ctx *c, DevTable t) override {
+    DevTable tk;
+    RET(topk_table(c, g, t, k, &tk));
+    free_table(c, t);
+    if (have) {
+      CollectSink cs;
+      cs.parts = {best, tk};
+      DevTable both;
+      RET(cs.concat(c, tk.w, true, &both));
+      RET(topk_table(c, g, both, k, &best));
+      free_table(c, both);
+    } else {
+      best = tk;
+      have = true;
+    }
+    if (prune_ptr && best.n == k) {  // rows scoring above the k-th best can never enter
+      float kth;
+      CK(cudaMemcpyAsync(&kth, best.score + (k - 1), sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      *prune_ptr = kth;
+    }
+    return DM_OK;
+  }
+};
+
+int ensure_motif(dm_ctx *c, DevGraph *g, int id);
+
+int build_motif_by_joins(dm_ctx *c, DevGraph *g, const MotifDef &md) {
+  // Alg. 2: Res(M) <- Delta-Motif(M, DB), with DB = Res(M2) plus the smaller motifs built so far
+  Plan mp;
+  mp.n_p = md.k;
+  std::vector<std::vector<int>> adj(md.k);
+  for (auto &e : md.edges) {
+    adj[e.first].push_back(e.second);
+    adj[e.second].push_back(e.first);
+  }
+  mp.rp.assign(md.k + 1, 0);
+  for (int u = 0; u < md.k; u++) {
+    std::sort(adj[u].begin(), adj[u].end());
+    mp.rp[u + 1] = mp.rp[u] + (int)adj[u].size();
+    for (int v : adj[u]) mp.ci.push_back(v);
+  }
+  std::vector<int32_t> set{2};
+  for (auto &kv : g->motifs) {
+    MotifDef d;
+    if (kv.first >= 2 && motif_def(kv.first, &d) && d.k < md.k) set.push_back(kv.first);
+  }
+  RET(ensure_motif(c, g, 2));
+  GraphStats gs;
+  gs.V = g->V;
+  int r = decompose(mp, set, DM_ORDER_PAPER, gs, nullptr, nullptr, &mp.steps, mp.col_vertex);
+  if (r != DM_OK) return r;
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &mp;
+  ex.mode = DM_ALL;
+  ex.use_qerr = false;
+  CollectSink sink;
+  ex.sink = &sink;
+  dm_stats saved = c->stats;
+  r = ex.run();
+  c->stats = saved;
+  if (r != DM_OK) return r;
+  DevTable t;
+  RET(sink.concat(c, md.k, g->eerr != nullptr, &t));
+  g->motifs[md.id] = t;
+  return DM_OK;
+}
+
+int ensure_motif(dm_ctx *c, DevGraph *g, int id) {
+  if (g->motifs.count(id)) return DM_OK;
+  DevTable t;
+  if (id == MOTIF_VERTEX) {
+    t.n = g->V;
+    t.w = 1;
+    RET(dalloc_t(c, &t.rows, std::max(1, g->V)));
+    if (g->eerr) RET(dalloc_t(c, &t.score, std::max(1, g->V)));
+    CK(dmk::launch_vertex_table(g->V, t.rows, t.score, c->stream));
+    g->motifs[id] = t;
+    return DM_OK;
+  }
+  if (id == 2) {
+    t.n = g->nnz;
+    t.w = 2;
+    RET(dalloc_t(c, &t.rows, (size_t)std::max<int64_t>(1, g->nnz) * 2));
+    if (g->eerr) RET(dalloc_t(c, &t.score, std::max<int64_t>(1, g->nnz)));
+    CK(dmk::launch_csr_to_m2(g->row_ptr, g->col_idx, g->eerr, g->V, g->nnz, t.rows, t.score, c->stream));
+    g->motifs[id] = t;
+    return DM_OK;
+  }
+  MotifDef md;
+  if (!motif_def(id, &md)) return DM_E_NOTFOUND;
+  return build_motif_by_joins(c, g, md);
+}
+
+DevGraph *get_graph(dm_ctx *c, dm_graph g) {
+  if (!c || g < 0 || g >= (int)c->graphs.size()) return nullptr;
+  return c->graphs[g];
+}
+
+void reset_stats(dm_ctx *c) { memset(&c->stats, 0, sizeof(c->stats)); }
+
+}  // namespace
+
+// =================================================================== C ABI ==============
+extern "C" {
+
+const char *dm_strerror(int code) {
+  switch (code) {
+    case DM_OK: return "ok";
+    case DM_E_INVAL: return "invalid argument or malformed graph";
+    case DM_E_DISCONNECTED: return "graph not connected";
+    case DM_E_NOMEM: return "out of memory";
+    case DM_E_CAPACITY: return "capacity exceeded";
+    case DM_E_TIMEOUT: return "device wait timed out";
+    case DM_E_CUDA: return "CUDA error";
+    case DM_E_CANCELLED: return "cancelled by callback";
+    case DM_E_NOTFOUND: return "unknown graph or motif";
+    default: return "unknown error";
+  }
+}
+
+const char *dm_last_error(dm_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int dm_create(dm_ctx **out, int device, uint64_t mem_budget_bytes) {
+  if (!out) return DM_E_INVAL;
+  dm_ctx *c = new dm_ctx();
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    return DM_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return DM_E_CUDA;
+  }
+  c->stream = c->own;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (cudaMalloc(&c->d_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess ||
+      cudaMallocHost(&c->h_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess) {
+    dm_destroy(c);
+    return DM_E_NOMEM;
+  }
+  c->h_stage_bytes = 64ull << 20;
+  if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) {
+    dm_destroy(c);
+    return DM_E_NOMEM;
+  }
+  cudaEventCreate(&c->ev0);
+  cudaEventCreate(&c->ev1);
+  if (dm_set_budget(c, mem_budget_bytes) != DM_OK) {
+    dm_destroy(c);
+    return DM_E_CUDA;
+  }
+  *out = c;
+  return DM_OK;
+}
+
+int dm_set_budget(dm_ctx *c, uint64_t bytes) {
+  if (!c) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  if (bytes == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return DM_E_CUDA;
+    bytes = fr / 2;
+  }
+  c->budget = bytes;
+  return DM_OK;
+}
+
+int dm_set_stream(dm_ctx *c, void *stream) {
+  if (!c) return DM_E_INVAL;
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  return DM_OK;
+}
+
+int dm_destroy(dm_ctx *c) {
+  if (!c) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (DevGraph *g : c->graphs) {
+    if (!g) continue;
+    for (auto &kv : g->motifs) {
+      cudaFreeAsync(kv.second.rows, c->stream);
+      if (kv.second.score) cudaFreeAsync(kv.second.score, c->stream);
+    }
+    for (auto &kv : g->indices) {
+      cudaFreeAsync(kv.second.rows, c->stream);
+      if (kv.second.score) cudaFreeAsync(kv.second.score, c->stream);
+      if (kv.second.offsets) cudaFreeAsync(kv.second.offsets, c->stream);
+      if (kv.second.slots) cudaFreeAsync(kv.second.slots, c->stream);
+    }
+    cudaFree(g->row_ptr);
+    cudaFree(g->col_idx);
+    cudaFree(g->eerr);
+    cudaFree(g->qerr);
+    cudaFree(g->adj);
+    delete g;
+  }
+  cudaStreamSynchronize(c->stream);
+  if (c->d_ctr) cudaFree(c->d_ctr);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+  return DM_OK;
+}
+
+int dm_load_data_graph(dm_ctx *c, int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const float *edge_err,
+                       const float *qubit_err, dm_graph *out) {
+  if (!c || !out || n < 1) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  HostCSR h;
+  RET(validate_csr(n, row_ptr, col_idx, edge_err, &h));
+  if (!connected(h, n)) return DM_E_DISCONNECTED;
+  DevGraph *g = new DevGraph();
+  g->V = n;
+  g->nnz = (int64_t)h.ci.size();
+  int32_t md = 0;
+  for (int32_t u = 0; u < n; u++) md = std::max(md, h.rp[u + 1] - h.rp[u]);
+  g->max_deg = md;
+  g->avg_deg = (double)g->nnz / n;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) return DM_E_NOMEM;
+    if (bytes && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return DM_E_CUDA;
+    return DM_OK;
+  };
+  int r = up((void **)&g->row_ptr, h.rp.data(), sizeof(int32_t) * (n + 1));
+  if (r == DM_OK) r = up((void **)&g->col_idx, h.ci.data(), sizeof(int32_t) * h.ci.size());
+  if (r == DM_OK && edge_err) r = up((void **)&g->eerr, h.ee.data(), sizeof(float) * h.ee.size());
+  if (r == DM_OK && qubit_err) r = up((void **)&g->qerr, qubit_err, sizeof(float) * n);
+  if (r == DM_OK && n <= 65536) {
+    g->adj_words = (n + 63) / 64;
+    size_t bytes = (size_t)n * g->adj_words * 8;
+    if (cudaMalloc(&g->adj, bytes) != cudaSuccess) r = DM_E_NOMEM;
+    else if (cudaMemsetAsync(g->adj, 0, bytes, c->stream) != cudaSuccess) r = DM_E_CUDA;
+    else if (dmk::launch_bitmap(g->row_ptr, g->col_idx, n, g->nnz, g->adj_words, g->adj, c->stream) != cudaSuccess)
+      r = DM_E_CUDA;
+  }
+  if (r == DM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) r = DM_E_CUDA;
+  c->graphs.push_back(g);
+  *out = (dm_graph)(c->graphs.size() - 1);
+  if (r == DM_OK) r = ensure_motif(c, g, 2);
+  if (r != DM_OK) return r;
+  return DM_OK;
+}
+
+int dm_motif_table(dm_ctx *c, dm_graph gh, int32_t motif_id, int32_t *out_rows, int64_t cap, int64_t *out_n,
+                   int32_t *out_k) {
+  DevGraph *g = get_graph(c, gh);
+  if (!g) return DM_E_NOTFOUND;
+  cudaSetDevice(c->device);
+  RET(ensure_motif(c, g, motif_id));
+  DevTable &T = g->motifs.at(motif_id);
+  if (out_n) *out_n = T.n;
+  if (out_k) *out_k = T.w;
+  if (out_rows && cap > 0 && T.n > 0) {
+    DevTable s;
+    s.n = T.n;
+    s.w = T.w;
+    RET(dalloc_t(c, &s.rows, (size_t)T.n * T.w));
+    CK(cudaMemcpyAsync(s.rows, T.rows, sizeof(int32_t) * T.n * T.w, cudaMemcpyDeviceToDevice, c->stream));
+    RET(sort_canonical(c, s, graph_bits(g)));
+    int64_t m = std::min(cap, s.n);
+    CK(cudaMemcpyAsync(out_rows, s.rows, sizeof(int32_t) * m * s.w, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    free_table(c, s);
+  }
+  return DM_OK;
+}
+
+int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
+            const dm_plan_opts *opts, dm_plan_t **out) {
+  if (!c || !out) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, gh);
+  if (!g) return DM_E_NOTFOUND;
+  if (n_p < 1 || n_p > MAXW) return DM_E_INVAL;
+  if (opts && opts->induced) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  HostCSR h;
+  RET(validate_csr(n_p, p_row_ptr, p_col_idx, nullptr, &h));
+  if (!connected(h, n_p)) return DM_E_DISCONNECTED;
+  std::unique_ptr<dm_plan_t> pl(new dm_plan_t());
+  Plan &p = pl->p;
+  p.n_p = n_p;
+  p.rp = h.rp;
+  p.ci = h.ci;
+  p.graph = gh;
+  p.order = opts ? opts->order : DM_ORDER_PAPER;
+  p.join_algo = opts ? opts->join_algo : DM_JOIN_AUTO;
+  p.chunk_rows = opts ? opts->chunk_rows : 0;
+  p.max_rows = opts ? opts->max_rows : 0;
+  if (opts && opts->motifs && opts->n_motifs > 0) {
+    p.motifs.assign(opts->motifs, opts->motifs + opts->n_motifs);
+  } else if (g->max_deg <= 3) {
+    p.motifs = {4, 2};  // heavy-hex preset of Sec. 5.1: {M2, M4}
+  } else if (g->max_deg == 4) {
+    p.motifs = {DM_MOTIF_CYCLE(4), DM_MOTIF_CYCLE(6), 2};  // square-grid preset: {M2, M4-O, M6-O}
+  } else {
+    p.motifs = {3, 2};
+  }
+  GraphStats gs;
+  gs.V = g->V;
+  gs.nnz = g->nnz;
+  gs.avg_deg = g->avg_deg;
+  gs.max_deg = g->max_deg;
+  for (int id : p.motifs) {
+    MotifDef md;
+    if (!motif_def(id, &md) || md.k < 2 || md.k > MAXM) return DM_E_NOTFOUND;
+    RET(ensure_motif(c, g, id));
+    gs.motifs.push_back({id, g->motifs.at(id).n});
+  }
+  if (n_p == 1) RET(ensure_motif(c, g, MOTIF_VERTEX));
+  RET(decompose(p, p.motifs, p.order, gs, nullptr, nullptr, &p.steps, p.col_vertex));
+  if ((int)p.steps.size() > DM_MAX_STEPS) return DM_E_CAPACITY;
+  for (size_t j = 1; j < p.steps.size(); j++) {
+    Index *ix;
+    const StepSpec &s = p.steps[j];
+    RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1, &ix));
+  }
+  *out = pl.release();
+  return DM_OK;
+}
+
+void dm_plan_free(dm_plan_t *p) { delete p; }
+
+static int32_t describe_steps(const std::vector<StepSpec> &steps, int32_t *buf, int32_t buf_len) {
+  std::vector<int32_t> v;
+  v.push_back((int32_t)steps.size());
+  for (auto &s : steps) {
+    v.push_back(s.motif);
+    v.push_back(s.k);
+    for (int i = 0; i < s.k; i++) v.push_back(s.slice[i]);
+    v.push_back(s.n_keys);
+    v.push_back(s.n_be);
+    for (int i = 0; i < s.n_be; i++) {
+      v.push_back(s.be_vtx[i][0]);
+      v.push_back(s.be_vtx[i][1]);
+    }
+  }
+  if (buf)
+    for (int32_t i = 0; i < buf_len && i < (int32_t)v.size(); i++) buf[i] = v[i];
+  return (int32_t)v.size();
+}
+
+int32_t dm_plan_describe(const dm_plan_t *pl, int32_t *buf, int32_t buf_len) {
+  if (!pl) return DM_E_INVAL;
+  return describe_steps(pl->p.steps, buf, buf_len);
+}
+
+int32_t dm_decompose(int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx, const int32_t *motifs,
+                     int32_t n_motifs, int32_t order, int32_t *buf, int32_t buf_len) {
+  if (n_p < 1 || n_p > MAXW || (n_motifs > 0 && !motifs) || n_motifs < 0) return DM_E_INVAL;
+  HostCSR h;
+  RET(validate_csr(n_p, p_row_ptr, p_col_idx, nullptr, &h));
+  if (!connected(h, n_p)) return DM_E_DISCONNECTED;
+  Plan p;
+  p.n_p = n_p;
+  p.rp = h.rp;
+  p.ci = h.ci;
+  std::vector<int32_t> set(motifs, motifs + n_motifs);
+  GraphStats gs;
+  gs.V = 1;
+  gs.avg_deg = 1;
+  gs.max_deg = 1;
+  for (int id : set) gs.motifs.push_back({id, 1});
+  RET(decompose(p, set, order, gs, nullptr, nullptr, &p.steps, p.col_vertex));
+  return describe_steps(p.steps, buf, buf_len);
+}
+
+int dm_match(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *user, uint64_t *out_count,
+             uint64_t *out_checksum) {
+  if (!c || !pl) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  int base_mode = mode & 0xF;
+  if (base_mode != DM_ALL && base_mode != DM_COUNT) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &pl->p;
+  ex.mode = base_mode;
+  ex.use_qerr = true;
+  ex.chunk_rows = pl->p.chunk_rows;
+  ex.max_rows = pl->p.max_rows;
+  c->inflight = 0;
+  AllSink sink;
+  sink.flags = mode;
+  sink.cb = cb;
+  sink.user = user;
+  sink.bits = graph_bits(g);
+  ex.sink = &sink;
+  int r = ex.run();
+  uint64_t cnt = ex.count, cs = ex.checksum;
+  if (r == DM_OK && base_mode == DM_ALL) {
+    r = sink.finish(c, pl->p.n_p, g->eerr != nullptr);
+    cnt = sink.count;
+    cs = sink.checksum;
+  }
+  for (auto &h : sink.held) free_table(c, h);
+  cudaStreamSynchronize(c->stream);
+  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (r != DM_OK) return r;
+  if (out_count) *out_count = cnt;
+  if (out_checksum) *out_checksum = cs;
+  return DM_OK;
+}
+
+int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, int mode, uint64_t *out_counts,
+                   uint64_t *out_checksums) {
+  if (!c || (!plans && n_plans > 0) || n_plans < 0 || (mode & 0xF) != DM_COUNT) return DM_E_INVAL;
+  for (int32_t i = 0; i < n_plans; i++) {
+    uint64_t cnt = 0, cs = 0;
+    RET(dm_match(c, plans[i], DM_COUNT, nullptr, nullptr, &cnt, &cs));
+    if (out_counts) out_counts[i] = cnt;
+    if (out_checksums) out_checksums[i] = cs;
+  }
+  return DM_OK;
+}
+
+int dm_score_topk(dm_ctx *c, const dm_plan_t *pl, int32_t k, int32_t *out_rows, float *out_scores, int32_t *out_n) {
+  if (!c || !pl || k < 1 || !out_rows || !out_n) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  if (!g->eerr) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &pl->p;
+  ex.mode = DM_ALL;
+  ex.use_qerr = true;
+  ex.chunk_rows = pl->p.chunk_rows;
+  ex.max_rows = pl->p.max_rows;
+  c->inflight = 0;
+  TopkSink sink;
+  sink.g = g;
+  sink.k = k;
+  sink.prune_ptr = &ex.prune;
+  ex.sink = &sink;
+  int r = ex.run();
+  if (r == DM_OK) {
+    int64_t m = sink.have ? sink.best.n : 0;
+    if (m > 0) {
+      CK(cudaMemcpyAsync(out_rows, sink.best.rows, sizeof(int32_t) * m * sink.best.w, cudaMemcpyDeviceToHost, c->stream));
+      if (out_scores)
+        CK(cudaMemcpyAsync(out_scores, sink.best.score, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *out_n = (int32_t)m;
+  }
+  if (sink.have) free_table(c, sink.best);
+  cudaStreamSynchronize(c->stream);
+  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return r;
+}
+
+int dm_get_stats(dm_ctx *c, dm_stats *out) {
+  if (!c || !out) return DM_E_INVAL;
+  *out = c->stats;
+  return DM_OK;
+}
+
+int dm_enable_timing(dm_ctx *c, int on) {
+  if (!c) return DM_E_INVAL;
+  c->timing = on != 0;
+  return DM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal types of the Delta-Motif GB300 library: plan steps (host) and the POD argument
+// blocks the kernels receive by value. Nothing here is part of the C ABI.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace dmi {
+
+constexpr int MAXW = 64;   // pattern vertices = maximum row width of an intermediate table
+constexpr int MAXM = 20;   // motif vertices
+constexpr int MAXBE = 64;  // back-edge checks in one step
+constexpr int MAXSTEPS = 128;
+
+constexpr int MOTIF_VERTEX = 1;  // the one-vertex "motif" (degenerate single-vertex pattern)
+
+// ------------------------------------------------------------------- motifs (host) -----
+struct MotifDef {
+  int id = 0;
+  int k = 0;
+  std::vector<std::pair<int, int>> edges;
+  uint32_t adj[MAXM] = {};  // adjacency bitmask per motif position
+  int parent[MAXM] = {};    // an earlier neighbour of each position (-1 for position 0)
+  std::string name;
+};
+
+bool motif_def(int id, MotifDef *out);
+
+// ------------------------------------------------------------------- plans (host) ------
+// One join step of Alg. 1: R <- FilterOverlappingNodes(InnerJoin(R, Res(M), C)).
+struct StepSpec {
+  int32_t motif = 0;
+  int32_t k = 0;
+  int32_t slice[MAXM] = {};    // motif position -> pattern vertex (the slice S_i)
+  int32_t n_keys = 0;          // motif positions whose pattern vertex is already mapped
+  int32_t key_mpos[MAXM] = {}; // ... ascending
+  int32_t key_col[MAXM] = {};  // ... and the working column holding that vertex
+  int32_t n_new = 0;           // new positions (ascending); they become columns w_in + i
+  int32_t new_mpos[MAXM] = {};
+  int32_t w_in = 0, w_out = 0;
+  int32_t n_be = 0;            // uncovered pattern edges closed by this step (back-edges)
+  int32_t be_col[MAXBE][2] = {};
+  int32_t be_vtx[MAXBE][2] = {};
+  double est_rows = 0.0;       // planner's estimate of the rows after the step
+  float feat[32] = {};         // features seen by the cardinality model
+};
+
+struct MotifStats {
+  int32_t id;
+  int64_t rows;      // |Res(M)|
+};
+
+struct GraphStats {
+  int32_t V = 0;
+  int64_t nnz = 0;
+  double avg_deg = 0, max_deg = 0;
+  std::vector<MotifStats> motifs;
+  int64_t rows_of(int id) const {
+    for (auto &m : motifs)
+      if (m.id == id) return m.rows;
+    return -1;
+  }
+};
+
+// Cardinality model: returns predicted log(rows after the step) for each candidate (one
+// feature vector of NFEAT floats each). Used by DM_ORDER_LEARNED.
+constexpr int NFEAT = 32;
+typedef int (*CardModelFn)(void *self, const float *feats, int n, float *out_log_rows);
+
+struct Plan {
+  int32_t n_p = 0;
+  std::vector<int32_t> rp, ci;          // pattern CSR
+  std::vector<int32_t> motifs;          // motif set used
+  std::vector<StepSpec> steps;
+  int32_t col_vertex[MAXW] = {};        // working column -> pattern vertex
+  int32_t graph = -1;
+  int32_t order = 0, join_algo = 0;
+  int64_t chunk_rows = 0, max_rows = 0;
+};
+
+// Decompose a pattern (Sec. 3.2). Returns 0 or a DM_E_* code.
+int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
+              const GraphStats &gs, CardModelFn model, void *model_self, std::vector<StepSpec> *out,
+              int32_t *col_vertex);
+
+// Features of a candidate step (for the heuristic and the learned model).
+void step_features(const StepSpec &s, double log_rows_prev, int n_p, int mapped_before,
+                   int uncovered_before, const GraphStats &gs, float *feat);
+double heuristic_log_rows(const float *feat);
+
+// ------------------------------------------------------------------- device args -------
+struct HashSlot {
+  unsigned long long key;
+  int32_t start;
+  int32_t len;
+};
+constexpr unsigned long long HASH_EMPTY = ~0ull;
+
+struct IndexView {
+  int32_t nkeys;          // 0 = every row matches, 1 = direct offsets, 2 = hashed packed key
+  int32_t kpos[2];        // motif positions forming the key
+  const int32_t *rows;    // motif rows sorted by key, [n x mw]
+  const float *score;     // edge-error sum of each motif row (nullable)
+  int64_t n;
+  int32_t mw;
+  const int32_t *offsets; // nkeys == 1: [V + 1]
+  const HashSlot *slots;  // nkeys == 2: 2^log2cap slots
+  uint32_t log2cap;
+};
+
+enum { CTR_ROWS = 0, CTR_NEXT = 1, CTR_SUM = 2, CTR_OVF = 3, CTR_CAND = 4, CTR_N = 8 };
+
+struct JoinArgs {
+  // input table R (row-major, width w); R == nullptr with w == 0 seeds from the motif table
+  const int32_t *R;
+  const float *Rs;
+  int64_t N;
+  int32_t w;
+  // the motif side
+  IndexView ix;
+  int32_t key_col[2];
+  int32_t n_chk;
+  int8_t chk_mpos[MAXM];
+  int8_t chk_col[MAXM];
+  int32_t n_new;
+  int8_t new_mpos[MAXM];
+  int32_t n_be;
+  int8_t be_a[MAXBE];
+  int8_t be_b[MAXBE];
+  int32_t wo;                // output width = w + n_new
+  int8_t out_pos[MAXW];      // working column -> position in the written row
+  // data graph
+  const unsigned long long *adj;
+  int32_t adj_words;
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const float *eerr;
+  const float *qerr;
+  int32_t scored;
+  float prune;               // drop rows whose score exceeds this (no pruning: +inf)
+  // output
+  int32_t mode;              // 0 = write rows, 1 = count + checksum
+  int32_t *out;
+  float *outs;
+  int32_t *out_next;         // candidate count of each written row for the next step (nullable)
+  int64_t out_cap;
+  unsigned long long *ctr;   // CTR_* counters
+  IndexView nx;              // next step's index (nkeys < 0: none)
+  int32_t nx_key_col[2];
+  // seed mode (R == nullptr): motif rows [seed_lo, seed_hi) are the candidates
+  int64_t seed_lo, seed_hi;
+};
+
+}  // namespace dmi

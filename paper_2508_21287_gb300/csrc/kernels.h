@@ -1,0 +1,61 @@
+// Launchers of the library's sm_103a kernels (kernels.cu). All take the stream to run on;
+// none synchronises. Sizes are in elements unless the name says bytes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dm_internal.h"
+
+namespace dmk {
+
+constexpr int JOIN_BLK = 256;
+
+// Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
+// + compaction). Returns the dynamic shared memory it needs for the given widths.
+size_t join_smem_bytes(int w, int wo, int tile_rows);
+int join_tile_rows(int w);
+cudaError_t launch_join(const dmi::JoinArgs &a, int grid, int tile_rows, cudaStream_t s);
+int join_grid(const dmi::JoinArgs &a, int tile_rows, int num_sms);
+
+// Data-graph preparation.
+cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, const float *eerr,
+                             int32_t V, int64_t nnz, int32_t *rows, float *score, cudaStream_t s);
+cudaError_t launch_vertex_table(int32_t V, int32_t *rows, float *score, cudaStream_t s);
+cudaError_t launch_bitmap(const int32_t *row_ptr, const int32_t *col_idx, int32_t V, int64_t nnz,
+                          int32_t words, unsigned long long *adj, cudaStream_t s);
+
+// Exclusive scan of n values into out[0..n], out[n] = total. tmp must hold
+// scan_tmp_elems(n) int64 values.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+
+// One stable LSD pass: perm_out = perm_in stably sorted by the 8-bit digit
+// (key >> shift) & 255 of key = keys[perm_in[i] * stride]. hist must hold
+// radix_hist_elems(n) int64, tmp scan_tmp_elems(radix_hist_elems(n)).
+int64_t radix_hist_elems(int64_t n);
+cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm_in,
+                       int32_t *perm_out, int64_t n, int shift, int64_t *hist, int64_t *hist_scan,
+                       int64_t *tmp, cudaStream_t s);
+cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+cudaError_t launch_gather_rows(const int32_t *in, const float *ins, const int32_t *perm, int64_t n,
+                               int32_t w, int32_t *out, float *outs, cudaStream_t s);
+
+// Motif-table indices.
+cudaError_t launch_offsets_direct(const int32_t *rows, int32_t mw, int32_t kpos, int64_t n,
+                                  int32_t V, int32_t *offsets, cudaStream_t s);
+cudaError_t launch_hash_build(const int32_t *rows, int32_t mw, int32_t kp0, int32_t kp1, int64_t n,
+                              dmi::HashSlot *slots, uint32_t log2cap, unsigned long long *ctr,
+                              cudaStream_t s);
+
+// Top-k support: histogram of the 8-bit digit at `shift` of the FP32 score bits, over the
+// scores whose bits agree with `prefix` on `pmask`; and compaction of indices with bits <= T.
+cudaError_t launch_score_hist(const float *sc, int64_t n, uint32_t prefix, uint32_t pmask, int shift,
+                              unsigned long long *hist, cudaStream_t s);
+cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx,
+                             unsigned long long *ctr, cudaStream_t s);
+
+// Sum over rows of the checksum hash H(row) into ctr[CTR_SUM] (count = n).
+cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned long long *ctr, cudaStream_t s);
+
+}  // namespace dmk

@@ -414,3 +414,41 @@ def c2_pattern(seed: int, n_min: int = 10, n_max: int = 30) -> Graph:
     if seed % 2 == 0:
         return random_tree(n, seed)
     return cycle_with_chords(n, seed, n_chords=1 + rng.below(2))
+
+
+def random_subtree(g: Graph, n: int, seed: int) -> Graph:
+    """Random n-vertex tree that is a subgraph of g: a random spanning tree (Kruskal over
+    SplitMix64 edge keys) of the patch ``sub_patch(g, n, seed)``. Always embeddable in g;
+    its maximum degree is at most g's."""
+    patch = sub_patch(g, n, seed)
+    rng = SplitMix64(seed ^ 0x7EEE)
+    es = patch.edges()
+    keys = [rng.next_u64() for _ in es]
+    parent = list(range(n))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    tree = []
+    for _, (u, v) in sorted(zip(keys, es)):
+        a, b = find(u), find(v)
+        if a != b:
+            parent[a] = b
+            tree.append((u, v))
+    t = from_edges(n, tree, name=f"subtree{n}_s{seed}", meta={"kind": "subtree"})
+    return t
+
+
+def layout_query(g: Graph, seed: int, n_min: int = 10, n_max: int = 30) -> Graph:
+    """A layout query that fits the device graph g: even seeds give a random spanning tree of
+    a random device patch, odd seeds the induced patch itself (on heavy-hex it contains the
+    12-cycles of the cells with the paths between them as chords). Size uniform in
+    [n_min, n_max]."""
+    rng = SplitMix64(0x1A70 + seed)
+    n = n_min + rng.below(n_max - n_min + 1)
+    if seed % 2 == 0:
+        return random_subtree(g, n, seed)
+    return sub_patch(g, n, seed)

@@ -1,0 +1,290 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Embedding sets are compared bit-exactly in canonical order (integer work); FP32 layout scores
+within 1e-5 relative of the FP64 oracle (the sum has at most ~150 non-negative terms, so FP32
+recursive summation stays below 150 * 2^-24 ~ 9e-6 relative); top-k by position with the
+tie rule of the library's reading (rows equal except inside the 1e-5 band around the k-th).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_21287_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2508_21287_gb300 import build
+    build.build()
+    from paper_2508_21287_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def _rows_equal(a, b):
+    assert a.shape == b.shape, (a.shape, b.shape)
+    assert np.array_equal(a, b)
+
+
+def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True):
+    plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows)
+    rows, sc, cnt, cs = plan.all()
+    ref = oracle.enumerate(g, p)
+    if chunk_rows:
+        rows = rows[np.lexsort(rows.T[::-1])] if len(rows) else rows
+    _rows_equal(rows, ref.rows)
+    assert cnt == ref.count and cs == ref.checksum
+    c2, cs2 = plan.count()
+    assert c2 == ref.count and cs2 == ref.checksum
+    if scores and g.edge_err is not None and ref.count:
+        want = oracle.scores(g, p, rows)
+        np.testing.assert_allclose(sc, want, rtol=RTOL, atol=0)
+    return ref
+
+
+def check_topk(ctx, gid, g, p, k, **kw):
+    plan = ctx.plan(gid, p, **kw)
+    rows, scores = plan.topk(k)
+    allrows = oracle.enumerate(g, p).rows
+    m = min(k, len(allrows))
+    assert rows.shape == (m, p.n)
+    if m == 0:
+        return
+    s = oracle.scores(g, p, allrows)
+    order = oracle.topk(allrows, s, k)
+    np.testing.assert_allclose(scores, s[order], rtol=RTOL, atol=0)
+    pos = {tuple(r): i for i, r in enumerate(allrows.tolist())}
+    idx = [pos.get(tuple(r)) for r in rows.tolist()]
+    assert None not in idx and len(set(idx)) == m
+    np.testing.assert_allclose(s[idx], scores, rtol=RTOL, atol=0)
+    kth = s[order[-1]]
+    must = {i for i in np.nonzero(s < kth * (1 - RTOL))[0].tolist()}
+    assert must <= set(idx)
+
+
+# ------------------------------------------------------------------ 6x6 grid (tiny) -------
+@pytest.mark.parametrize("motifs", [None, [2], [4, 2], [3], [104], [201], [104, 106], [202, 4]])
+def test_grid6x6_path5_cycle4(ctx, motifs):
+    g = I.grid(6, 6)
+    gid = ctx.load(g)
+    r = check_all(ctx, gid, g, I.path(5), motifs=motifs)
+    assert r.count == 1712
+    r = check_all(ctx, gid, g, I.cycle(4), motifs=motifs)
+    assert r.count == 200
+
+
+def test_grid6x6_brute_force(ctx):
+    g = I.grid(6, 6)
+    gid = ctx.load(g)
+    plan = ctx.plan(gid, I.path(5))
+    rows, _, cnt, _ = plan.all()
+    _rows_equal(rows, oracle.brute_force(g, I.path(5)).rows)
+
+
+# ------------------------------------------------------------------ motif tables ----------
+def _motif_graph(mid):
+    if 2 <= mid <= 16:
+        return I.path(mid)
+    if 103 <= mid <= 116:
+        return I.cycle(mid - 100)
+    if mid == 201:
+        return I.star(3)
+    if mid == 202:
+        return I.grid(2, 3)
+    if mid == 203:
+        edges = [(i, (i + 1) % 12) for i in range(12)] + [(i, 12 + i // 2) for i in range(0, 12, 2)]
+        return I.from_edges(18, edges)
+    raise KeyError(mid)
+
+
+@pytest.mark.parametrize("mid", [2, 3, 4, 5, 7, 103, 104, 106, 112, 201, 202, 203])
+def test_motif_tables(ctx, mid):
+    for g in (I.grid(5, 6), I.heavy_hex(2, 3), I.random_regular3(40, 3)):
+        gid = ctx.load(g)
+        got = ctx.motif_table(gid, mid)
+        want = oracle.enumerate(g, _motif_graph(mid)).rows
+        _rows_equal(got, want)
+
+
+# ------------------------------------------------------------------ heavy-hex ~160 ---------
+@pytest.fixture(scope="module")
+def hh(ctx):
+    g = I.lognormal_weights(I.heavy_hex(4, 6), seed=7, qubits=True)
+    return g, ctx.load(g)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_c2_patterns_all_scores(ctx, hh, seed):
+    g, gid = hh
+    check_all(ctx, gid, g, I.c2_pattern(seed))
+    for n in (10, 20, 30):
+        check_all(ctx, gid, g, I.sub_patch(g, n, seed))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_c2_top100(ctx, hh, seed):
+    g, gid = hh
+    check_topk(ctx, gid, g, I.sub_patch(g, 12 + 3 * seed, seed), 100)
+    check_topk(ctx, gid, g, I.path(8 + seed), 100)
+
+
+def test_topk_more_than_count_and_no_embeddings(ctx, hh, B):
+    g, gid = hh
+    check_topk(ctx, gid, g, I.cycle(12), 1000)      # 576 < k
+    check_topk(ctx, gid, g, I.cycle(8), 10)         # girth 12: none
+    ug = I.heavy_hex(2, 2)
+    ugid = ctx.load(ug)
+    with pytest.raises(B.DMError):
+        ctx.plan(ugid, I.path(4)).topk(5)           # no weights loaded
+
+
+@pytest.mark.parametrize("k", [10, 16, 24, 30])
+def test_heavy_hex_paths(ctx, hh, k):
+    g, gid = hh
+    r = check_all(ctx, gid, g, I.path(k), scores=k <= 16)
+    assert r.count == {10: 3696, 16: 18528, 24: 138648, 30: 548048}.get(k, r.count)
+
+
+# ------------------------------------------------------------------ orders, chunks ---------
+@pytest.mark.parametrize("order", [0, 1])
+def test_orders_agree(ctx, hh, order):
+    g, gid = hh
+    for s in range(4):
+        check_all(ctx, gid, g, I.sub_patch(g, 18, 100 + s), order=order)
+        check_all(ctx, gid, g, I.random_tree(14, s), order=order)
+
+
+@pytest.mark.parametrize("chunk_rows", [64, 1000, 20000])
+def test_chunked_streaming(ctx, hh, chunk_rows):
+    g, gid = hh
+    check_all(ctx, gid, g, I.path(16), chunk_rows=chunk_rows, scores=False)
+    check_all(ctx, gid, g, I.sub_patch(g, 25, 3), chunk_rows=chunk_rows)
+
+
+def test_small_budget_streams(B, hh):
+    g, _ = hh
+    with B.Context(0, mem_budget_bytes=2 << 20) as c:
+        gid = c.load(g)
+        plan = c.plan(gid, I.path(20))
+        cnt, cs = plan.count()
+        ref = oracle.enumerate(g, I.path(20), rows=False)
+        assert cnt == ref.count and cs == ref.checksum
+        rows, _, cnt2, cs2 = plan.all()
+        assert cnt2 == ref.count and cs2 == ref.checksum
+        assert c.stats()["chunks"] > c.stats()["n_steps"]
+
+
+# ------------------------------------------------------------------ larger heavy-hex -------
+@pytest.mark.parametrize("m,n", [(12, 15), (27, 28)])
+def test_scaling_counts(ctx, m, n):
+    g = I.heavy_hex(m, n)
+    gid = ctx.load(g)
+    for p in (I.path(8), I.path(16), I.path(24), I.sub_patch(g, 12, 1), I.sub_patch(g, 25, 2), I.sub_patch(g, 40, 3)):
+        plan = ctx.plan(gid, p)
+        cnt, cs = plan.count()
+        ref = oracle.enumerate(g, p, rows=False, threads=8)
+        assert cnt == ref.count and cs == ref.checksum
+
+
+def test_largest_heavy_hex_p24(ctx):
+    g = I.heavy_hex(53, 59)
+    gid = ctx.load(g)
+    plan = ctx.plan(gid, I.path(24))
+    cnt, cs = plan.count()
+    ref = oracle.enumerate(g, I.path(24), rows=False, threads=16)
+    assert cnt == ref.count and cs == ref.checksum
+
+
+# ------------------------------------------------------------------ other graphs -----------
+def _er(n, p1000, seed):
+    rng = I.SplitMix64(seed)
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.below(1000) < p1000]
+    edges += [(i, i + 1) for i in range(n - 1)]  # keep it connected
+    return I.from_edges(n, edges)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dense_random_graphs(ctx, seed):
+    g = _er(12, 350, seed)
+    gid = ctx.load(g)
+    pats = [I.complete(3), I.complete(4), I.cycle(5), I.random_tree(6, seed), I.cycle_with_chords(6, seed)]
+    for p in pats:
+        for motifs in (None, [2], [103], [4], [104, 3]):
+            check_all(ctx, gid, g, p, motifs=motifs)
+
+
+def test_regular3_and_grid32(ctx):
+    g = I.random_regular3(256, 5)
+    gid = ctx.load(g)
+    for p in (I.path(7), I.cycle(6), I.random_tree(9, 2)):
+        check_all(ctx, gid, g, p, scores=False)
+    g = I.grid(12, 12)
+    gid = ctx.load(g)
+    for p in (I.path(7), I.cycle(8), I.subdivided_grid(2, 2), I.grid(2, 3)):
+        check_all(ctx, gid, g, p, scores=False)
+
+
+def test_relabelled_data_graph(ctx):
+    g = I.heavy_hex(3, 3)
+    rng = I.SplitMix64(9)
+    perm = list(range(g.n))
+    rng.shuffle(perm)
+    h = I.relabel(g, perm)
+    p = I.sub_patch(g, 15, 4)
+    a = ctx.plan(ctx.load(g), p).all()[0]
+    b = ctx.plan(ctx.load(h), p).all()[0]
+    mapped = np.asarray(perm, dtype=np.int32)[a]
+    mapped = mapped[np.lexsort(mapped.T[::-1])]
+    _rows_equal(mapped, b)
+
+
+# ------------------------------------------------------------------ edge cases -------------
+def test_edge_cases(ctx, B):
+    g = I.lognormal_weights(I.grid(4, 4), seed=1)
+    gid = ctx.load(g)
+    one = I.from_edges(1, [])
+    check_all(ctx, gid, g, one)                                   # every vertex
+    check_all(ctx, gid, g, I.path(2))                              # = 2|E|
+    assert check_all(ctx, gid, g, I.path(17)).count == 0          # larger than the graph
+    assert check_all(ctx, gid, g, I.complete(3)).count == 0       # no triangles in a grid
+    two = I.from_edges(4, [(0, 1), (2, 3)])
+    with pytest.raises(B.DMError) as e:
+        ctx.plan(gid, two)
+    assert e.value.code == B.DM_E_DISCONNECTED
+    with pytest.raises(B.DMError) as e:
+        B.dm_load_data_graph(ctx.h, 3, [0, 1, 2, 2], [1, 0], None, None)  # 0-1 plus isolated 2
+    assert e.value.code == B.DM_E_DISCONNECTED
+    with pytest.raises(B.DMError) as e:
+        B.dm_load_data_graph(ctx.h, 2, [0, 1, 1], [1], None, None)        # asymmetric
+    assert e.value.code == B.DM_E_INVAL
+    with pytest.raises(B.DMError) as e:
+        B.dm_load_data_graph(ctx.h, 2, [0, 2, 3], [1, 1, 0], None, None)  # duplicate edge
+    assert e.value.code == B.DM_E_INVAL
+    # self-loops are dropped on load (Res(M2) excludes them)
+    sl = B.dm_load_data_graph(ctx.h, 3, [0, 2, 5, 6], [0, 1, 0, 1, 2, 1], None, None)
+    assert ctx.motif_table(sl, 2).tolist() == [[0, 1], [1, 0], [1, 2], [2, 1]]
+
+
+def test_capacity_cap(ctx, B, hh):
+    g, gid = hh
+    plan = ctx.plan(gid, I.path(20), max_rows=1000)
+    with pytest.raises(B.DMError) as e:
+        plan.count()
+    assert e.value.code == B.DM_E_CAPACITY
+
+
+def test_callback_cancel(ctx, B, hh):
+    g, gid = hh
+    plan = ctx.plan(gid, I.path(6))
+    with pytest.raises(B.DMError) as e:
+        B.dm_match(ctx.h, plan.h, B.DM_ALL, lambda r, s: 1)
+    assert e.value.code == B.DM_E_CANCELLED
