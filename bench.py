@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the Delta-Motif GB300 library (one JSON line on rank 0).
+
+Workload (layout selection on a ~160-qubit heavy-hex device): data graph = heavy-hex 4 x 6
+(159 vertices, 182 edges) with log-normal(-5, 0.5) FP32 edge errors; one step = a batch of
+layout queries (10-30 vertices, max degree 3; even seeds a random spanning tree of a random
+device patch, odd seeds the induced patch with its cell cycles), each planned (motif
+decomposition) and matched: every embedding in canonical order with its FP32 layout score,
+plus the top-100 layouts. Embeddings stay on the device for `value`; `e2e` repeats the step
+through the same C ABI with every embedding copied to host memory.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the library's
+stream, with a 256 MiB write between steps to flush L2 (outside the events). Under torchrun
+each rank runs its own batch (replicas, weak scaling; no collective on the data path) and the
+maximum time over ranks is reported.
+
+--impl reference times the CPU oracle (plain backtracking, FP64 scores, top-100) on the same
+workload on the host cores, a bounded number of passes over the batch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "embeddings/sec"
+UNIT = "embeddings/s"
+K_TOP = 100
+BATCH = 32
+WORKLOAD = "C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 10-30 vertices, all embeddings + FP32 scores + top-100"
+
+# Per-launch DRAM traffic of k_join from the ncu capture summarised in profiles/ (None when the
+# kernel changed after the capture).
+JOIN_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
+    ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
+    return ap.parse_args()
+
+
+WORKLOAD_C3 = ("C3 scaling: heavy-hex {m}x{n} (V={V}), seeded paths of 8-24 vertices and sub-patches of 12-40 "
+               "vertices, count + 64-bit checksum")
+
+
+def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: int = 0):
+    from paper_2508_21287_gb300 import inputs as I
+    if kind == "c2":
+        g = I.lognormal_weights(I.heavy_hex(4, 6), seed=7)
+        pats = [I.layout_query(g, rank * batch + i) for i in range(batch)]
+        return g, pats
+    g = I.heavy_hex(*hh)
+    if only_path:
+        return g, [I.path(only_path)]
+    rng = I.SplitMix64(0xC3 + rank)
+    pats = []
+    for i in range(batch):
+        if i % 2 == 0:
+            pats.append(I.path(8 + rng.below(17)))
+        else:
+            pats.append(I.sub_patch(g, 12 + rng.below(29), rank * batch + i))
+    return g, pats
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.th = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        mx = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[4 + i] and "Not" not in s[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(g, pats, budget_s: float = 12.0, count_only: bool = False):
+    """The oracle as it stands, on the host cores, over whole passes of the batch."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    passes, emb = 0, 0
+    while True:
+        for p in pats:
+            r = oracle.enumerate(g, p, threads=threads, rows=not count_only)
+            if r.count and not count_only:
+                s = oracle.scores(g, p, r.rows)
+                oracle.topk(r.rows, s, K_TOP)
+            emb += r.count
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or passes >= 50:
+            break
+    return {"value": emb / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{passes} pass(es) over the {len(pats)}-query batch ({emb} embeddings, {el:.1f} s): "
+                      + ("backtracking, count + checksum" if count_only else
+                         "backtracking + FP64 scores + top-100 per query")}
+
+
+def wl_name(args):
+    if args.workload == "c2":
+        return WORKLOAD
+    m, n = (int(x) for x in args.hh.split(","))
+    return WORKLOAD_C3.format(m=m, n=n, V=5 * m * n + 4 * m + 4 * n - 1)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, pats = workload(0, args.batch, args.workload, tuple(int(x) for x in args.hh.split(",")))
+    import oracle
+    oracle.build()
+    cb = cpu_baseline(g, pats, budget_s=max(5.0, 3.0 * (args.steps + args.warmup)), count_only=args.workload == "c3")
+    line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl_name(args), "parallelism": "host cores"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2508_21287_gb300 import build
+    build.build()
+    from paper_2508_21287_gb300 import binding as B
+
+    hh = tuple(int(x) for x in args.hh.split(","))
+    g, pats = workload(rank, args.batch, args.workload, hh, args.only_path)
+    count_mode = args.workload == "c3"
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    B.dm_set_stream(ctx.h, stream)
+    gid = ctx.load(g)
+    B.dm_enable_timing(ctx.h, True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0}
+
+    def step(host_rows: bool, record: bool):
+        emb = 0
+        for p in pats:
+            plan = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
+            if count_mode:
+                cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
+            elif host_rows:
+                sink = []
+                _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL, lambda r, s: sink.append((r, s)) and 0,
+                                               K_TOP, p.n)
+                if record:
+                    acc["d2h"] += sum(r.nbytes + (0 if s is None else s.nbytes) for r, s in sink)
+            else:
+                _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL | B.DM_DEVICE_ROWS, lambda *a: 0, K_TOP, p.n)
+            st = B.dm_get_stats(ctx.h)
+            B.dm_plan_free(plan)
+            if record:
+                acc["join_ms"] += st["join_ms"]
+                acc["join_bytes"] += st["join_bytes"]
+                acc["join_launches"] += st["join_launches"]
+                acc["launches"] += st["kernel_launches"]
+            emb += cnt
+        return emb
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False, False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            acc["emb"] += step(False, True)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    emb_total = acc["emb"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([emb_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        ms, emb_total = float(t.item()), float(e.item())
+    value = emb_total / (ms / 1e3)
+    clocks = clk.summary()
+
+    e2e = None
+    if not args.no_e2e and not count_mode:
+        h2d = sum(p.row_ptr.nbytes + p.col_idx.nbytes for p in pats)
+        acc2 = acc["d2h"]
+        barrier()
+        t0 = time.perf_counter()
+        emb2 = 0
+        for _ in range(args.steps):
+            emb2 += step(True, True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        d2h = (acc["d2h"] - acc2) // max(1, args.steps)
+        e2e = {"value": emb2 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = acc["join_bytes"] / (acc["join_ms"] / 1e3) / 1e9 if acc["join_ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_join", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": JOIN_TRAFFIC_BYTES_PER_LAUNCH,
+                "algorithmic_bytes_per_launch": acc["join_bytes"] / max(1, acc["join_launches"]),
+                "avg_launch_us": 1e3 * acc["join_ms"] / max(1, acc["join_launches"]),
+                "launches": acc["join_launches"]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl_name(args), "queries_per_step": len(pats), "embeddings_per_step": emb_total / args.steps / world,
+                       "data_graph": f"heavy-hex {'4x6' if not count_mode else args.hh.replace(',', 'x')}", "motifs": "M4,M2",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": acc["launches"], "clocks": clocks, "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g, pats, count_only=count_mode)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

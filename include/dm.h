@@ -174,6 +174,13 @@ int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, 
 int dm_score_topk(dm_ctx *ctx, const dm_plan_t *plan, int32_t k, int32_t *out_rows,
                   float *out_scores, int32_t *out_n);
 
+/* DM_ALL and top-k from one pass of the joins: every embedding goes through cb exactly as
+ * in dm_match, and the k best (score, row) rows are written to out_rows / out_scores as in
+ * dm_score_topk. Needs edge weights. */
+int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void *user,
+                  int32_t k, int32_t *out_rows, float *out_scores, int32_t *out_n,
+                  uint64_t *out_count, uint64_t *out_checksum);
+
 /* ------------------------------------------------------------------ statistics ------ */
 #define DM_MAX_STEPS 128
 typedef struct dm_stats {
@@ -186,6 +193,7 @@ typedef struct dm_stats {
     int64_t join_launches;
     double join_bytes;                /* algorithmic bytes of the join launches */
     double total_ms;                  /* host wall time of the call */
+    int64_t kernel_launches;          /* launches of the library's own kernels during the call */
 } dm_stats;
 
 /* Statistics of the last dm_match / dm_score_topk on this context. Device timings are

@@ -53,7 +53,7 @@ class dm_stats(ctypes.Structure):
                 ("candidates", ctypes.c_int64 * DM_MAX_STEPS), ("chunks", ctypes.c_int64),
                 ("max_rows", ctypes.c_int64), ("join_ms", ctypes.c_double),
                 ("join_launches", ctypes.c_int64), ("join_bytes", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
 
 DM_CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
@@ -82,6 +82,7 @@ _SIGS = {
     "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
     "dm_match_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _u64p, _u64p]),
     "dm_score_topk": (ctypes.c_int, [_vp, _vp, _i32, _i32p, _fp, _i32p]),
+    "dm_match_topk": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _i32, _i32p, _fp, _i32p, _u64p, _u64p]),
     "dm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dm_stats)]),
     "dm_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -217,12 +218,7 @@ def dm_decompose(n_p: int, row_ptr, col_idx, motifs, order: int = DM_ORDER_PAPER
     return _parse_description(buf.tolist())
 
 
-def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):
-    """Run the plan. cb(rows ndarray [m, n] int32, scores ndarray [m] or None) receives host
-    copies (DM_ALL); with DM_DEVICE_ROWS in mode it receives (rows_ptr, scores_ptr, m, n) raw
-    device pointers instead. Returns (count, checksum)."""
-    err = []
-
+def _make_cb(cb, mode, err):
     def _tramp(user, rows, scores, nrows, ncols):
         try:
             if mode & DM_DEVICE_ROWS:
@@ -236,8 +232,31 @@ def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):
         except BaseException as e:  # noqa: BLE001 - re-raised after the C call returns
             err.append(e)
             return 1
+    return DM_CHUNK_CB(_tramp) if cb is not None else DM_CHUNK_CB()
 
-    c_cb = DM_CHUNK_CB(_tramp) if cb is not None else DM_CHUNK_CB()
+
+def dm_match_topk(ctx, plan, mode: int, cb, k: int, n_p: int):
+    """All rows through cb (as dm_match) plus the top-k; returns (rows, scores, count, checksum)."""
+    err = []
+    c_cb = _make_cb(cb, mode, err)
+    rows = np.zeros((k, n_p), dtype=np.int32)
+    scores = np.zeros(k, dtype=np.float32)
+    n = _i32()
+    cnt, cs = _u64(), _u64()
+    rc = _lib.dm_match_topk(ctx, plan, int(mode), c_cb, None, int(k), _p32(rows), scores.ctypes.data_as(_fp),
+                            ctypes.byref(n), ctypes.byref(cnt), ctypes.byref(cs))
+    if err:
+        raise err[0]
+    _check(rc, "dm_match_topk", ctx)
+    return rows[:n.value], scores[:n.value], cnt.value, cs.value
+
+
+def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):
+    """Run the plan. cb(rows ndarray [m, n] int32, scores ndarray [m] or None) receives host
+    copies (DM_ALL); with DM_DEVICE_ROWS in mode it receives (rows_ptr, scores_ptr, m, n) raw
+    device pointers instead. Returns (count, checksum)."""
+    err = []
+    c_cb = _make_cb(cb, mode, err)
     cnt, cs = _u64(), _u64()
     rc = _lib.dm_match(ctx, plan, int(mode), c_cb, None, ctypes.byref(cnt), ctypes.byref(cs))
     if err:
@@ -271,7 +290,8 @@ def dm_get_stats(ctx) -> dict:
     n = s.n_steps
     return {"n_steps": n, "rows": list(s.rows[:n]), "candidates": list(s.candidates[:n]),
             "chunks": s.chunks, "max_rows": s.max_rows, "join_ms": s.join_ms,
-            "join_launches": s.join_launches, "join_bytes": s.join_bytes, "total_ms": s.total_ms}
+            "join_launches": s.join_launches, "join_bytes": s.join_bytes, "total_ms": s.total_ms,
+            "kernel_launches": s.kernel_launches}
 
 
 def dm_enable_timing(ctx, on: bool = True) -> None:

@@ -649,7 +649,11 @@ int deliver(dm_ctx *c, const DevTable &t, int flags, dm_chunk_cb cb, void *user)
   return DM_OK;
 }
 
+struct TopkSink;
+int topk_take(dm_ctx *c, TopkSink *t, DevTable tab);
+
 struct AllSink : Sink {
+  TopkSink *tap = nullptr;  // also feeds every final chunk to a top-k accumulator
   int flags;
   dm_chunk_cb cb;
   void *user;
@@ -666,6 +670,7 @@ struct AllSink : Sink {
     count += (uint64_t)t.n;
     checksum += c->h_ctr[CTR_SUM];
     int r = deliver(c, t, flags, cb, user);
+    if (r == DM_OK && tap) return topk_take(c, tap, t);  // the tap takes ownership
     free_table(c, t);
     return r;
   }
@@ -778,6 +783,8 @@ struct TopkSink : Sink {
   }
 };
 
+int topk_take(dm_ctx *c, TopkSink *t, DevTable tab) { return t->take(c, tab); }
+
 int ensure_motif(dm_ctx *c, DevGraph *g, int id);
 
 int build_motif_by_joins(dm_ctx *c, DevGraph *g, const MotifDef &md) {
@@ -854,7 +861,14 @@ DevGraph *get_graph(dm_ctx *c, dm_graph g) {
   return c->graphs[g];
 }
 
-void reset_stats(dm_ctx *c) { memset(&c->stats, 0, sizeof(c->stats)); }
+void reset_stats(dm_ctx *c) {
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->stats.kernel_launches = -dmk::launch_count();
+}
+void finish_stats(dm_ctx *c, std::chrono::steady_clock::time_point t0) {
+  c->stats.kernel_launches += dmk::launch_count();
+  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
 
 }  // namespace
 
@@ -1166,7 +1180,7 @@ int dm_match(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *use
   }
   for (auto &h : sink.held) free_table(c, h);
   cudaStreamSynchronize(c->stream);
-  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  finish_stats(c, t0);
   if (r != DM_OK) return r;
   if (out_count) *out_count = cnt;
   if (out_checksum) *out_checksum = cs;
@@ -1220,7 +1234,55 @@ int dm_score_topk(dm_ctx *c, const dm_plan_t *pl, int32_t k, int32_t *out_rows, 
   }
   if (sink.have) free_table(c, sink.best);
   cudaStreamSynchronize(c->stream);
-  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  finish_stats(c, t0);
+  return r;
+}
+
+int dm_match_topk(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *user, int32_t k, int32_t *out_rows,
+                  float *out_scores, int32_t *out_n, uint64_t *out_count, uint64_t *out_checksum) {
+  if (!c || !pl || k < 1 || !out_rows || !out_n || (mode & 0xF) != DM_ALL) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  if (!g->eerr) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &pl->p;
+  ex.mode = DM_ALL;
+  ex.use_qerr = true;
+  ex.chunk_rows = pl->p.chunk_rows;
+  ex.max_rows = pl->p.max_rows;
+  c->inflight = 0;
+  TopkSink tk;
+  tk.g = g;
+  tk.k = k;
+  AllSink sink;
+  sink.flags = mode;
+  sink.cb = cb;
+  sink.user = user;
+  sink.bits = graph_bits(g);
+  sink.tap = &tk;
+  ex.sink = &sink;
+  int r = ex.run();
+  if (r == DM_OK) r = sink.finish(c, pl->p.n_p, true);
+  for (auto &h : sink.held) free_table(c, h);
+  if (r == DM_OK) {
+    int64_t m = tk.have ? tk.best.n : 0;
+    if (m > 0) {
+      CK(cudaMemcpyAsync(out_rows, tk.best.rows, sizeof(int32_t) * m * tk.best.w, cudaMemcpyDeviceToHost, c->stream));
+      if (out_scores) CK(cudaMemcpyAsync(out_scores, tk.best.score, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *out_n = (int32_t)m;
+    if (out_count) *out_count = sink.count;
+    if (out_checksum) *out_checksum = sink.checksum;
+  }
+  if (tk.have) free_table(c, tk.best);
+  cudaStreamSynchronize(c->stream);
+  finish_stats(c, t0);
   return r;
 }
 

@@ -23,11 +23,16 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "kernels.h"
 
 using namespace dmi;
 
 namespace dmk {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launch_count() { return g_launches.load(); }
 
 #define FULL_MASK 0xffffffffu
 
@@ -349,6 +354,7 @@ cudaError_t launch_join(const JoinArgs &a, int grid, int tile_rows, cudaStream_t
     g_join_attr_set = true;
   }
   if (grid < 1) grid = 1;
+  g_launches++;
   k_join<JOIN_BLK><<<grid, JOIN_BLK, smem, s>>>(a, tile_rows);
   return cudaGetLastError();
 }
@@ -393,6 +399,7 @@ cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, con
                              int64_t nnz, int32_t *rows, float *score, cudaStream_t s) {
   if (nnz == 0) return cudaSuccess;
   int grid = (int)imin64((nnz + 255) / 256, 4096);
+  g_launches++;
   k_csr_to_m2<<<grid, 256, 0, s>>>(row_ptr, col_idx, eerr, V, nnz, rows, score);
   return cudaGetLastError();
 }
@@ -406,6 +413,7 @@ __global__ void k_vertex_table(int32_t V, int32_t *rows, float *score) {
 
 cudaError_t launch_vertex_table(int32_t V, int32_t *rows, float *score, cudaStream_t s) {
   if (V == 0) return cudaSuccess;
+  g_launches++;
   k_vertex_table<<<(V + 255) / 256, 256, 0, s>>>(V, rows, score);
   return cudaGetLastError();
 }
@@ -422,6 +430,7 @@ cudaError_t launch_bitmap(const int32_t *row_ptr, const int32_t *col_idx, int32_
                           unsigned long long *adj, cudaStream_t s) {
   if (nnz == 0) return cudaSuccess;
   int grid = (int)imin64((nnz + 255) / 256, 4096);
+  g_launches++;
   k_bitmap<<<grid, 256, 0, s>>>(row_ptr, col_idx, V, nnz, words, adj);
   return cudaGetLastError();
 }
@@ -495,13 +504,16 @@ static cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp,
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
+    g_launches++;
     k_scan_tile<T><<<1, SCAN_BLK, 0, s>>>(in, out, n, nullptr);
     return cudaGetLastError();
   }
   int64_t *sums = tmp, *sums_scan = tmp + nb, *rest = tmp + 2 * nb + 1;
+  g_launches++;
   k_scan_tile<T><<<(unsigned)nb, SCAN_BLK, 0, s>>>(in, out, n, sums);
   cudaError_t e = scan_impl<int64_t>(sums, sums_scan, nb, rest, s);
   if (e != cudaSuccess) return e;
+  g_launches++;
   k_scan_add<<<(unsigned)nb, SCAN_BLK, 0, s>>>(out, n, sums_scan, nb);
   return cudaGetLastError();
 }
@@ -580,9 +592,11 @@ cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm
                        int64_t n, int shift, int64_t *hist, int64_t *hist_scan, int64_t *tmp, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+  g_launches++;
   k_radix_hist<<<nb, RS_BLK, 0, s>>>(keys, stride, perm_in, n, shift, hist, nb);
   cudaError_t e = scan_i64(hist, hist_scan, (int64_t)256 * nb, tmp, s);
   if (e != cudaSuccess) return e;
+  g_launches++;
   k_radix_scatter<<<nb, RS_BLK, 0, s>>>(keys, stride, perm_in, n, shift, hist_scan, nb, perm_out);
   return cudaGetLastError();
 }
@@ -594,6 +608,7 @@ __global__ void k_iota(int32_t *p, int64_t n) {
 
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  g_launches++;
   k_iota<<<(int)imin64((n + 255) / 256, 8192), 256, 0, s>>>(p, n);
   return cudaGetLastError();
 }
@@ -614,6 +629,7 @@ cudaError_t launch_gather_rows(const int32_t *in, const float *ins, const int32_
                                int32_t *out, float *outs, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int64_t ne = n * w;
+  g_launches++;
   k_gather_rows<<<(int)imin64((ne + 255) / 256, 16384), 256, 0, s>>>(in, ins, perm, n, w, out, outs);
   return cudaGetLastError();
 }
@@ -634,6 +650,7 @@ __global__ void k_offsets_direct(const int32_t *rows, int32_t mw, int32_t kpos, 
 
 cudaError_t launch_offsets_direct(const int32_t *rows, int32_t mw, int32_t kpos, int64_t n, int32_t V,
                                   int32_t *offsets, cudaStream_t s) {
+  g_launches++;
   k_offsets_direct<<<(V + 256) / 256, 256, 0, s>>>(rows, mw, kpos, n, V, offsets);
   return cudaGetLastError();
 }
@@ -667,6 +684,7 @@ __global__ void k_hash_build(const int32_t *rows, int32_t mw, int32_t kp0, int32
 cudaError_t launch_hash_build(const int32_t *rows, int32_t mw, int32_t kp0, int32_t kp1, int64_t n,
                               HashSlot *slots, uint32_t log2cap, unsigned long long *ctr, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  g_launches++;
   k_hash_build<<<(int)imin64((n + 255) / 256, 8192), 256, 0, s>>>(rows, mw, kp0, kp1, n, slots, log2cap, ctr);
   return cudaGetLastError();
 }
@@ -688,6 +706,7 @@ __global__ void k_score_hist(const float *sc, int64_t n, uint32_t prefix, uint32
 cudaError_t launch_score_hist(const float *sc, int64_t n, uint32_t prefix, uint32_t pmask, int shift,
                               unsigned long long *hist, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  g_launches++;
   k_score_hist<<<(int)imin64((n + 255) / 256, 2048), 256, 0, s>>>(sc, n, prefix, pmask, shift, hist);
   return cudaGetLastError();
 }
@@ -702,6 +721,7 @@ __global__ void k_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out
 cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx, unsigned long long *ctr,
                              cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  g_launches++;
   k_select_le<<<(int)imin64((n + 255) / 256, 4096), 256, 0, s>>>(sc, n, T, out_idx, ctr);
   return cudaGetLastError();
 }
@@ -722,6 +742,7 @@ __global__ void k_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned 
 
 cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned long long *ctr, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  g_launches++;
   k_hash_rows<<<(int)imin64((n + 255) / 256, 2048), 256, 0, s>>>(rows, n, w, ctr);
   return cudaGetLastError();
 }

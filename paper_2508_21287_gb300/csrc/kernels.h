@@ -10,6 +10,9 @@ namespace dmk {
 
 constexpr int JOIN_BLK = 256;
 
+// Number of kernels launched by this library in the process so far.
+int64_t launch_count();
+
 // Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
 // + compaction). Returns the dynamic shared memory it needs for the given widths.
 size_t join_smem_bytes(int w, int wo, int tile_rows);

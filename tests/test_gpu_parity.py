@@ -137,6 +137,26 @@ def test_c2_top100(ctx, hh, seed):
     check_topk(ctx, gid, g, I.path(8 + seed), 100)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_match_topk_one_pass(ctx, hh, B, seed):
+    g, gid = hh
+    p = I.layout_query(g, seed)
+    plan = ctx.plan(gid, p)
+    got = []
+    rows_k, sc_k, cnt, cs = B.dm_match_topk(ctx.h, plan.h, B.DM_ALL, lambda r, s: got.append((r, s)) and 0, 100, p.n)
+    ref = oracle.enumerate(g, p)
+    rows = np.concatenate([r for r, _ in got])
+    scores = np.concatenate([s for _, s in got])
+    _rows_equal(rows, ref.rows)
+    assert cnt == ref.count and cs == ref.checksum
+    s = oracle.scores(g, p, ref.rows)
+    np.testing.assert_allclose(scores, s, rtol=RTOL, atol=0)
+    order = oracle.topk(ref.rows, s, 100)
+    np.testing.assert_allclose(sc_k, s[order], rtol=RTOL, atol=0)
+    st = B.dm_get_stats(ctx.h)
+    assert st["kernel_launches"] > 0 and st["join_launches"] == st["chunks"]
+
+
 def test_topk_more_than_count_and_no_embeddings(ctx, hh, B):
     g, gid = hh
     check_topk(ctx, gid, g, I.cycle(12), 1000)      # 576 < k
