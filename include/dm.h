@@ -181,6 +181,28 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
                   int32_t k, int32_t *out_rows, float *out_scores, int32_t *out_n,
                   uint64_t *out_count, uint64_t *out_checksum);
 
+/* ------------------------------------------------------------------ no-allocation sort */
+/* No counterpart in the paper: a library service for callers that cannot allocate device
+ * memory when they need it (cudaMalloc/cudaFree synchronise the device, which a latency-bound
+ * serving thread cannot afford; a framework's caching allocator may hold nearly all device
+ * memory; some callers are only handed pre-reserved buffers).
+ *
+ * Sorts n rows of w int32 ids (row-major, device memory) into ascending lexicographic order
+ * (column 0 most significant), writing rows_out (n x w, device) and, when scores_in is not
+ * NULL, the scores carried along to scores_out (n floats, device). Every id must be below
+ * 2^bits (1 <= bits <= 31). Inputs and outputs are caller-owned and must not overlap.
+ * The temporaries live in one fixed device array of the library (about 10.5 MB, held by
+ * every GPU that loads the library until exit); nothing is allocated or freed.
+ * Limits: n <= DM_SORT_STATIC_MAX_ROWS (else DM_E_CAPACITY), 1 <= w <= 64 (else DM_E_INVAL).
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream) and the call
+ * returns without waiting. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. All calls share the one array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and corrupt each other's results; serialise them. */
+#define DM_SORT_STATIC_MAX_ROWS (1 << 20)
+int dm_sort_rows_static(const int32_t *rows_in, const float *scores_in, int64_t n, int32_t w,
+                        int32_t bits, int32_t *rows_out, float *scores_out, void *stream);
+
 /* ------------------------------------------------------------------ statistics ------ */
 #define DM_MAX_STEPS 128
 typedef struct dm_stats {

@@ -88,6 +88,7 @@ _SIGS = {
     "dm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dm_last_error": (ctypes.c_char_p, [_vp]),
     "dm_decompose": (_i32, [_i32, _i32p, _i32p, _i32p, _i32, _i32, _i32p, _i32]),
+    "dm_sort_rows_static": (ctypes.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -292,6 +293,21 @@ def dm_get_stats(ctx) -> dict:
             "chunks": s.chunks, "max_rows": s.max_rows, "join_ms": s.join_ms,
             "join_launches": s.join_launches, "join_bytes": s.join_bytes, "total_ms": s.total_ms,
             "kernel_launches": s.kernel_launches}
+
+
+DM_SORT_STATIC_MAX_ROWS = 1 << 20
+
+
+def dm_sort_rows_static(rows_in_ptr: int, scores_in_ptr, n: int, w: int, bits: int, rows_out_ptr: int,
+                        scores_out_ptr, stream=None) -> None:
+    """Sort n x w device rows into rows_out without allocating (raw device pointers, e.g.
+    torch's data_ptr()); work is enqueued on `stream` and not waited for. For callers that
+    cannot allocate device memory at that point (see include/dm.h)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = _lib.dm_sort_rows_static(_vp(rows_in_ptr), _vp(scores_in_ptr) if scores_in_ptr else None, int(n), int(w),
+                                  int(bits), _vp(rows_out_ptr), _vp(scores_out_ptr) if scores_out_ptr else None,
+                                  _vp(raw) if raw else None)
+    _check(rc, "dm_sort_rows_static")
 
 
 def dm_enable_timing(ctx, on: bool = True) -> None:
