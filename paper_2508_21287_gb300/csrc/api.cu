@@ -26,6 +26,7 @@ struct DevTable {
   float *score = nullptr;
   int64_t n = 0;
   int32_t w = 0;
+  bool borrowed = false;  // lives in the context's arena: never freed by its holder
 };
 
 struct Index {
@@ -68,6 +69,11 @@ struct dm_ctx {
   std::string last_error;
   void *h_stage = nullptr;
   size_t h_stage_bytes = 0;
+  // arena of the device-driven path: two halves alternate as the input and output of a step
+  unsigned char *arena = nullptr;
+  size_t arena_bytes = 0;
+  unsigned long long *d_ctr_steps = nullptr;  // CTR_N counters per step
+  unsigned long long *h_ctr_steps = nullptr;
 };
 
 struct dm_plan_s {
@@ -115,8 +121,10 @@ void dfree(dm_ctx *c, void *p) {
   if (p) cudaFreeAsync(p, c->stream);
 }
 void free_table(dm_ctx *c, DevTable &t) {
-  dfree(c, t.rows);
-  dfree(c, t.score);
+  if (!t.borrowed) {
+    dfree(c, t.rows);
+    dfree(c, t.score);
+  }
   t.rows = nullptr;
   t.score = nullptr;
   t.n = 0;
@@ -249,14 +257,26 @@ int gather_table(dm_ctx *c, const DevTable &t, const int32_t *perm, int64_t n, D
 
 // Replace t by its rows in canonical (lexicographic) order.
 int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
-  if (t.n <= 1) return DM_OK;
-  std::vector<int> cols(t.w);
-  for (int i = 0; i < t.w; i++) cols[i] = i;
+  (void)bits;
+  if (t.n <= 1) {
+    if (t.borrowed && t.n == 1) {  // take a private copy so the holder may free it
+      DevTable o;
+      int32_t *one = nullptr;
+      RET(dalloc_t(c, &one, 1));
+      CK(dmk::launch_iota(one, 1, c->stream));
+      RET(gather_table(c, t, one, 1, &o));
+      dfree(c, one);
+      t = o;
+    }
+    return DM_OK;
+  }
+  void *tmp = nullptr;
+  RET(dalloc(c, &tmp, (size_t)dmk::msort_tmp_bytes(t.n)));
   int32_t *perm = nullptr;
-  RET(sort_perm_by_columns(c, t, cols, bits, &perm));
+  CK(dmk::msort_rows(t.rows, t.n, t.w, tmp, &perm, c->stream));
   DevTable o;
   RET(gather_table(c, t, perm, t.n, &o));
-  dfree(c, perm);
+  dfree(c, tmp);
   free_table(c, t);
   t = o;
   return DM_OK;
@@ -403,7 +423,9 @@ struct Exec {
       }
       a.w = s.w_in;
       a.wo = s.w_out;
-      for (int cc = 0; cc < a.wo; cc++) a.out_pos[cc] = (int8_t)(j == S - 1 ? p->col_vertex[cc] : cc);
+      for (int cc = 0; cc < a.wo; cc++) a.src_col[cc] = (int8_t)cc;
+      if (j == S - 1)  // the last step writes rows in pattern-vertex order
+        for (int cc = 0; cc < a.wo; cc++) a.src_col[p->col_vertex[cc]] = (int8_t)cc;
       a.adj = g->adj;
       a.adj_words = g->adj_words;
       a.row_ptr = g->row_ptr;
@@ -581,10 +603,128 @@ struct Exec {
     return DM_OK;
   }
 
+  // Device-driven execution: every step's output goes to one half of the arena, each launch
+  // reads its input row count from the previous launch's counters, and the host waits once
+  // at the end. *fits is false when some step overflowed its half (nothing is delivered then).
+  int run_fast(bool *fits) {
+    const int S = (int)st.size();
+    *fits = false;
+    size_t half = (c->arena_bytes / 2) / 256 * 256;
+    unsigned char *buf[2] = {c->arena, c->arena + half};
+    CK(cudaMemsetAsync(c->d_ctr_steps, 0, sizeof(unsigned long long) * CTR_N * S, c->stream));
+    if (c->timing) CK(cudaEventRecord(c->ev0, c->stream));
+    int32_t *prev_rows = nullptr;
+    float *prev_score = nullptr;
+    int64_t prev_cap = 0;
+    for (int j = 0; j < S; j++) {
+      JoinArgs a = st[j].base;
+      a.prune = prune;
+      a.ctr = c->d_ctr_steps + (size_t)j * CTR_N;
+      a.out_next = nullptr;
+      a.nx.nkeys = -1;
+      int64_t rb = 4ll * a.wo + (a.scored ? 4 : 0);
+      int64_t cap = std::max<int64_t>(1, ((int64_t)half - 512) / rb);
+      int32_t *orows = (int32_t *)buf[j & 1];
+      float *oscore = (float *)(buf[j & 1] + ((size_t)cap * a.wo * 4 + 255) / 256 * 256);
+      a.out = a.mode == 0 ? orows : nullptr;
+      a.outs = (a.mode == 0 && a.scored) ? oscore : nullptr;
+      a.out_cap = cap;
+      if (j == 0) {
+        a.R = nullptr;
+        a.seed_lo = 0;
+        a.seed_hi = st[0].seed_table->n;
+      } else {
+        a.R = prev_rows;
+        a.Rs = prev_score;
+        a.N = 0;
+        a.n_dev = c->d_ctr_steps + (size_t)(j - 1) * CTR_N + CTR_ROWS;
+        a.in_cap = prev_cap;
+      }
+      int grid = dmk::join_grid(a, st[j].tile_rows, c->num_sms);
+      CK(dmk::launch_join(a, grid, st[j].tile_rows, c->stream));
+      prev_rows = orows;
+      prev_score = a.outs;
+      prev_cap = cap;
+    }
+    if (c->timing) CK(cudaEventRecord(c->ev1, c->stream));
+    CK(cudaMemcpyAsync(c->h_ctr_steps, c->d_ctr_steps, sizeof(unsigned long long) * CTR_N * S,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int j = 0; j < S; j++)
+      if (c->h_ctr_steps[(size_t)j * CTR_N + CTR_OVF]) return DM_OK;  // does not fit: caller falls back
+    *fits = true;
+    if (c->timing) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      c->stats.join_ms += ms;
+    }
+    int64_t nin = st[0].seed_table->n;
+    for (int j = 0; j < S; j++) {
+      const unsigned long long *h = c->h_ctr_steps + (size_t)j * CTR_N;
+      const JoinArgs &a = st[j].base;
+      int64_t rows = (int64_t)h[CTR_ROWS];
+      double bytes = (double)st[j].motif_bytes + (j ? (double)nin * (4.0 * a.w + (a.scored ? 4 : 0)) : 0.0);
+      if (a.mode == 0) bytes += (double)rows * (4.0 * a.wo + (a.scored ? 4 : 0));
+      c->stats.join_bytes += bytes;
+      c->stats.join_launches++;
+      c->stats.chunks++;
+      if (j < DM_MAX_STEPS) {
+        c->stats.rows[j] += rows;
+        c->stats.candidates[j] += (int64_t)h[CTR_CAND];
+      }
+      if (j + 1 < S) c->stats.max_rows = std::max(c->stats.max_rows, rows);
+      nin = rows;
+    }
+    const unsigned long long *hl = c->h_ctr_steps + (size_t)(S - 1) * CTR_N;
+    if (st[S - 1].base.mode == 1) {
+      count += hl[CTR_ROWS];
+      checksum += hl[CTR_SUM];
+      return DM_OK;
+    }
+    DevTable t;
+    t.rows = prev_rows;
+    t.score = prev_score;
+    t.n = (int64_t)hl[CTR_ROWS];
+    t.w = st[S - 1].base.wo;
+    t.borrowed = true;
+    return sink->take(c, t);
+  }
+
+  int ensure_arena(size_t bytes) {
+    if (c->arena_bytes >= bytes) return DM_OK;
+    if (c->arena) {
+      CK(cudaStreamSynchronize(c->stream));
+      cudaFree(c->arena);
+      c->arena = nullptr;
+      c->arena_bytes = 0;
+    }
+    if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return DM_E_NOMEM;
+    }
+    c->arena_bytes = bytes;
+    return DM_OK;
+  }
+
   int run() {
     RET(setup());
     const int S = (int)st.size();
     c->stats.n_steps = S;
+    if (chunk_rows == 0 && max_rows == 0 && st[0].seed_table->n > 0) {
+      // device-driven path first; grow the arena (up to the budget) while a step overflows
+      size_t want = std::max<size_t>(c->arena_bytes, (size_t)256 << 20);
+      while (true) {
+        want = std::min<size_t>(want, (size_t)c->budget);
+        if (ensure_arena(want) != DM_OK) break;
+        bool fits = false;
+        dm_stats saved = c->stats;
+        RET(run_fast(&fits));
+        if (fits) return DM_OK;
+        c->stats = saved;
+        if (want >= (size_t)c->budget) break;
+        want *= 4;
+      }
+    }
     DevTable *T = st[0].seed_table;
     int64_t n0 = T->n;
     if (n0 == 0) return DM_OK;
@@ -752,23 +892,48 @@ int topk_table(dm_ctx *c, DevGraph *g, const DevTable &t, int64_t k, DevTable *o
   return DM_OK;
 }
 
+// k best of a canonically sorted table (rows in pattern order + scores), in (score, row)
+// order; consumes t.
+int topk_of_sorted(dm_ctx *c, DevGraph *g, DevTable &t, int64_t k, DevTable *out) {
+  if (k > 1024) {  // large k: select by radix on the score bits, then sort the candidates
+    RET(topk_table(c, g, t, k, out));
+    free_table(c, t);
+    return DM_OK;
+  }
+  DevTable o;
+  o.w = t.w;
+  o.n = std::min<int64_t>(k, t.n);
+  RET(dalloc_t(c, &o.rows, (size_t)std::max<int64_t>(1, o.n) * t.w));
+  RET(dalloc_t(c, &o.score, std::max<int64_t>(1, o.n)));
+  if (o.n > 0) {
+    void *tmp = nullptr;
+    RET(dalloc(c, &tmp, (size_t)dmk::topk_tmp_bytes(t.n)));
+    CK(dmk::topk_sorted(t.rows, t.score, t.n, t.w, (int32_t)k, tmp, o.rows, o.score, c->stream));
+    dfree(c, tmp);
+  }
+  free_table(c, t);
+  *out = o;
+  return DM_OK;
+}
+
 struct TopkSink : Sink {
   DevGraph *g;
   int64_t k;
-  DevTable best;  // current best min(k, seen) rows
+  bool input_sorted = false;  // tables arrive in canonical order (from AllSink)
+  DevTable best;              // current best min(k, seen) rows, (score, row) order
   bool have = false;
   float *prune_ptr = nullptr;
   int take(dm_ctx *c, DevTable t) override {
+    if (!input_sorted || t.borrowed) RET(sort_canonical(c, t, graph_bits(g)));
     DevTable tk;
-    RET(topk_table(c, g, t, k, &tk));
-    free_table(c, t);
+    RET(topk_of_sorted(c, g, t, k, &tk));
     if (have) {
       CollectSink cs;
       cs.parts = {best, tk};
       DevTable both;
       RET(cs.concat(c, tk.w, true, &both));
-      RET(topk_table(c, g, both, k, &best));
-      free_table(c, both);
+      RET(sort_canonical(c, both, graph_bits(g)));
+      RET(topk_of_sorted(c, g, both, k, &best));
     } else {
       best = tk;
       have = true;
@@ -917,6 +1082,11 @@ int dm_create(dm_ctx **out, int device, uint64_t mem_budget_bytes) {
     dm_destroy(c);
     return DM_E_NOMEM;
   }
+  if (cudaMalloc(&c->d_ctr_steps, sizeof(unsigned long long) * CTR_N * DM_MAX_STEPS) != cudaSuccess ||
+      cudaMallocHost(&c->h_ctr_steps, sizeof(unsigned long long) * CTR_N * DM_MAX_STEPS) != cudaSuccess) {
+    dm_destroy(c);
+    return DM_E_NOMEM;
+  }
   c->h_stage_bytes = 64ull << 20;
   if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) {
     dm_destroy(c);
@@ -975,6 +1145,9 @@ int dm_destroy(dm_ctx *c) {
   }
   cudaStreamSynchronize(c->stream);
   if (c->d_ctr) cudaFree(c->d_ctr);
+  if (c->d_ctr_steps) cudaFree(c->d_ctr_steps);
+  if (c->h_ctr_steps) cudaFreeHost(c->h_ctr_steps);
+  if (c->arena) cudaFree(c->arena);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1259,6 +1432,7 @@ int dm_match_topk(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void
   TopkSink tk;
   tk.g = g;
   tk.k = k;
+  tk.input_sorted = true;
   AllSink sink;
   sink.flags = mode;
   sink.cb = cb;

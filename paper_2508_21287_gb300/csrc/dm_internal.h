@@ -116,6 +116,8 @@ struct JoinArgs {
   const int32_t *R;
   const float *Rs;
   int64_t N;
+  const unsigned long long *n_dev;  // when set, the row count of R is read from here on the device,
+  int64_t in_cap;                   // clamped to in_cap (rows R can hold; a producer may have overflowed)
   int32_t w;
   // the motif side
   IndexView ix;
@@ -129,7 +131,7 @@ struct JoinArgs {
   int8_t be_a[MAXBE];
   int8_t be_b[MAXBE];
   int32_t wo;                // output width = w + n_new
-  int8_t out_pos[MAXW];      // working column -> position in the written row
+  int8_t src_col[MAXW];      // position q of a written row holds working column src_col[q]
   // data graph
   const unsigned long long *adj;
   int32_t adj_words;

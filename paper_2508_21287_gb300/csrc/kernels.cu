@@ -31,7 +31,7 @@ using namespace dmi;
 
 namespace dmk {
 
-static std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_launches{0};
 int64_t launch_count() { return g_launches.load(); }
 
 #define FULL_MASK 0xffffffffu
@@ -154,7 +154,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x
 
 // ------------------------------------------------------------------ join kernel --------
 int join_tile_rows(int w) {
-  if (w <= 0) return 32;
+  if (w <= 0) return JOIN_BLK;
   int ws = w | 1;
   int tr = 32768 / (ws * 4);
   tr = tr / 32 * 32;
@@ -163,212 +163,318 @@ int join_tile_rows(int w) {
   return tr;
 }
 
+static int join_cpt(int n_new) { return n_new <= 4 ? 4 : 1; }
+
 size_t join_smem_bytes(int w, int wo, int tile_rows) {
+  (void)wo;
   int ws = w > 0 ? (w | 1) : 1;
-  size_t b = (size_t)tile_rows * ws * 4;    // tile
-  b += (size_t)tile_rows * 4;               // tile scores
-  b += (size_t)tile_rows * 4;               // group starts
-  b += (size_t)(tile_rows + 1) * 4;         // group offsets
+  size_t b = (size_t)tile_rows * ws * 4;  // tile
   b = (b + 15) / 16 * 16;
-  b += (size_t)JOIN_BLK * wo * 4;           // output staging
-  b += (size_t)JOIN_BLK * 4;                // staged scores
+  b += (size_t)tile_rows * 16;            // 128-bit vertex signature per row
+  b += (size_t)tile_rows * 4;             // tile scores
+  b += (size_t)tile_rows * 4;             // group starts
+  b += (size_t)(tile_rows + 1) * 4;       // group offsets
+  b = (b + 15) / 16 * 16;
+  b += (size_t)JOIN_BLK * 4 * 8;          // survivor (row, motif row) pairs of one round
   return b;
 }
 
-template <int BLK>
+// 7-bit position of a vertex id in the 128-bit row signature.
+__device__ __forceinline__ unsigned sig_bit(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> 25; }
+
+struct JoinSmem {
+  int32_t *tile;
+  unsigned long long *sig;
+  float *tile_s;
+  int32_t *gstart, *goff;
+  int32_t *surv_r, *surv_m;
+};
+
+__device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int ws, int BLKCPT) {
+  JoinSmem m;
+  size_t off = 0;
+  m.tile = (int32_t *)(smem + off);
+  off += (size_t)TR * ws * 4;
+  off = (off + 15) / 16 * 16;
+  m.sig = (unsigned long long *)(smem + off);
+  off += (size_t)TR * 16;
+  m.tile_s = (float *)(smem + off);
+  off += (size_t)TR * 4;
+  m.gstart = (int32_t *)(smem + off);
+  off += (size_t)TR * 4;
+  m.goff = (int32_t *)(smem + off);
+  off += (size_t)(TR + 1) * 4;
+  off = (off + 15) / 16 * 16;
+  m.surv_r = (int32_t *)(smem + off);
+  m.surv_m = m.surv_r + BLKCPT;
+  return m;
+}
+
+// Value of working column `col` of the joined row (R row `rrow`, motif row `trow`).
+__device__ __forceinline__ int32_t join_value(const JoinArgs &a, const int32_t *rrow, const int32_t *trow, int col) {
+  return col < a.w ? rrow[col] : __ldg(trow + a.new_mpos[col - a.w]);
+}
+
+// Join, filter and score one candidate (R row r of the tile, motif row m).
+template <int MAXNEW>
+__device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, int ws, bool seed, int r, int64_t m,
+                                          float &sc) {
+  const int32_t *rrow = S.tile + r * ws;
+  const int32_t *trow = a.ix.rows + m * a.ix.mw;
+  bool ok = true;
+  for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
+  int32_t nv[MAXNEW];
+#pragma unroll
+  for (int i = 0; i < MAXNEW; i++)
+    if (i < a.n_new) nv[i] = __ldg(trow + a.new_mpos[i]);
+  if (ok && !seed) {  // FilterOverlappingNodes: new vertices must not repeat a mapped one
+    const unsigned long long s0 = S.sig[2 * r], s1 = S.sig[2 * r + 1];
+#pragma unroll
+    for (int i = 0; i < MAXNEW; i++) {
+      if (i < a.n_new) {
+        unsigned b = sig_bit(nv[i]);
+        unsigned long long word = b < 64 ? s0 : s1;
+        if ((word >> (b & 63)) & 1ull)
+          for (int c = 0; c < a.w; c++) ok &= rrow[c] != nv[i];
+      }
+    }
+  }
+  sc = 0.f;
+  if (a.scored) {
+    sc = (!seed && a.Rs) ? S.tile_s[r] : 0.f;
+    if (a.ix.score) sc += __ldg(a.ix.score + m);
+    if (a.qerr) {
+#pragma unroll
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new) sc += __ldg(a.qerr + nv[i]);
+    }
+  }
+  for (int e = 0; e < a.n_be && ok; e++) {
+    int32_t va = join_value(a, rrow, trow, a.be_a[e]);
+    int32_t vb = join_value(a, rrow, trow, a.be_b[e]);
+    ok = adjacent(a, va, vb);
+    if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
+  }
+  if (sc > a.prune) ok = false;
+  return ok;
+}
+
+template <int BLK, int MAXNEW, int CPT, int MODE>
 __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a, int TR) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_warp[BLK / 32];
   __shared__ unsigned long long s_red[BLK / 32];
   __shared__ long long s_base;
-  __shared__ int s_cand;
 
   const bool seed = a.R == nullptr;
   const int w = a.w, wo = a.wo;
   const int ws = w > 0 ? (w | 1) : 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  const JoinSmem S = join_smem(smem, TR, ws, BLK * CPT);
+  const int64_t N = seed ? 0 : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
+  const int64_t nt = seed ? (a.seed_hi - a.seed_lo + (int64_t)BLK * CPT - 1) / ((int64_t)BLK * CPT)
+                          : (N + TR - 1) / TR;
+  const float inv_wo = 1.0f / (float)wo;
 
-  int32_t *tile = (int32_t *)smem;
-  float *tile_s = (float *)(tile + (size_t)TR * ws);
-  int32_t *gstart = (int32_t *)(tile_s + TR);
-  int32_t *goff = gstart + TR;
-  size_t stage_off = ((size_t)((unsigned char *)(goff + TR + 1) - smem) + 15) / 16 * 16;
-  int32_t *stage = (int32_t *)(smem + stage_off);
-  float *stage_s = (float *)(stage + (size_t)BLK * wo);
-
-  const int64_t nt = seed ? (a.seed_hi - a.seed_lo + BLK - 1) / BLK : (a.N + TR - 1) / TR;
+  unsigned long long acc_rows = 0, acc_sum = 0, acc_cand = 0;
 
   for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    int64_t r0 = 0;
-    int nr = 0;
     int C;
     if (!seed) {
-      r0 = t * TR;
-      nr = (int)imin64(TR, a.N - r0);
+      const int64_t r0 = t * TR;
+      const int nr = (int)imin64(TR, N - r0);
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
       for (int e = tid; e < ne; e += BLK) {
         int r = e / w;
-        tile[r * ws + (e - r * w)] = __ldg(src + e);
+        S.tile[r * ws + (e - r * w)] = __ldg(src + e);
       }
       if (a.Rs)
-        for (int r = tid; r < nr; r += BLK) tile_s[r] = __ldg(a.Rs + r0 + r);
+        for (int r = tid; r < nr; r += BLK) S.tile_s[r] = __ldg(a.Rs + r0 + r);
       __syncthreads();
       int len = 0, start = 0;
       if (tid < nr) {
-        int32_t ka = tile[tid * ws + a.key_col[0]];
-        int32_t kb = a.ix.nkeys == 2 ? tile[tid * ws + a.key_col[1]] : 0;
-        ix_lookup(a.ix, ka, kb, start, len);
+        const int32_t *row = S.tile + tid * ws;
+        unsigned long long s0 = 0, s1 = 0;
+        for (int c = 0; c < w; c++) {
+          unsigned b = sig_bit(row[c]);
+          if (b < 64) s0 |= 1ull << b;
+          else s1 |= 1ull << (b - 64);
+        }
+        S.sig[2 * tid] = s0;
+        S.sig[2 * tid + 1] = s1;
+        ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
       }
       int total;
       int off = block_excl_scan<BLK>(tid < TR ? len : 0, total, s_warp);
       if (tid < TR) {
-        gstart[tid] = start;
-        goff[tid] = off;
+        S.gstart[tid] = start;
+        S.goff[tid] = off;
       }
-      if (tid == 0) goff[TR] = total;
+      if (tid == 0) S.goff[TR] = total;
       __syncthreads();
       C = total;
     } else {
-      C = (int)imin64(BLK, a.seed_hi - (a.seed_lo + t * BLK));
+      C = (int)imin64((int64_t)BLK * CPT, a.seed_hi - (a.seed_lo + t * BLK * CPT));
     }
-    if (tid == 0) atomicAdd(a.ctr + CTR_CAND, (unsigned long long)C);
+    acc_cand += tid == 0 ? (unsigned long long)C : 0ull;
 
-    for (int cb = 0; cb < C; cb += BLK) {
-      const int c = cb + tid;
-      const bool valid = c < C;
-      int r = 0;
-      int64_t m = 0;
-      if (valid) {
-        if (seed) {
-          m = a.seed_lo + t * BLK + c;
-        } else {
-          int lo = 0, hi = TR;
-          while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (goff[mid] <= c) lo = mid;
-            else hi = mid;
+    for (int rb = 0; rb < C; rb += BLK * CPT) {
+      int myr[CPT];
+      int64_t mym[CPT];
+      float mys[CPT];
+      unsigned pass = 0;
+#pragma unroll
+      for (int k = 0; k < CPT; k++) {
+        const int c = rb + k * BLK + tid;
+        myr[k] = 0;
+        mym[k] = 0;
+        mys[k] = 0.f;
+        if (c < C) {
+          int r = 0;
+          int64_t m;
+          if (seed) {
+            m = a.seed_lo + t * BLK * CPT + c;
+          } else {
+            int lo = 0, hi = TR;
+            while (hi - lo > 1) {
+              int mid = (lo + hi) >> 1;
+              if (S.goff[mid] <= c) lo = mid;
+              else hi = mid;
+            }
+            r = lo;
+            m = (int64_t)S.gstart[r] + (c - S.goff[r]);
           }
-          r = lo;
-          m = (int64_t)gstart[r] + (c - goff[r]);
+          float sc;
+          if (join_eval<MAXNEW>(a, S, ws, seed, r, m, sc)) {
+            pass |= 1u << k;
+            myr[k] = r;
+            mym[k] = m;
+            mys[k] = sc;
+            if (MODE == 1) {
+              const int32_t *rrow = S.tile + r * ws;
+              const int32_t *trow = a.ix.rows + m * a.ix.mw;
+              unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
+              for (int q = 0; q < wo; q++)
+                h = dmix64(h ^ (unsigned long long)(uint32_t)join_value(a, rrow, trow, a.src_col[q]));
+              acc_sum += h;
+              acc_rows++;
+            }
+          }
         }
       }
-      bool ok = valid;
-      int32_t nv[MAXM];
-      float sc = 0.f;
-      const int32_t *rrow = tile + r * ws;
-      if (valid) {
-        const int32_t *trow = a.ix.rows + m * a.ix.mw;
-        for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
-        for (int i = 0; i < a.n_new; i++) nv[i] = __ldg(trow + a.new_mpos[i]);
-        if (ok)
-          for (int c2 = 0; c2 < w; c2++) {
-            int32_t x = rrow[c2];
-            for (int i = 0; i < a.n_new; i++) ok &= x != nv[i];
-          }
-        if (a.scored) {
-          sc = (!seed && a.Rs) ? tile_s[r] : 0.f;
-          if (a.ix.score) sc += __ldg(a.ix.score + m);
-          if (a.qerr)
-            for (int i = 0; i < a.n_new; i++) sc += __ldg(a.qerr + nv[i]);
-        }
-        for (int e = 0; e < a.n_be && ok; e++) {
-          int ca = a.be_a[e], cbb = a.be_b[e];
-          int32_t va = ca < w ? rrow[ca] : nv[ca - w];
-          int32_t vb = cbb < w ? rrow[cbb] : nv[cbb - w];
-          ok = adjacent(a, va, vb);
-          if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
-        }
-        if (sc > a.prune) ok = false;
-      }
-      // warp-ballot compaction of the survivors into the staging buffer
-      unsigned bal = __ballot_sync(FULL_MASK, ok);
-      if (lane == 0) s_warp[warp] = __popc(bal);
+      if (MODE == 1) continue;
+      // compaction: block scan of per-thread survivor counts, one atomic per round
+      int K;
+      const int pos0 = block_excl_scan<BLK>(__popc(pass), K, s_warp);
+      if (K == 0) continue;
+      if (tid == 0) s_base = (long long)atomicAdd(a.ctr + CTR_ROWS, (unsigned long long)K);
       __syncthreads();
-      int woff = 0, K = 0;
-      for (int i = 0; i < BLK / 32; i++) {
-        int v = s_warp[i];
-        woff += i < warp ? v : 0;
-        K += v;
+      const long long base = s_base;
+      int Kc = K;
+      if (base + K > a.out_cap) {
+        Kc = (int)imax64(0, a.out_cap - base);
+        if (tid == 0) atomicOr(a.ctr + CTR_OVF, 1ull);
       }
-      if (ok) {
-        int pos = woff + __popc(bal & lanemask_lt());
-        int32_t *dst = stage + (size_t)pos * wo;
-        for (int c2 = 0; c2 < w; c2++) dst[a.out_pos[c2]] = rrow[c2];
-        for (int i = 0; i < a.n_new; i++) dst[a.out_pos[w + i]] = nv[i];
-        stage_s[pos] = sc;
-      }
-      if (tid == 0 && K > 0) s_base = (long long)atomicAdd(a.ctr + CTR_ROWS, (unsigned long long)K);
-      __syncthreads();
-      if (K > 0) {
-        const long long base = s_base;
-        if (a.mode == 0) {
-          int Ke = K;
-          if (base + K > a.out_cap) {
-            Ke = (int)imax64(0, a.out_cap - base);
-            if (tid == 0) atomicOr(a.ctr + CTR_OVF, 1ull);
-          }
-          int32_t *dst = a.out + base * wo;
-          const int ne = Ke * wo;
-          for (int e = tid; e < ne; e += BLK) dst[e] = stage[e];
-          unsigned long long nsum = 0;
-          for (int i = tid; i < Ke; i += BLK) {
-            if (a.outs) a.outs[base + i] = stage_s[i];
+      unsigned long long nsum = 0;
+      int pos = pos0;
+#pragma unroll
+      for (int k = 0; k < CPT; k++) {
+        if (pass >> k & 1u) {
+          S.surv_r[pos] = myr[k];
+          S.surv_m[pos] = (int32_t)mym[k];
+          if (pos < Kc) {
+            if (a.outs) a.outs[base + pos] = mys[k];
             if (a.out_next) {
-              const int32_t *row = stage + (size_t)i * wo;
+              const int32_t *rrow = S.tile + myr[k] * ws;
+              const int32_t *trow = a.ix.rows + mym[k] * a.ix.mw;
               int32_t st, ln;
-              ix_lookup(a.nx, row[a.nx_key_col[0]], a.nx.nkeys == 2 ? row[a.nx_key_col[1]] : 0, st, ln);
-              a.out_next[base + i] = ln;
+              ix_lookup(a.nx, join_value(a, rrow, trow, a.nx_key_col[0]),
+                        a.nx.nkeys == 2 ? join_value(a, rrow, trow, a.nx_key_col[1]) : 0, st, ln);
+              a.out_next[base + pos] = ln;
               nsum += (unsigned long long)ln;
             }
           }
-          if (a.out_next) {
-            unsigned long long tot = block_sum_u64<BLK>(nsum, s_red);
-            if (tid == 0 && tot) atomicAdd(a.ctr + CTR_NEXT, tot);
-          }
-        } else {
-          unsigned long long hs = 0;
-          for (int i = tid; i < K; i += BLK) {
-            const int32_t *row = stage + (size_t)i * wo;
-            unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
-            for (int c2 = 0; c2 < wo; c2++) h = dmix64(h ^ (unsigned long long)(uint32_t)row[c2]);
-            hs += h;
-          }
-          unsigned long long tot = block_sum_u64<BLK>(hs, s_red);
-          if (tid == 0) atomicAdd(a.ctr + CTR_SUM, tot);
+          pos++;
         }
       }
       __syncthreads();
+      // coalesced materialisation: element e of the block's output range is row e / wo,
+      // position e % wo (the float quotient is exact for e < 2^20)
+      int32_t *dst = a.out + base * wo;
+      const int ne = Kc * wo;
+      for (int e = tid; e < ne; e += BLK) {
+        const int sidx = __float2int_rd(((float)e + 0.5f) * inv_wo);
+        const int q = e - sidx * wo;
+        const int col = a.src_col[q];
+        const int32_t *rrow = S.tile + S.surv_r[sidx] * ws;
+        dst[e] = col < w ? rrow[col] : __ldg(a.ix.rows + (int64_t)S.surv_m[sidx] * a.ix.mw + a.new_mpos[col - w]);
+      }
+      if (a.out_next) {
+        unsigned long long tot = block_sum_u64<BLK>(nsum, s_red);
+        if (tid == 0 && tot) atomicAdd(a.ctr + CTR_NEXT, tot);
+      }
+      __syncthreads();
+    }
+    __syncthreads();  // the next tile overwrites the shared-memory tile
+  }
+  unsigned long long tc = block_sum_u64<BLK>(acc_cand, s_red);
+  if (tid == 0 && tc) atomicAdd(a.ctr + CTR_CAND, tc);
+  if (MODE == 1) {
+    unsigned long long tr = block_sum_u64<BLK>(acc_rows, s_red);
+    unsigned long long ts = block_sum_u64<BLK>(acc_sum, s_red);
+    if (tid == 0) {
+      if (tr) atomicAdd(a.ctr + CTR_ROWS, tr);
+      atomicAdd(a.ctr + CTR_SUM, ts);
     }
   }
-  (void)s_cand;
 }
 
-static bool g_join_attr_set = false;
+typedef void (*JoinKernel)(JoinArgs, int);
+
+static JoinKernel pick_join(const JoinArgs &a, int *cpt) {
+  *cpt = join_cpt(a.n_new);
+  if (a.mode == 1) {
+    if (a.n_new <= 1) return k_join<JOIN_BLK, 1, 4, 1>;
+    if (a.n_new <= 4) return k_join<JOIN_BLK, 4, 4, 1>;
+    return k_join<JOIN_BLK, MAXM, 1, 1>;
+  }
+  if (a.n_new <= 1) return k_join<JOIN_BLK, 1, 4, 0>;
+  if (a.n_new <= 4) return k_join<JOIN_BLK, 4, 4, 0>;
+  return k_join<JOIN_BLK, MAXM, 1, 0>;
+}
+
+static void set_join_attrs() {
+  static bool done = false;
+  if (done) return;
+  JoinKernel ks[] = {k_join<JOIN_BLK, 1, 4, 1>, k_join<JOIN_BLK, 4, 4, 1>, k_join<JOIN_BLK, MAXM, 1, 1>,
+                     k_join<JOIN_BLK, 1, 4, 0>, k_join<JOIN_BLK, 4, 4, 0>, k_join<JOIN_BLK, MAXM, 1, 0>};
+  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  done = true;
+}
 
 cudaError_t launch_join(const JoinArgs &a, int grid, int tile_rows, cudaStream_t s) {
+  set_join_attrs();
+  int cpt;
+  JoinKernel k = pick_join(a, &cpt);
   size_t smem = join_smem_bytes(a.w, a.wo, tile_rows);
-  if (!g_join_attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_join<JOIN_BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    g_join_attr_set = true;
-  }
   if (grid < 1) grid = 1;
   g_launches++;
-  k_join<JOIN_BLK><<<grid, JOIN_BLK, smem, s>>>(a, tile_rows);
+  k<<<grid, JOIN_BLK, smem, s>>>(a, tile_rows);
   return cudaGetLastError();
 }
 
 int join_grid(const JoinArgs &a, int tile_rows, int num_sms) {
-  int64_t nt = a.R == nullptr ? (a.seed_hi - a.seed_lo + JOIN_BLK - 1) / JOIN_BLK
-                              : (a.N + tile_rows - 1) / tile_rows;
+  set_join_attrs();
+  int cpt;
+  JoinKernel k = pick_join(a, &cpt);
+  int64_t nt;
+  if (a.R == nullptr) nt = (a.seed_hi - a.seed_lo + (int64_t)JOIN_BLK * cpt - 1) / ((int64_t)JOIN_BLK * cpt);
+  else if (a.n_dev) nt = INT64_MAX;  // row count known only on the device: fill the GPU
+  else nt = (a.N + tile_rows - 1) / tile_rows;
   size_t smem = join_smem_bytes(a.w, a.wo, tile_rows);
   int per_sm = 1;
-  if (!g_join_attr_set) {
-    cudaFuncSetAttribute(k_join<JOIN_BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    g_join_attr_set = true;
-  }
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_join<JOIN_BLK>, JOIN_BLK, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, JOIN_BLK, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t g = (int64_t)num_sms * per_sm;
   if (nt < g) g = nt;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dm_internal.h"
 
 namespace dmk {
@@ -12,6 +14,7 @@ constexpr int JOIN_BLK = 256;
 
 // Number of kernels launched by this library in the process so far.
 int64_t launch_count();
+extern std::atomic<int64_t> g_launches;
 
 // Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
 // + compaction). Returns the dynamic shared memory it needs for the given widths.
@@ -60,5 +63,16 @@ cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *ou
 
 // Sum over rows of the checksum hash H(row) into ctr[CTR_SUM] (count = n).
 cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned long long *ctr, cudaStream_t s);
+
+// Canonical row order by comparison sort (sort.cu): *perm_out (inside tmp) receives the
+// row indices in ascending lexicographic order. tmp holds msort_tmp_bytes(n) bytes.
+int64_t msort_tmp_bytes(int64_t n);
+cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, void *tmp, int32_t **perm_out, cudaStream_t s);
+
+// The min(k, n) smallest (score bits, row index) of a canonically sorted table, k <= 1024,
+// gathered into orows / osc in that order. tmp holds topk_tmp_bytes(n) bytes.
+int64_t topk_tmp_bytes(int64_t n);
+cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t w, int32_t k, void *tmp,
+                        int32_t *orows, float *osc, cudaStream_t s);
 
 }  // namespace dmk
