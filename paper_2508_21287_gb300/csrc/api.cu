@@ -257,7 +257,6 @@ int gather_table(dm_ctx *c, const DevTable &t, const int32_t *perm, int64_t n, D
 
 // Replace t by its rows in canonical (lexicographic) order.
 int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
-  (void)bits;
   if (t.n <= 1) {
     if (t.borrowed && t.n == 1) {  // take a private copy so the holder may free it
       DevTable o;
@@ -273,7 +272,7 @@ int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
   void *tmp = nullptr;
   RET(dalloc(c, &tmp, (size_t)dmk::msort_tmp_bytes(t.n)));
   int32_t *perm = nullptr;
-  CK(dmk::msort_rows(t.rows, t.n, t.w, tmp, &perm, c->stream));
+  CK(dmk::msort_rows(t.rows, t.n, t.w, bits, tmp, &perm, c->stream));
   DevTable o;
   RET(gather_table(c, t, perm, t.n, &o));
   dfree(c, tmp);
@@ -712,7 +711,7 @@ struct Exec {
     c->stats.n_steps = S;
     if (chunk_rows == 0 && max_rows == 0 && st[0].seed_table->n > 0) {
       // device-driven path first; grow the arena (up to the budget) while a step overflows
-      size_t want = std::max<size_t>(c->arena_bytes, (size_t)256 << 20);
+      size_t want = std::max<size_t>(c->arena_bytes, (size_t)4 << 30);
       while (true) {
         want = std::min<size_t>(want, (size_t)c->budget);
         if (ensure_arena(want) != DM_OK) break;

@@ -176,6 +176,7 @@ size_t join_smem_bytes(int w, int wo, int tile_rows) {
   b += (size_t)(tile_rows + 1) * 4;       // group offsets
   b = (b + 15) / 16 * 16;
   b += (size_t)JOIN_BLK * 4 * 8;          // survivor (row, motif row) pairs of one round
+  b += (size_t)JOIN_BLK * 4 * 4;          // tile row of each candidate of one round
   return b;
 }
 
@@ -188,6 +189,7 @@ struct JoinSmem {
   float *tile_s;
   int32_t *gstart, *goff;
   int32_t *surv_r, *surv_m;
+  int32_t *cand_row;
 };
 
 __device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int ws, int BLKCPT) {
@@ -207,6 +209,7 @@ __device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int w
   off = (off + 15) / 16 * 16;
   m.surv_r = (int32_t *)(smem + off);
   m.surv_m = m.surv_r + BLKCPT;
+  m.cand_row = m.surv_m + BLKCPT;
   return m;
 }
 
@@ -234,8 +237,12 @@ __device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, 
       if (i < a.n_new) {
         unsigned b = sig_bit(nv[i]);
         unsigned long long word = b < 64 ? s0 : s1;
-        if ((word >> (b & 63)) & 1ull)
-          for (int c = 0; c < a.w; c++) ok &= rrow[c] != nv[i];
+        if ((word >> (b & 63)) & 1ull)  // likely collisions are recent columns: scan backwards
+          for (int c = a.w - 1; c >= 0; c--)
+            if (rrow[c] == nv[i]) {
+              ok = false;
+              break;
+            }
       }
     }
   }
@@ -260,7 +267,7 @@ __device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, 
 }
 
 template <int BLK, int MAXNEW, int CPT, int MODE>
-__global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a, int TR) {
+__global__ void __launch_bounds__(BLK, 4) k_join(const __grid_constant__ JoinArgs a, int TR) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_warp[BLK / 32];
   __shared__ unsigned long long s_red[BLK / 32];
@@ -274,7 +281,9 @@ __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a
   const int64_t N = seed ? 0 : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
   const int64_t nt = seed ? (a.seed_hi - a.seed_lo + (int64_t)BLK * CPT - 1) / ((int64_t)BLK * CPT)
                           : (N + TR - 1) / TR;
-  const float inv_wo = 1.0f / (float)wo;
+  const int ld_r0 = w > 0 ? tid / w : 0, ld_c0 = w > 0 ? tid % w : 0;
+  const int ld_dr = w > 0 ? BLK / w : 0, ld_dc = w > 0 ? BLK % w : 0;
+  const int st_s0 = tid / wo, st_q0 = tid % wo, st_ds = BLK / wo, st_dq = BLK % wo;
 
   unsigned long long acc_rows = 0, acc_sum = 0, acc_cand = 0;
 
@@ -285,9 +294,17 @@ __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a
       const int nr = (int)imin64(TR, N - r0);
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
-      for (int e = tid; e < ne; e += BLK) {
-        int r = e / w;
-        S.tile[r * ws + (e - r * w)] = __ldg(src + e);
+      {  // element e = r * w + c of the tile; (r, c) advance by (BLK / w, BLK % w) with carry
+        int r = ld_r0, c = ld_c0;
+        for (int e = tid; e < ne; e += BLK) {
+          S.tile[r * ws + c] = __ldg(src + e);
+          r += ld_dr;
+          c += ld_dc;
+          if (c >= w) {
+            c -= w;
+            r++;
+          }
+        }
       }
       if (a.Rs)
         for (int r = tid; r < nr; r += BLK) S.tile_s[r] = __ldg(a.Rs + r0 + r);
@@ -320,6 +337,15 @@ __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a
     acc_cand += tid == 0 ? (unsigned long long)C : 0ull;
 
     for (int rb = 0; rb < C; rb += BLK * CPT) {
+      if (!seed) {  // tile row of every candidate of this round
+        if (MODE == 1 && rb > 0) __syncthreads();  // the previous round's readers are done
+        const int re = rb + BLK * CPT;
+        for (int r = tid; r < TR; r += BLK) {
+          int lo = max(S.goff[r], rb), hi = min(S.goff[r + 1], re);
+          for (int c = lo; c < hi; c++) S.cand_row[c - rb] = r;
+        }
+        __syncthreads();
+      }
       int myr[CPT];
       int64_t mym[CPT];
       float mys[CPT];
@@ -336,13 +362,7 @@ __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a
           if (seed) {
             m = a.seed_lo + t * BLK * CPT + c;
           } else {
-            int lo = 0, hi = TR;
-            while (hi - lo > 1) {
-              int mid = (lo + hi) >> 1;
-              if (S.goff[mid] <= c) lo = mid;
-              else hi = mid;
-            }
-            r = lo;
+            r = S.cand_row[c - rb];
             m = (int64_t)S.gstart[r] + (c - S.goff[r]);
           }
           float sc;
@@ -403,12 +423,19 @@ __global__ void __launch_bounds__(BLK) k_join(const __grid_constant__ JoinArgs a
       // position e % wo (the float quotient is exact for e < 2^20)
       int32_t *dst = a.out + base * wo;
       const int ne = Kc * wo;
-      for (int e = tid; e < ne; e += BLK) {
-        const int sidx = __float2int_rd(((float)e + 0.5f) * inv_wo);
-        const int q = e - sidx * wo;
-        const int col = a.src_col[q];
-        const int32_t *rrow = S.tile + S.surv_r[sidx] * ws;
-        dst[e] = col < w ? rrow[col] : __ldg(a.ix.rows + (int64_t)S.surv_m[sidx] * a.ix.mw + a.new_mpos[col - w]);
+      {  // element e = sidx * wo + q; (sidx, q) advance by (BLK / wo, BLK % wo) with carry
+        int sidx = st_s0, q = st_q0;
+        for (int e = tid; e < ne; e += BLK) {
+          const int col = a.src_col[q];
+          const int32_t *rrow = S.tile + S.surv_r[sidx] * ws;
+          dst[e] = col < w ? rrow[col] : __ldg(a.ix.rows + (int64_t)S.surv_m[sidx] * a.ix.mw + a.new_mpos[col - w]);
+          sidx += st_ds;
+          q += st_dq;
+          if (q >= wo) {
+            q -= wo;
+            sidx++;
+          }
+        }
       }
       if (a.out_next) {
         unsigned long long tot = block_sum_u64<BLK>(nsum, s_red);

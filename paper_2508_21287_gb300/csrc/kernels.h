@@ -65,9 +65,11 @@ cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *ou
 cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned long long *ctr, cudaStream_t s);
 
 // Canonical row order by comparison sort (sort.cu): *perm_out (inside tmp) receives the
-// row indices in ascending lexicographic order. tmp holds msort_tmp_bytes(n) bytes.
+// row indices in ascending lexicographic order; ids are below 2^bits. tmp holds
+// msort_tmp_bytes(n) bytes.
 int64_t msort_tmp_bytes(int64_t n);
-cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, void *tmp, int32_t **perm_out, cudaStream_t s);
+cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
+                       cudaStream_t s);
 
 // The min(k, n) smallest (score bits, row index) of a canonically sorted table, k <= 1024,
 // gathered into orows / osc in that order. tmp holds topk_tmp_bytes(n) bytes.

@@ -25,29 +25,35 @@ constexpr int MS_BLK = 512;
 constexpr unsigned long long KEY_INF = ~0ull;
 
 
-// a < b for rows (key0, idx); idx < 0 is a padding element greater than every row
-__device__ __forceinline__ bool row_less(const int32_t *rows, int32_t w, unsigned long long ka, int32_t ia,
+// a < b for rows (key0, idx); idx < 0 is a padding element greater than every row. The key
+// packs the first kc columns (floor(64 / bits) of them), so ties compare from column kc on.
+__device__ __forceinline__ bool row_less(const int32_t *rows, int32_t w, int kc, unsigned long long ka, int32_t ia,
                                          unsigned long long kb, int32_t ib) {
   if (ka != kb) return ka < kb;
   if (ia < 0 || ib < 0) return ib < 0 && ia >= 0;
   const int32_t *ra = rows + (int64_t)ia * w, *rb = rows + (int64_t)ib * w;
-  for (int c = 2; c < w; c++) {
+  for (int c = kc; c < w; c++) {
     int32_t x = __ldg(ra + c), y = __ldg(rb + c);
     if (x != y) return x < y;
   }
   return ia < ib;
 }
 
-__global__ void k_pack_keys(const int32_t *rows, int64_t n, int32_t w, unsigned long long *key, int32_t *idx) {
+__global__ void k_pack_keys(const int32_t *rows, int64_t n, int32_t w, int bits, int kcols,
+                            unsigned long long *key, int32_t *idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t *r = rows + i * w;
-    unsigned long long hi = (uint32_t)__ldg(r), lo = w > 1 ? (uint32_t)__ldg(r + 1) : 0u;
-    key[i] = (hi << 32) | lo;
+    unsigned long long k = 0;
+    for (int c = 0; c < kcols; c++) {
+      unsigned long long v = c < w ? (uint32_t)__ldg(r + c) : 0u;
+      k |= v << (64 - bits * (c + 1));
+    }
+    key[i] = k;
     idx[i] = (int32_t)i;
   }
 }
 
-__global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int32_t w, int64_t n,
+__global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int32_t w, int kc, int64_t n,
                                                        unsigned long long *key, int32_t *idx) {
   __shared__ unsigned long long sk[MS_TILE];
   __shared__ int32_t si[MS_TILE];
@@ -64,7 +70,7 @@ __global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int3
         int i = 2 * t - (t & (j - 1));
         int p = i + j;
         bool up = (i & k) == 0;
-        bool gt = row_less(rows, w, sk[p], si[p], sk[i], si[i]);
+        bool gt = row_less(rows, w, kc, sk[p], si[p], sk[i], si[i]);
         if (gt == up) {
           unsigned long long tk = sk[i];
           sk[i] = sk[p];
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int3
 }
 
 // Merge the sorted runs [b, b+L) and [b+L, b+2L) of (key, idx) into (okey, oidx).
-__global__ void k_merge_pass(const int32_t *rows, int32_t w, int64_t n, int64_t L, const unsigned long long *key,
+__global__ void k_merge_pass(const int32_t *rows, int32_t w, int kc, int64_t n, int64_t L, const unsigned long long *key,
                              const int32_t *idx, unsigned long long *okey, int32_t *oidx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pair = i / (2 * L);
@@ -101,8 +107,8 @@ __global__ void k_merge_pass(const int32_t *rows, int32_t w, int64_t n, int64_t 
     // A elements go before equal B elements: count B < x for A, A <= x for B
     while (lo < hi) {
       int64_t mid = (lo + hi) >> 1;
-      bool before = inA ? row_less(rows, w, key[mid], idx[mid], kx, ix)
-                        : !row_less(rows, w, kx, ix, key[mid], idx[mid]);
+      bool before = inA ? row_less(rows, w, kc, key[mid], idx[mid], kx, ix)
+                        : !row_less(rows, w, kc, kx, ix, key[mid], idx[mid]);
       if (before) lo = mid + 1;
       else hi = mid;
     }
@@ -114,7 +120,8 @@ __global__ void k_merge_pass(const int32_t *rows, int32_t w, int64_t n, int64_t 
 
 int64_t msort_tmp_bytes(int64_t n) { return n * (8 + 4) * 2 + 256; }
 
-cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, void *tmp, int32_t **perm_out, cudaStream_t s) {
+cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
+                       cudaStream_t s) {
   unsigned long long *k0 = (unsigned long long *)tmp;
   unsigned long long *k1 = k0 + n;
   int32_t *i0 = (int32_t *)(k1 + n);
@@ -123,11 +130,15 @@ cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, void *tmp, int
   if (n <= 0) return cudaSuccess;
   int grid = (int)((n + 255) / 256);
   if (grid > 16384) grid = 16384;
-  k_pack_keys<<<grid, 256, 0, s>>>(rows, n, w, k0, i0);
-  k_sort_tiles<<<(unsigned)((n + MS_TILE - 1) / MS_TILE), MS_BLK, 0, s>>>(rows, w, n, k0, i0);
+  if (bits < 1) bits = 1;
+  if (bits > 32) bits = 32;
+  int kcols = 64 / bits;
+  if (kcols > w) kcols = w;
+  k_pack_keys<<<grid, 256, 0, s>>>(rows, n, w, bits, kcols, k0, i0);
+  k_sort_tiles<<<(unsigned)((n + MS_TILE - 1) / MS_TILE), MS_BLK, 0, s>>>(rows, w, kcols, n, k0, i0);
   int launches = 2;
   for (int64_t L = MS_TILE; L < n; L *= 2) {
-    k_merge_pass<<<grid, 256, 0, s>>>(rows, w, n, L, k0, i0, k1, i1);
+    k_merge_pass<<<grid, 256, 0, s>>>(rows, w, kcols, n, L, k0, i0, k1, i1);
     launches++;
     std::swap(k0, k1);
     std::swap(i0, i1);
