@@ -168,6 +168,16 @@ int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void 
 int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, int mode,
                    uint64_t *out_counts, uint64_t *out_checksums);
 
+/* Launch shape of the last dm_match_batch (tile rows per CTA step, root rows per work item,
+ * CTAs of the persistent launch), as picked by the autotuner. */
+int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid);
+
+/* Tuning knobs: autotune (1 = time the candidate launch shapes on the first dm_match_batch
+ * of a new set of plans and keep the fastest), hash_load_factor (fill of two-key hash
+ * indices, 0 < f <= 0.95; changing it rebuilds those indices). Plans made before a change
+ * of the load factor must be made again. */
+int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor);
+
 /* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,
  * row) key, in that order. out_rows: k x n_p int32 host buffer; out_scores: k floats
  * (nullable); out_n receives the number written. Needs edge weights (DM_E_INVAL if none). */

@@ -89,6 +89,8 @@ _SIGS = {
     "dm_last_error": (ctypes.c_char_p, [_vp]),
     "dm_decompose": (_i32, [_i32, _i32p, _i32p, _i32p, _i32, _i32, _i32p, _i32]),
     "dm_sort_rows_static": (ctypes.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp]),
+    "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p]),
+    "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -274,6 +276,16 @@ def dm_match_batch(ctx, plans, mode: int = DM_COUNT):
                              sums.ctypes.data_as(_u64p))
     _check(rc, "dm_match_batch", ctx)
     return counts, sums
+
+
+def dm_batch_config(ctx) -> dict:
+    tr, ch, gr = _i32(), _i64(), _i32()
+    _check(_lib.dm_batch_config(ctx, ctypes.byref(tr), ctypes.byref(ch), ctypes.byref(gr)), "dm_batch_config", ctx)
+    return {"tile_rows": tr.value, "root_chunk": ch.value, "grid": gr.value}
+
+
+def dm_set_tuning(ctx, autotune: bool = True, hash_load_factor: float = 0.5) -> None:
+    _check(_lib.dm_set_tuning(ctx, int(bool(autotune)), float(hash_load_factor)), "dm_set_tuning", ctx)
 
 
 def dm_score_topk(ctx, plan, k: int, n_p: int):

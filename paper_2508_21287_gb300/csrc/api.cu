@@ -74,6 +74,9 @@ struct dm_ctx {
   size_t arena_bytes = 0;
   unsigned long long *d_ctr_steps = nullptr;  // CTR_N counters per step
   unsigned long long *h_ctr_steps = nullptr;
+  struct BatchState *batch = nullptr;  // cached device image of the last batch of plans
+  int autotune = 1;
+  double hash_lf = 0.5;               // load factor of two-key hash indices
 };
 
 struct dm_plan_s {
@@ -336,7 +339,7 @@ int ensure_index(dm_ctx *c, DevGraph *g, int motif, int kp0, int kp1, Index **ou
     ix.bytes += 4 * ((int64_t)g->V + 1);
   } else {
     uint32_t lg = 1;
-    while ((1ll << lg) < 2 * std::max<int64_t>(1, T.n)) lg++;
+    while ((double)(1ll << lg) * c->hash_lf < (double)std::max<int64_t>(1, T.n)) lg++;
     RET(dalloc_t(c, &ix.slots, (size_t)1 << lg));
     CK(cudaMemsetAsync(ix.slots, 0xFF, sizeof(HashSlot) << lg, c->stream));
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
@@ -1020,9 +1023,176 @@ int ensure_motif(dm_ctx *c, DevGraph *g, int id) {
   return build_motif_by_joins(c, g, md);
 }
 
+}  // namespace
+
+// Device image of a batch of plans for the persistent kernel, with its tuned launch shape
+// and the CUDA graph that replays memsets + launch + result copy.
+struct BatchState {
+  std::vector<const dm_plan_t *> key;
+  double hash_lf = 0;
+  int TR = 64;
+  int64_t root_chunk = 16;
+  dmk::BatchParams prm{};
+  int grid = 0;
+  void *d_args = nullptr, *d_plans = nullptr, *d_items = nullptr, *d_work = nullptr, *scratch = nullptr;
+  unsigned long long *h_out = nullptr;
+  int32_t n_plans = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool tuned = false;
+};
+
+namespace {
+
+void batch_release(dm_ctx *c, BatchState *b) {
+  if (!b) return;
+  cudaStreamSynchronize(c->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_args);
+  cudaFree(b->d_plans);
+  cudaFree(b->d_items);
+  cudaFree(b->d_work);
+  cudaFree(b->scratch);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  delete b;
+}
+
+int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
+                BatchState **out);
+
 DevGraph *get_graph(dm_ctx *c, dm_graph g) {
   if (!c || g < 0 || g >= (int)c->graphs.size()) return nullptr;
   return c->graphs[g];
+}
+
+int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
+                BatchState **out) {
+  std::unique_ptr<BatchState> b(new BatchState());
+  b->key.assign(plans, plans + n);
+  b->hash_lf = c->hash_lf;
+  b->TR = TR;
+  b->root_chunk = root_chunk;
+  b->n_plans = n;
+  std::vector<JoinArgs> args;
+  std::vector<dmk::BatchPlan> bplans(n);
+  std::vector<std::pair<double, dmk::BatchItem>> items;
+  std::vector<int64_t> cap(MAXSTEPS, 0), maxw(MAXSTEPS, 0);
+  int ws_max = 1;
+  for (int32_t i = 0; i < n; i++) {
+    Exec ex;
+    ex.c = c;
+    ex.g = g;
+    ex.p = &plans[i]->p;
+    ex.mode = DM_COUNT;
+    ex.use_qerr = false;
+    RET(ex.setup());
+    const int S = (int)ex.st.size();
+    bplans[i].n_steps = S;
+    bplans[i].args_off = (int32_t)args.size();
+    double cost = 0;
+    for (int j = 0; j < S; j++) {
+      JoinArgs a = ex.st[j].base;
+      a.scored = 0;
+      a.qerr = nullptr;
+      a.eerr = nullptr;
+      a.out_next = nullptr;
+      a.nx.nkeys = -1;
+      a.prune = INFINITY;
+      args.push_back(a);
+      ws_max = std::max(ws_max, a.w > 0 ? (a.w | 1) : 1);
+      maxw[j] = std::max<int64_t>(maxw[j], a.wo);
+      if (j > 0) cap[j] = std::max<int64_t>(cap[j], (int64_t)TR * ex.st[j].max_group);
+      cost += ex.p->steps[j].est_rows;
+    }
+    cap[0] = std::max<int64_t>(cap[0], root_chunk);
+    int64_t n0 = ex.st[0].seed_table->n;
+    for (int64_t lo = 0; lo < n0; lo += root_chunk) {
+      dmk::BatchItem it{};
+      it.plan = i;
+      it.lo = lo;
+      it.hi = std::min(n0, lo + root_chunk);
+      items.push_back({cost / std::max<double>(1.0, (double)(n0 + root_chunk - 1) / root_chunk), it});
+    }
+  }
+  // expensive chunks first: the tail of the persistent loop is made of cheap ones
+  std::stable_sort(items.begin(), items.end(), [](const std::pair<double, dmk::BatchItem> &x,
+                                                  const std::pair<double, dmk::BatchItem> &y) { return x.first > y.first; });
+  std::vector<dmk::BatchItem> hitems(items.size());
+  for (size_t i = 0; i < items.size(); i++) hitems[i] = items[i].second;
+  dmk::BatchParams &P = b->prm;
+  int64_t off = 0;
+  for (int j = 0; j < MAXSTEPS; j++) {
+    P.lvl_off[j] = off;
+    P.lvl_cap[j] = cap[j];
+    off += (cap[j] * std::max<int64_t>(1, maxw[j]) * 4 + 255) / 256 * 256;
+  }
+  P.cta_bytes = off;
+  P.TR = TR;
+  P.ws_max = ws_max;
+  P.n_items = (int64_t)hitems.size();
+  b->grid = dmk::batch_grid(TR, ws_max, c->num_sms);
+  while (b->grid > c->num_sms && (uint64_t)b->grid * P.cta_bytes > c->budget / 2) b->grid /= 2;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return DM_E_NOMEM;
+    }
+    cudaError_t e = bytes ? cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
+    return DM_OK;
+  };
+  RET(up(&b->d_args, args.data(), sizeof(JoinArgs) * args.size()));
+  RET(up(&b->d_plans, bplans.data(), sizeof(dmk::BatchPlan) * bplans.size()));
+  RET(up(&b->d_items, hitems.data(), sizeof(dmk::BatchItem) * hitems.size()));
+  if (cudaMalloc(&b->d_work, sizeof(unsigned long long) * (2 + 2 * (size_t)n)) != cudaSuccess) {
+    cudaGetLastError();
+    return DM_E_NOMEM;
+  }
+  if (cudaMalloc(&b->scratch, std::max<size_t>(16, (size_t)b->grid * P.cta_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return DM_E_NOMEM;
+  }
+  if (cudaMallocHost(&b->h_out, sizeof(unsigned long long) * (2 + 2 * (size_t)n)) != cudaSuccess) return DM_E_NOMEM;
+  unsigned long long *work = (unsigned long long *)b->d_work;
+  P.args = (const JoinArgs *)b->d_args;
+  P.plans = (const dmk::BatchPlan *)b->d_plans;
+  P.items = (const dmk::BatchItem *)b->d_items;
+  P.next_item = work;
+  P.ovf = work + 1;
+  P.out = work + 2;
+  P.scratch = (unsigned char *)b->scratch;
+  *out = b.release();
+  return DM_OK;
+}
+
+// One execution of a built batch: reset counters, run the persistent kernel, copy the results
+// back. The sequence is captured once into a CUDA graph and replayed afterwards.
+int batch_run(dm_ctx *c, BatchState *b) {
+  size_t wbytes = sizeof(unsigned long long) * (2 + 2 * (size_t)b->n_plans);
+  if (!b->exec) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(b->d_work, 0, wbytes, cs);
+      dmk::launch_batch(b->prm, b->grid, cs);
+      cudaMemcpyAsync(b->h_out, b->d_work, wbytes, cudaMemcpyDeviceToHost, cs);
+      e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch graph capture");
+  } else {
+    dmk::g_launches++;  // the replayed graph holds one launch of the batch kernel
+  }
+  CK(cudaGraphLaunch(b->exec, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (b->h_out[1]) {
+    c->last_error = "batch level buffer overflow";
+    return DM_E_CAPACITY;
+  }
+  return DM_OK;
 }
 
 void reset_stats(dm_ctx *c) {
@@ -1123,6 +1293,8 @@ int dm_destroy(dm_ctx *c) {
   if (!c) return DM_E_INVAL;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  batch_release(c, c->batch);
+  c->batch = nullptr;
   for (DevGraph *g : c->graphs) {
     if (!g) continue;
     for (auto &kv : g->motifs) {
@@ -1362,11 +1534,84 @@ int dm_match(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *use
 int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, int mode, uint64_t *out_counts,
                    uint64_t *out_checksums) {
   if (!c || (!plans && n_plans > 0) || n_plans < 0 || (mode & 0xF) != DM_COUNT) return DM_E_INVAL;
+  if (n_plans == 0) return DM_OK;
+  DevGraph *g = get_graph(c, plans[0] ? plans[0]->p.graph : -1);
+  if (!g) return DM_E_NOTFOUND;
+  for (int32_t i = 0; i < n_plans; i++)
+    if (!plans[i] || plans[i]->p.graph != plans[0]->p.graph) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  BatchState *b = c->batch;
+  bool same = b && b->hash_lf == c->hash_lf && (int32_t)b->key.size() == n_plans &&
+              std::equal(b->key.begin(), b->key.end(), plans);
+  if (!same) {
+    batch_release(c, b);
+    c->batch = nullptr;
+    int TR = 64;
+    int64_t chunk = 16;
+    if (c->autotune) {  // time each launch shape once on this batch, keep the fastest
+      double best = 1e300;
+      const int trs[] = {32, 64, 128};
+      const int64_t chunks[] = {4, 16, 64};
+      for (int tr : trs)
+        for (int64_t ch : chunks) {
+          BatchState *t = nullptr;
+          int r = batch_build(c, g, plans, n_plans, tr, ch, &t);
+          if (r != DM_OK) {
+            batch_release(c, t);
+            continue;
+          }
+          auto s0 = std::chrono::steady_clock::now();
+          r = batch_run(c, t);
+          double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s0).count();
+          batch_release(c, t);
+          if (r == DM_OK && ms < best) {
+            best = ms;
+            TR = tr;
+            chunk = ch;
+          }
+        }
+    }
+    RET(batch_build(c, g, plans, n_plans, TR, chunk, &b));
+    b->tuned = c->autotune != 0;
+    c->batch = b;
+  }
+  RET(batch_run(c, b));
   for (int32_t i = 0; i < n_plans; i++) {
-    uint64_t cnt = 0, cs = 0;
-    RET(dm_match(c, plans[i], DM_COUNT, nullptr, nullptr, &cnt, &cs));
-    if (out_counts) out_counts[i] = cnt;
-    if (out_checksums) out_checksums[i] = cs;
+    if (out_counts) out_counts[i] = b->h_out[2 + 2 * i];
+    if (out_checksums) out_checksums[i] = b->h_out[3 + 2 * i];
+  }
+  finish_stats(c, t0);
+  return DM_OK;
+}
+
+int dm_batch_config(dm_ctx *c, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid) {
+  if (!c || !c->batch) return DM_E_INVAL;
+  if (tile_rows) *tile_rows = c->batch->TR;
+  if (root_chunk) *root_chunk = c->batch->root_chunk;
+  if (grid) *grid = c->batch->grid;
+  return DM_OK;
+}
+
+int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor) {
+  if (!c || hash_load_factor <= 0.0 || hash_load_factor > 0.95) return DM_E_INVAL;
+  c->autotune = autotune;
+  if (hash_load_factor != c->hash_lf) {
+    c->hash_lf = hash_load_factor;
+    for (DevGraph *g : c->graphs) {  // two-key indices are rebuilt at the new load factor
+      if (!g) continue;
+      for (auto it = g->indices.begin(); it != g->indices.end();) {
+        if (it->second.v.nkeys == 2) {
+          cudaFreeAsync(it->second.rows, c->stream);
+          if (it->second.score) cudaFreeAsync(it->second.score, c->stream);
+          cudaFreeAsync(it->second.slots, c->stream);
+          it = g->indices.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
   }
   return DM_OK;
 }

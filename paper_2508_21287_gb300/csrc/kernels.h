@@ -77,4 +77,33 @@ int64_t topk_tmp_bytes(int64_t n);
 cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t w, int32_t k, void *tmp,
                         int32_t *orows, float *osc, cudaStream_t s);
 
+// Persistent batch kernel (batch.cu).
+struct BatchPlan {
+  int32_t n_steps;
+  int32_t args_off;  // index of the plan's first step in BatchParams::args
+};
+struct BatchItem {
+  int32_t plan;
+  int32_t pad;
+  int64_t lo, hi;    // rows of the first slice's motif table
+};
+struct BatchParams {
+  const dmi::JoinArgs *args;
+  const BatchPlan *plans;
+  const BatchItem *items;
+  int64_t n_items;
+  unsigned long long *next_item;  // work counter (zeroed before the launch)
+  unsigned long long *out;        // count, checksum per plan (zeroed before the launch)
+  unsigned long long *ovf;
+  unsigned char *scratch;         // grid * cta_bytes
+  int64_t cta_bytes;
+  int64_t lvl_off[dmi::MAXSTEPS]; // byte offset of level j inside a CTA's scratch
+  int64_t lvl_cap[dmi::MAXSTEPS]; // rows level j can hold
+  int TR;                         // rows per tile
+  int ws_max;                     // odd shared-memory row stride covering every step
+};
+size_t batch_smem_bytes(int tile_rows, int ws_max);
+int batch_grid(int tile_rows, int ws_max, int num_sms);
+cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s);
+
 }  // namespace dmk

@@ -1,0 +1,89 @@
+"""Persistent batch kernel (dm_match_batch) against the oracle and against dm_match alone.
+
+One launch runs count + checksum for every plan; each plan's result must equal its own
+single-plan run and the oracle's, for uneven plan sizes, plans with no embedding, two-key
+(hash-indexed) joins, every autotuned launch shape and a changed hash load factor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_21287_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2508_21287_gb300 import build
+    build.build()
+    from paper_2508_21287_gb300 import binding
+    return binding
+
+
+def _run(B, ctx, gid, pats, **kw):
+    plans = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, **kw) for p in pats]
+    counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+    single = [B.dm_match(ctx.h, pl, B.DM_COUNT) for pl in plans]
+    for pl in plans:
+        B.dm_plan_free(pl)
+    return counts, sums, single
+
+
+def _check(g, pats, counts, sums, single):
+    for p, c, s, (c1, s1) in zip(pats, counts.tolist(), sums.tolist(), single):
+        ref = oracle.enumerate(g, p, rows=False, threads=8)
+        assert (c, s) == (ref.count, ref.checksum), p.name
+        assert (c1, s1) == (c, s)
+
+
+def test_batch_mixed_heavy_hex(B):
+    g = I.heavy_hex(12, 6)
+    pats = [I.mixed_pattern(s, 5, 40) for s in range(60)]
+    with B.Context(0) as ctx:
+        gid = ctx.load(g)
+        counts, sums, single = _run(B, ctx, gid, pats)
+        _check(g, pats, counts, sums, single)
+        cfg = B.dm_batch_config(ctx.h)
+        assert cfg["tile_rows"] in (32, 64, 128) and cfg["root_chunk"] in (4, 16, 64)
+        # the same plans again: the cached device image and graph are replayed
+        counts2, sums2, _ = _run(B, ctx, gid, pats)
+        assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
+
+
+def test_batch_paths_and_patches(B):
+    g = I.heavy_hex(8, 9)
+    pats = [I.path(k) for k in (2, 3, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]
+    pats += [I.from_edges(1, [])]  # single vertex: one-step plan
+    with B.Context(0) as ctx:
+        gid = ctx.load(g)
+        B.dm_set_tuning(ctx.h, False, 0.5)
+        counts, sums, single = _run(B, ctx, gid, pats)
+        _check(g, pats, counts, sums, single)
+
+
+@pytest.mark.parametrize("lf", [0.25, 0.9])
+def test_batch_two_key_joins_on_grid(B, lf):
+    g = I.grid(10, 10)
+    pats = [I.cycle(4), I.cycle(6), I.cycle(8), I.grid(2, 3), I.grid(3, 3), I.subdivided_grid(2, 2),
+            I.random_tree(7, 1), I.path(6)]
+    with B.Context(0) as ctx:
+        B.dm_set_tuning(ctx.h, True, lf)
+        gid = ctx.load(g)
+        counts, sums, single = _run(B, ctx, gid, pats, motifs=[104, 106, 202, 2])
+        _check(g, pats, counts, sums, single)
+
+
+def test_batch_rejects_mixed_graphs_and_modes(B):
+    with B.Context(0) as ctx:
+        a = ctx.load(I.grid(3, 3))
+        b = ctx.load(I.grid(4, 4))
+        p = I.path(3)
+        pa = B.dm_plan(ctx.h, a, p.n, p.row_ptr, p.col_idx)
+        pb = B.dm_plan(ctx.h, b, p.n, p.row_ptr, p.col_idx)
+        with pytest.raises(B.DMError):
+            B.dm_match_batch(ctx.h, [pa, pb], B.DM_COUNT)
+        with pytest.raises(B.DMError):
+            B.dm_match_batch(ctx.h, [pa], B.DM_ALL)
+        B.dm_plan_free(pa)
+        B.dm_plan_free(pb)
