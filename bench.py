@@ -51,9 +51,10 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
+    ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
     return ap.parse_args()
 
 
@@ -67,6 +68,9 @@ def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: in
         g = I.lognormal_weights(I.heavy_hex(4, 6), seed=7)
         pats = [I.layout_query(g, rank * batch + i) for i in range(batch)]
         return g, pats
+    if kind == "c4":
+        g = I.heavy_hex(12, 6)
+        return g, [I.mixed_pattern(rank * batch + i, 5, 40) for i in range(batch)]
     g = I.heavy_hex(*hh)
     if only_path:
         return g, [I.path(only_path)]
@@ -158,9 +162,15 @@ def cpu_baseline(g, pats, budget_s: float = 12.0, count_only: bool = False):
                          "backtracking + FP64 scores + top-100 per query")}
 
 
+WORKLOAD_C4 = ("C4 batched: heavy-hex 12x6 (V=431), 512 seeded patterns of 5-40 vertices (trees / cycles / "
+               "subdivided 2xk grids), count + checksum, one persistent launch per step")
+
+
 def wl_name(args):
     if args.workload == "c2":
         return WORKLOAD
+    if args.workload == "c4":
+        return WORKLOAD_C4
     m, n = (int(x) for x in args.hh.split(","))
     return WORKLOAD_C3.format(m=m, n=n, V=5 * m * n + 4 * m + 4 * n - 1)
 
@@ -310,10 +320,86 @@ def run_ours(args):
     return 0
 
 
+def run_c4(args):
+    """Batched form: every pattern of the batch in one persistent launch (dm_match_batch),
+    against the plain form (one dm_match per pattern) on the same GPU, plans made up front."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2508_21287_gb300 import build
+    build.build()
+    from paper_2508_21287_gb300 import binding as B
+    g, pats = workload(rank, args.batch if args.batch != BATCH else 512, "c4")
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream()
+    B.dm_set_stream(ctx.h, stream)
+    gid = ctx.load(g)
+    order = B.DM_ORDER_LEARNED if args.learned else B.DM_ORDER_PAPER
+    t0 = time.perf_counter()
+    plans = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=order) for p in pats]
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+    emb_per_step = int(counts.sum())
+    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+            ev[i][1].record(stream)
+            launches += B.dm_get_stats(ctx.h)["kernel_launches"]
+        torch.cuda.synchronize()
+    batch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(batch_ms)
+    value = emb_per_step * args.steps / (ms / 1e3)
+    # plain form: one call per pattern, each timed on its own
+    lat = []
+    plain_emb = 0
+    for p in plans:
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        c, _ = B.dm_match(ctx.h, p, B.DM_COUNT)
+        lat.append(1e3 * (time.perf_counter() - s0))
+        plain_emb += c
+    plain_ms = sum(lat)
+    lat.sort()
+    pct = lambda xs, q: xs[min(len(xs) - 1, int(q * len(xs)))]
+    bs = sorted(batch_ms)
+    cfg = B.dm_batch_config(ctx.h)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl_name(args), "patterns_per_step": len(pats), "embeddings_per_step": emb_per_step,
+                       "order": "learned" if args.learned else "paper", "plan_ms_total": plan_ms,
+                       "batch_launch": cfg, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "batched": {"value": value, "p50_ms_per_pattern": pct(bs, 0.5), "p99_ms_per_pattern": pct(bs, 0.99),
+                        "note": "every pattern's result is ready when the batch returns"},
+            "plain": {"value": plain_emb / (plain_ms / 1e3), "p50_ms_per_pattern": pct(lat, 0.5),
+                      "p99_ms_per_pattern": pct(lat, 0.99), "total_ms": plain_ms},
+            "gpu_launches": launches, "clocks": clk.summary(), "e2e": None}
+    for p in plans:
+        B.dm_plan_free(p)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 

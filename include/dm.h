@@ -191,6 +191,49 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
                   int32_t k, int32_t *out_rows, float *out_scores, int32_t *out_n,
                   uint64_t *out_count, uint64_t *out_checksum);
 
+/* ------------------------------------------------------------------ learned planner --- */
+/* No counterpart in the paper (which notes that motif choice and ordering matter, Sec. 5.2):
+ * a 3-layer MLP (32 -> 128 -> 128 -> 1, ReLU; BF16 tensor-core matmuls with FP32
+ * accumulation) predicts, for a candidate join step, the log growth of the intermediate
+ * table, log(1 + rows after) - log(1 + rows before). DM_ORDER_LEARNED plans pick, at each
+ * decomposition step, the candidate slice with the smallest predicted growth per newly
+ * mapped vertex; without a trained model they fall back to the independence heuristic.
+ * The output set never depends on the order. Feature vectors are DM_MODEL_FEATURES floats
+ * (dm_plan_estimates / dm_step_log give them); parameters are FP32, flat, in the order
+ * W1[128][32] b1[128] W2[128][128] b2[128] w3[128] b3, followed by the 32 input means and
+ * 32 input standard deviations used to standardise the features. */
+#define DM_MODEL_FEATURES 32
+
+/* Fresh He-uniform weights from a SplitMix64 stream seeded by `seed`; forgets training. */
+int dm_model_init(dm_ctx *ctx, uint64_t seed);
+
+/* Train on n (features, log growth) samples with Adam (mini-batches of `batch` >= 16,
+ * `epochs` passes, learning rate lr, shuffling seeded by `seed`), all on the GPU.
+ * out_loss (nullable) receives the mean squared error of each epoch. */
+int dm_model_train(dm_ctx *ctx, const float *feats, const float *targets, int32_t n, int32_t epochs,
+                   int32_t batch, float lr, uint64_t seed, float *out_loss);
+
+/* Predicted log growth of n feature vectors (host in, host out). */
+int dm_model_predict(dm_ctx *ctx, const float *feats, int32_t n, float *out);
+
+/* One forward + backward pass on raw (already standardised) inputs, for checking the
+ * kernels: predictions, the gradient of the mean squared error (flat, parameter order) and
+ * the loss. targets may be NULL (forward only). */
+int dm_model_grad(dm_ctx *ctx, const float *feats, const float *targets, int32_t n, float *out_pred,
+                  float *out_grads, float *out_loss);
+
+/* Parameters + standardisation (n_floats receives the count); set them back (checkpoint). */
+int dm_model_weights(dm_ctx *ctx, float *out, int64_t *n_floats);
+int dm_model_set_weights(dm_ctx *ctx, const float *w, int64_t n_floats);
+
+/* The (features, observed log growth) samples logged by every dm_match so far: up to cap of
+ * them are copied out, out_n receives how many exist, clear != 0 empties the log. */
+int dm_step_log(dm_ctx *ctx, float *feats, float *targets, int64_t cap, int64_t *out_n, int clear);
+
+/* The model inputs of a plan's steps (cap rows of DM_MODEL_FEATURES) and the independence
+ * heuristic's log growth of each; returns the number of steps. */
+int dm_plan_estimates(const dm_plan_t *plan, float *feats, float *heur_growth, int32_t cap);
+
 /* ------------------------------------------------------------------ no-allocation sort */
 /* No counterpart in the paper: a library service for callers that cannot allocate device
  * memory when they need it (cudaMalloc/cudaFree synchronise the device, which a latency-bound

@@ -91,6 +91,14 @@ _SIGS = {
     "dm_sort_rows_static": (ctypes.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp]),
     "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p]),
     "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+    "dm_model_init": (ctypes.c_int, [_vp, _u64]),
+    "dm_model_train": (ctypes.c_int, [_vp, _fp, _fp, _i32, _i32, _i32, ctypes.c_float, _u64, _fp]),
+    "dm_model_predict": (ctypes.c_int, [_vp, _fp, _i32, _fp]),
+    "dm_model_grad": (ctypes.c_int, [_vp, _fp, _fp, _i32, _fp, _fp, _fp]),
+    "dm_model_weights": (ctypes.c_int, [_vp, _fp, ctypes.POINTER(_i64)]),
+    "dm_model_set_weights": (ctypes.c_int, [_vp, _fp, _i64]),
+    "dm_step_log": (ctypes.c_int, [_vp, _fp, _fp, _i64, ctypes.POINTER(_i64), ctypes.c_int]),
+    "dm_plan_estimates": (_i32, [_vp, _fp, _fp, _i32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -286,6 +294,79 @@ def dm_batch_config(ctx) -> dict:
 
 def dm_set_tuning(ctx, autotune: bool = True, hash_load_factor: float = 0.5) -> None:
     _check(_lib.dm_set_tuning(ctx, int(bool(autotune)), float(hash_load_factor)), "dm_set_tuning", ctx)
+
+
+DM_MODEL_FEATURES = 32
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _pf(a: np.ndarray):
+    return a.ctypes.data_as(_fp)
+
+
+def dm_model_init(ctx, seed: int = 1) -> None:
+    _check(_lib.dm_model_init(ctx, int(seed)), "dm_model_init", ctx)
+
+
+def dm_model_train(ctx, feats, targets, epochs: int = 30, batch: int = 256, lr: float = 1e-3, seed: int = 1):
+    x, t = _f32(feats).reshape(-1, DM_MODEL_FEATURES), _f32(targets)
+    loss = np.zeros(epochs, dtype=np.float32)
+    _check(_lib.dm_model_train(ctx, _pf(x), _pf(t), len(t), int(epochs), int(batch), float(lr), int(seed), _pf(loss)),
+           "dm_model_train", ctx)
+    return loss
+
+
+def dm_model_predict(ctx, feats) -> np.ndarray:
+    x = _f32(feats).reshape(-1, DM_MODEL_FEATURES)
+    out = np.zeros(len(x), dtype=np.float32)
+    _check(_lib.dm_model_predict(ctx, _pf(x), len(x), _pf(out)), "dm_model_predict", ctx)
+    return out
+
+
+def dm_model_grad(ctx, feats, targets=None):
+    x = _f32(feats).reshape(-1, DM_MODEL_FEATURES)
+    t = None if targets is None else _f32(targets)
+    pred = np.zeros(len(x), dtype=np.float32)
+    n = _i64()
+    _lib.dm_model_weights(ctx, None, ctypes.byref(n))
+    grads = np.zeros(n.value - 2 * DM_MODEL_FEATURES, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(_lib.dm_model_grad(ctx, _pf(x), None if t is None else _pf(t), len(x), _pf(pred),
+                              _pf(grads) if t is not None else None, _pf(loss)), "dm_model_grad", ctx)
+    return pred, (grads if t is not None else None), float(loss[0])
+
+
+def dm_model_weights(ctx) -> np.ndarray:
+    n = _i64()
+    _check(_lib.dm_model_weights(ctx, None, ctypes.byref(n)), "dm_model_weights", ctx)
+    w = np.zeros(n.value, dtype=np.float32)
+    _check(_lib.dm_model_weights(ctx, _pf(w), ctypes.byref(n)), "dm_model_weights", ctx)
+    return w
+
+
+def dm_model_set_weights(ctx, w) -> None:
+    w = _f32(w)
+    _check(_lib.dm_model_set_weights(ctx, _pf(w), len(w)), "dm_model_set_weights", ctx)
+
+
+def dm_step_log(ctx, clear: bool = False):
+    n = _i64()
+    _check(_lib.dm_step_log(ctx, None, None, 0, ctypes.byref(n), 0), "dm_step_log", ctx)
+    f = np.zeros((n.value, DM_MODEL_FEATURES), dtype=np.float32)
+    t = np.zeros(n.value, dtype=np.float32)
+    _check(_lib.dm_step_log(ctx, _pf(f), _pf(t), n.value, ctypes.byref(n), int(bool(clear))), "dm_step_log", ctx)
+    return f, t
+
+
+def dm_plan_estimates(plan):
+    n = _lib.dm_plan_estimates(plan, None, None, 0)
+    f = np.zeros((n, DM_MODEL_FEATURES), dtype=np.float32)
+    h = np.zeros(n, dtype=np.float32)
+    _lib.dm_plan_estimates(plan, _pf(f), _pf(h), n)
+    return f, h
 
 
 def dm_score_topk(ctx, plan, k: int, n_p: int):

@@ -75,6 +75,13 @@ struct dm_ctx {
   unsigned long long *d_ctr_steps = nullptr;  // CTR_N counters per step
   unsigned long long *h_ctr_steps = nullptr;
   struct BatchState *batch = nullptr;  // cached device image of the last batch of plans
+  // cardinality model (DM_ORDER_LEARNED) and the step log it is trained on
+  float *m_params = nullptr, *m_grads = nullptr, *m_m = nullptr, *m_v = nullptr;
+  int m_step = 0;
+  bool m_trained = false;
+  float m_mean[NFEAT] = {}, m_std[NFEAT] = {};
+  bool log_steps = true;
+  std::vector<float> log_feat, log_target;
   int autotune = 1;
   double hash_lf = 0.5;               // load factor of two-key hash indices
 };
@@ -1195,6 +1202,89 @@ int batch_run(dm_ctx *c, BatchState *b) {
   return DM_OK;
 }
 
+// Model input of a planner feature vector: the model predicts growth, so the absolute
+// estimate f[0] is dropped and the heuristic's absolute estimate f[22] becomes its growth.
+void model_input(const float *f, float *x) {
+  for (int i = 0; i < NFEAT; i++) x[i] = f[i];
+  x[22] = f[22] - f[0];
+  x[0] = 0.f;
+}
+
+// Log (features, observed log growth) of every executed step of a plan (training data).
+void log_plan_steps(dm_ctx *c, const Plan &p) {
+  if (!c->log_steps || c->log_target.size() > (size_t)4 << 20) return;
+  double prev = 0.0;
+  for (size_t j = 0; j < p.steps.size() && j < (size_t)DM_MAX_STEPS; j++) {
+    double cur = log1p((double)c->stats.rows[j]);
+    float x[NFEAT];
+    model_input(p.steps[j].feat, x);
+    c->log_feat.insert(c->log_feat.end(), x, x + NFEAT);
+    c->log_target.push_back((float)(cur - prev));
+    prev = cur;
+  }
+}
+
+int model_alloc(dm_ctx *c) {
+  if (c->m_params) return DM_OK;
+  size_t b = sizeof(float) * (size_t)dmk::mlp_param_count();
+  if (cudaMalloc(&c->m_params, b) != cudaSuccess || cudaMalloc(&c->m_grads, b) != cudaSuccess ||
+      cudaMalloc(&c->m_m, b) != cudaSuccess || cudaMalloc(&c->m_v, b) != cudaSuccess) {
+    cudaGetLastError();
+    return DM_E_NOMEM;
+  }
+  CK(cudaMemset(c->m_grads, 0, b));
+  CK(cudaMemset(c->m_m, 0, b));
+  CK(cudaMemset(c->m_v, 0, b));
+  return DM_OK;
+}
+
+// Forward (and backward when targets and grads are given) over n samples of raw inputs.
+int model_run(dm_ctx *c, const float *x_host, const float *t_host, int32_t n, float *y_host, float *grads_dev,
+              float *loss_host) {
+  int rows = (n + 15) / 16 * 16;
+  float *X = nullptr, *T = nullptr, *Y = nullptr, *L = nullptr;
+  void *work = nullptr;
+  RET(dalloc_t(c, &X, (size_t)rows * NFEAT));
+  RET(dalloc_t(c, &Y, rows));
+  RET(dalloc_t(c, &L, 1));
+  RET(dalloc(c, &work, (size_t)dmk::mlp_work_bytes(rows)));
+  CK(cudaMemsetAsync(X, 0, sizeof(float) * rows * NFEAT, c->stream));
+  CK(cudaMemcpyAsync(X, x_host, sizeof(float) * n * NFEAT, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(L, 0, sizeof(float), c->stream));
+  if (t_host) {
+    RET(dalloc_t(c, &T, rows));
+    CK(cudaMemsetAsync(T, 0, sizeof(float) * rows, c->stream));
+    CK(cudaMemcpyAsync(T, t_host, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(dmk::mlp_forward_backward(c->m_params, X, T, rows, n, Y, grads_dev, L, work, c->stream));
+  if (y_host) CK(cudaMemcpyAsync(y_host, Y, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (loss_host) CK(cudaMemcpyAsync(loss_host, L, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  dfree(c, X);
+  dfree(c, T);
+  dfree(c, Y);
+  dfree(c, L);
+  dfree(c, work);
+  return DM_OK;
+}
+
+void normalise(const dm_ctx *c, const float *x, int32_t n, std::vector<float> &out) {
+  out.resize((size_t)n * NFEAT);
+  for (int32_t i = 0; i < n; i++)
+    for (int k = 0; k < NFEAT; k++) out[(size_t)i * NFEAT + k] = (x[(size_t)i * NFEAT + k] - c->m_mean[k]) / c->m_std[k];
+}
+
+// DM_ORDER_LEARNED: predicted log rows after each candidate step (planner feature vectors).
+int model_predict_plan(void *self, const float *feats, int n, float *out) {
+  dm_ctx *c = (dm_ctx *)self;
+  std::vector<float> x((size_t)n * NFEAT), xn, y(n);
+  for (int i = 0; i < n; i++) model_input(feats + (size_t)i * NFEAT, &x[(size_t)i * NFEAT]);
+  normalise(c, x.data(), n, xn);
+  RET(model_run(c, xn.data(), nullptr, n, y.data(), nullptr, nullptr));
+  for (int i = 0; i < n; i++) out[i] = feats[(size_t)i * NFEAT] + y[i];
+  return DM_OK;
+}
+
 void reset_stats(dm_ctx *c) {
   memset(&c->stats, 0, sizeof(c->stats));
   c->stats.kernel_launches = -dmk::launch_count();
@@ -1319,6 +1409,10 @@ int dm_destroy(dm_ctx *c) {
   if (c->d_ctr_steps) cudaFree(c->d_ctr_steps);
   if (c->h_ctr_steps) cudaFreeHost(c->h_ctr_steps);
   if (c->arena) cudaFree(c->arena);
+  cudaFree(c->m_params);
+  cudaFree(c->m_grads);
+  cudaFree(c->m_m);
+  cudaFree(c->m_v);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1433,7 +1527,8 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
     gs.motifs.push_back({id, g->motifs.at(id).n});
   }
   if (n_p == 1) RET(ensure_motif(c, g, MOTIF_VERTEX));
-  RET(decompose(p, p.motifs, p.order, gs, nullptr, nullptr, &p.steps, p.col_vertex));
+  CardModelFn model = (p.order == DM_ORDER_LEARNED && c->m_trained) ? model_predict_plan : nullptr;
+  RET(decompose(p, p.motifs, p.order, gs, model, c, &p.steps, p.col_vertex));
   if ((int)p.steps.size() > DM_MAX_STEPS) return DM_E_CAPACITY;
   for (size_t j = 1; j < p.steps.size(); j++) {
     Index *ix;
@@ -1526,6 +1621,7 @@ int dm_match(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *use
   cudaStreamSynchronize(c->stream);
   finish_stats(c, t0);
   if (r != DM_OK) return r;
+  log_plan_steps(c, pl->p);
   if (out_count) *out_count = cnt;
   if (out_checksum) *out_checksum = cs;
   return DM_OK;
@@ -1702,6 +1798,169 @@ int dm_match_topk(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void
   cudaStreamSynchronize(c->stream);
   finish_stats(c, t0);
   return r;
+}
+
+int dm_model_init(dm_ctx *c, uint64_t seed) {
+  if (!c) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  RET(model_alloc(c));
+  const int64_t P = dmk::mlp_param_count();
+  std::vector<float> w(P, 0.f);
+  uint64_t st = seed;
+  auto next = [&]() {  // SplitMix64
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto unif = [&]() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; };
+  const int H = 128, IN = NFEAT;
+  double a1 = sqrt(6.0 / IN), a2 = sqrt(6.0 / H), a3 = sqrt(3.0 / H);  // He-uniform
+  size_t o = 0;
+  for (int i = 0; i < H * IN; i++) w[o++] = (float)(a1 * unif());
+  o += H;
+  for (int i = 0; i < H * H; i++) w[o++] = (float)(a2 * unif());
+  o += H;
+  for (int i = 0; i < H; i++) w[o++] = (float)(a3 * unif());
+  CK(cudaMemcpy(c->m_params, w.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+  CK(cudaMemset(c->m_m, 0, sizeof(float) * P));
+  CK(cudaMemset(c->m_v, 0, sizeof(float) * P));
+  c->m_step = 0;
+  c->m_trained = false;
+  for (int k = 0; k < NFEAT; k++) {
+    c->m_mean[k] = 0.f;
+    c->m_std[k] = 1.f;
+  }
+  return DM_OK;
+}
+
+int dm_model_weights(dm_ctx *c, float *out, int64_t *n_floats) {
+  if (!c) return DM_E_INVAL;
+  const int64_t P = dmk::mlp_param_count();
+  if (n_floats) *n_floats = P + 2 * NFEAT;
+  if (!out) return DM_OK;
+  if (!c->m_params) return DM_E_INVAL;
+  CK(cudaMemcpy(out, c->m_params, sizeof(float) * P, cudaMemcpyDeviceToHost));
+  memcpy(out + P, c->m_mean, sizeof(float) * NFEAT);
+  memcpy(out + P + NFEAT, c->m_std, sizeof(float) * NFEAT);
+  return DM_OK;
+}
+
+int dm_model_set_weights(dm_ctx *c, const float *w, int64_t n) {
+  const int64_t P = dmk::mlp_param_count();
+  if (!c || !w || n != P + 2 * NFEAT) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  RET(model_alloc(c));
+  CK(cudaMemcpy(c->m_params, w, sizeof(float) * P, cudaMemcpyHostToDevice));
+  for (int k = 0; k < NFEAT; k++) {
+    c->m_mean[k] = w[P + k];
+    c->m_std[k] = w[P + NFEAT + k] > 0.f ? w[P + NFEAT + k] : 1.f;
+  }
+  c->m_trained = true;
+  return DM_OK;
+}
+
+int dm_model_grad(dm_ctx *c, const float *feats, const float *targets, int32_t n, float *out_pred,
+                  float *out_grads, float *out_loss) {
+  if (!c || !feats || n < 1 || !c->m_params) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  const int64_t P = dmk::mlp_param_count();
+  if (targets) CK(cudaMemset(c->m_grads, 0, sizeof(float) * P));
+  RET(model_run(c, feats, targets, n, out_pred, targets ? c->m_grads : nullptr, out_loss));
+  if (targets && out_grads) CK(cudaMemcpy(out_grads, c->m_grads, sizeof(float) * P, cudaMemcpyDeviceToHost));
+  return DM_OK;
+}
+
+int dm_model_train(dm_ctx *c, const float *feats, const float *targets, int32_t n, int32_t epochs, int32_t batch,
+                   float lr, uint64_t seed, float *out_loss) {
+  if (!c || !feats || !targets || n < 1 || epochs < 1 || batch < 16) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  if (!c->m_params) RET(dm_model_init(c, seed));
+  if (!c->m_trained) {  // standardise each input feature over the training set
+    for (int k = 0; k < NFEAT; k++) {
+      double s = 0, s2 = 0;
+      for (int32_t i = 0; i < n; i++) {
+        double v = feats[(size_t)i * NFEAT + k];
+        s += v;
+        s2 += v * v;
+      }
+      double mu = s / n, var = s2 / n - mu * mu;
+      c->m_mean[k] = (float)mu;
+      c->m_std[k] = var > 1e-12 ? (float)sqrt(var) : 1.f;
+    }
+  }
+  std::vector<float> xn;
+  normalise(c, feats, n, xn);
+  const int64_t P = dmk::mlp_param_count();
+  std::vector<int32_t> idx(n);
+  for (int32_t i = 0; i < n; i++) idx[i] = i;
+  uint64_t st = seed ^ 0xA5A5A5A5ull;
+  std::vector<float> bx, bt;
+  for (int32_t ep = 0; ep < epochs; ep++) {
+    for (int32_t i = n - 1; i > 0; i--) {  // Fisher-Yates with SplitMix64
+      st += 0x9E3779B97F4A7C15ull;
+      uint64_t z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      std::swap(idx[i], idx[(int32_t)(z % (uint64_t)(i + 1))]);
+    }
+    double ep_loss = 0;
+    for (int32_t b0 = 0; b0 < n; b0 += batch) {
+      int32_t m = std::min(batch, n - b0);
+      bx.resize((size_t)m * NFEAT);
+      bt.resize(m);
+      for (int32_t i = 0; i < m; i++) {
+        memcpy(&bx[(size_t)i * NFEAT], &xn[(size_t)idx[b0 + i] * NFEAT], sizeof(float) * NFEAT);
+        bt[i] = targets[idx[b0 + i]];
+      }
+      float loss = 0;
+      CK(cudaMemsetAsync(c->m_grads, 0, sizeof(float) * P, c->stream));
+      RET(model_run(c, bx.data(), bt.data(), m, nullptr, c->m_grads, &loss));
+      c->m_step++;
+      CK(dmk::mlp_adam(c->m_params, c->m_grads, c->m_m, c->m_v, P, lr, c->m_step, c->stream));
+      ep_loss += (double)loss * m;
+    }
+    if (out_loss) out_loss[ep] = (float)(ep_loss / n);
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->m_trained = true;
+  return DM_OK;
+}
+
+int dm_model_predict(dm_ctx *c, const float *feats, int32_t n, float *out) {
+  if (!c || !feats || !out || n < 1 || !c->m_params) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  std::vector<float> xn;
+  normalise(c, feats, n, xn);
+  return model_run(c, xn.data(), nullptr, n, out, nullptr, nullptr);
+}
+
+int dm_step_log(dm_ctx *c, float *feats, float *targets, int64_t cap, int64_t *out_n, int clear) {
+  if (!c) return DM_E_INVAL;
+  int64_t n = (int64_t)c->log_target.size();
+  if (out_n) *out_n = n;
+  int64_t m = std::min(n, cap);
+  if (feats && m > 0) memcpy(feats, c->log_feat.data(), sizeof(float) * m * NFEAT);
+  if (targets && m > 0) memcpy(targets, c->log_target.data(), sizeof(float) * m);
+  if (clear) {
+    c->log_feat.clear();
+    c->log_target.clear();
+  }
+  return DM_OK;
+}
+
+int dm_plan_estimates(const dm_plan_t *pl, float *feats, float *heur_growth, int32_t cap) {
+  if (!pl) return DM_E_INVAL;
+  int32_t n = (int32_t)pl->p.steps.size();
+  for (int32_t j = 0; j < n && j < cap; j++) {
+    float x[NFEAT];
+    model_input(pl->p.steps[j].feat, x);
+    if (feats) memcpy(feats + (size_t)j * NFEAT, x, sizeof(x));
+    if (heur_growth) heur_growth[j] = x[22];
+  }
+  return n;
 }
 
 int dm_get_stats(dm_ctx *c, dm_stats *out) {

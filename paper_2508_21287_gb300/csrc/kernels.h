@@ -106,4 +106,12 @@ size_t batch_smem_bytes(int tile_rows, int ws_max);
 int batch_grid(int tile_rows, int ws_max, int num_sms);
 cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s);
 
+// Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.
+int64_t mlp_param_count();
+int64_t mlp_work_bytes(int rows);
+cudaError_t mlp_forward_backward(const float *params, const float *X, const float *target, int rows, int n_valid,
+                                 float *y, float *grads, float *loss, void *work, cudaStream_t s);
+cudaError_t mlp_adam(float *params, const float *grads, float *m, float *v, int64_t n, float lr, int step,
+                     cudaStream_t s);
+
 }  // namespace dmk
