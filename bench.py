@@ -179,10 +179,12 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    g, pats = workload(0, args.batch, args.workload, tuple(int(x) for x in args.hh.split(",")))
+    nb = 512 if args.workload == "c4" and args.batch == BATCH else args.batch
+    g, pats = workload(0, nb, args.workload, tuple(int(x) for x in args.hh.split(",")))
     import oracle
     oracle.build()
-    cb = cpu_baseline(g, pats, budget_s=max(5.0, 3.0 * (args.steps + args.warmup)), count_only=args.workload == "c3")
+    cb = cpu_baseline(g, pats, budget_s=max(5.0, 3.0 * (args.steps + args.warmup)),
+                      count_only=args.workload in ("c3", "c4"))
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -320,9 +322,40 @@ def run_ours(args):
     return 0
 
 
+def train_model(B, ctx, gid, g, n_train: int = 300):
+    """Train the cardinality model on steps logged from patterns disjoint from the benchmark's
+    (seeds 100000+), in both the paper's and the heuristic order. Returns the held-out MAE of
+    the model and of the heuristic on log growth."""
+    import numpy as np
+    from paper_2508_21287_gb300 import inputs as I
+    B.dm_step_log(ctx.h, clear=True)
+    for order in (B.DM_ORDER_PAPER, B.DM_ORDER_HEURISTIC):
+        for s in range(100000, 100000 + n_train):
+            p = I.mixed_pattern(s, 5, 40)
+            pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=order)
+            B.dm_match(ctx.h, pl, B.DM_COUNT)
+            B.dm_plan_free(pl)
+    f, t = B.dm_step_log(ctx.h, clear=True)
+    B.dm_model_init(ctx.h, 3)
+    t0 = time.perf_counter()
+    losses = B.dm_model_train(ctx.h, f, t, epochs=60, batch=256, lr=2e-3, seed=3)
+    train_s = time.perf_counter() - t0
+    for s in range(200000, 200060):
+        p = I.mixed_pattern(s, 5, 40)
+        pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=B.DM_ORDER_HEURISTIC)
+        B.dm_match(ctx.h, pl, B.DM_COUNT)
+        B.dm_plan_free(pl)
+    fh, th = B.dm_step_log(ctx.h, clear=True)
+    pred = B.dm_model_predict(ctx.h, fh)
+    return {"samples": int(len(t)), "train_s": train_s, "mse_first_epoch": float(losses[0]),
+            "mse_last_epoch": float(losses[-1]), "heldout_mae_model": float(np.mean(np.abs(pred - th))),
+            "heldout_mae_heuristic": float(np.mean(np.abs(fh[:, 22] - th)))}
+
+
 def run_c4(args):
-    """Batched form: every pattern of the batch in one persistent launch (dm_match_batch),
-    against the plain form (one dm_match per pattern) on the same GPU, plans made up front."""
+    """C4: 512 uneven patterns on one graph. Plain form: one dm_match per pattern, each timed
+    alone. Batched: every pattern in one persistent launch (dm_match_batch). Batched+learned:
+    the same with plans ordered by the trained cardinality model. Plans are made up front."""
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -332,61 +365,68 @@ def run_c4(args):
     from paper_2508_21287_gb300 import build
     build.build()
     from paper_2508_21287_gb300 import binding as B
-    g, pats = workload(rank, args.batch if args.batch != BATCH else 512, "c4")
+    nb = args.batch if args.batch != BATCH else 512
+    g, pats = workload(rank, nb, "c4")
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
     B.dm_set_stream(ctx.h, stream)
     gid = ctx.load(g)
-    order = B.DM_ORDER_LEARNED if args.learned else B.DM_ORDER_PAPER
-    t0 = time.perf_counter()
-    plans = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=order) for p in pats]
-    plan_ms = 1e3 * (time.perf_counter() - t0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
-    emb_per_step = int(counts.sum())
-    launches = 0
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    pct = lambda xs, q: sorted(xs)[min(len(xs) - 1, int(q * len(xs)))]
+
+    def make(order):
+        t0 = time.perf_counter()
+        pl = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=order) for p in pats]
+        return pl, 1e3 * (time.perf_counter() - t0)
+
+    def batched(plans, clk=None):
+        for _ in range(args.warmup):
+            counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches = 0
+        torch.cuda.synchronize()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
             ev[i][0].record(stream)
-            B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+            counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
             ev[i][1].record(stream)
             launches += B.dm_get_stats(ctx.h)["kernel_launches"]
         torch.cuda.synchronize()
-    batch_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(batch_ms)
-    value = emb_per_step * args.steps / (ms / 1e3)
-    # plain form: one call per pattern, each timed on its own
-    lat = []
-    plain_emb = 0
-    for p in plans:
+        ms = [a.elapsed_time(b) for a, b in ev]
+        emb = int(counts.sum())
+        return {"value": emb * len(ms) / (sum(ms) / 1e3), "ms_per_step": sum(ms) / len(ms),
+                "p50_ms_per_pattern": pct(ms, 0.5), "p99_ms_per_pattern": pct(ms, 0.99),
+                "launch": B.dm_batch_config(ctx.h), "embeddings_per_step": emb}, launches, ms
+
+    paper_plans, paper_plan_ms = make(B.DM_ORDER_PAPER)
+    lat, plain_emb = [], 0
+    for p in paper_plans:  # plain form
         torch.cuda.synchronize()
         s0 = time.perf_counter()
         c, _ = B.dm_match(ctx.h, p, B.DM_COUNT)
         lat.append(1e3 * (time.perf_counter() - s0))
         plain_emb += c
-    plain_ms = sum(lat)
-    lat.sort()
-    pct = lambda xs, q: xs[min(len(xs) - 1, int(q * len(xs)))]
-    bs = sorted(batch_ms)
-    cfg = B.dm_batch_config(ctx.h)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    plain = {"value": plain_emb / (sum(lat) / 1e3), "ms_total": sum(lat), "p50_ms_per_pattern": pct(lat, 0.5),
+             "p99_ms_per_pattern": pct(lat, 0.99), "plan_ms_total": paper_plan_ms}
+    bat, _, _ = batched(paper_plans)
+    model = train_model(B, ctx, gid, g)
+    learned_plans, learned_plan_ms = make(B.DM_ORDER_LEARNED)
+    with ClockSampler(local) as clk:
+        bl, launches, ms = batched(learned_plans)
+    bl["plan_ms_total"] = learned_plan_ms
+    assert bl["embeddings_per_step"] == bat["embeddings_per_step"] == plain_emb
+    line = {"metric": METRIC, "value": bl["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": bl["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl_name(args), "patterns_per_step": len(pats), "embeddings_per_step": emb_per_step,
-                       "order": "learned" if args.learned else "paper", "plan_ms_total": plan_ms,
-                       "batch_launch": cfg, "l2": "flushed between steps (256 MiB write)",
+            "config": {"workload": wl_name(args), "patterns_per_step": len(pats),
+                       "embeddings_per_step": bl["embeddings_per_step"], "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "batched": {"value": value, "p50_ms_per_pattern": pct(bs, 0.5), "p99_ms_per_pattern": pct(bs, 0.99),
-                        "note": "every pattern's result is ready when the batch returns"},
-            "plain": {"value": plain_emb / (plain_ms / 1e3), "p50_ms_per_pattern": pct(lat, 0.5),
-                      "p99_ms_per_pattern": pct(lat, 0.99), "total_ms": plain_ms},
+            "plain": plain, "batched": bat, "batched_learned": bl, "model": model,
             "gpu_launches": launches, "clocks": clk.summary(), "e2e": None}
-    for p in plans:
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(g, pats, count_only=True)
+    for p in paper_plans + learned_plans:
         B.dm_plan_free(p)
     ctx.close()
     if rank == 0:

@@ -234,6 +234,49 @@ int dm_step_log(dm_ctx *ctx, float *feats, float *targets, int64_t cap, int64_t 
  * heuristic's log growth of each; returns the number of steps. */
 int dm_plan_estimates(const dm_plan_t *plan, float *feats, float *heur_growth, int32_t cap);
 
+/* ------------------------------------------------------------------ serving ---------- */
+/* Layout-query server (Sec. 5.4's layout selection as a service; the paper has no serving
+ * loop): top-k requests are taken in arrival order by n_slots worker slots, each with its own
+ * context and CUDA stream, so requests admitted while others run overlap on the GPU. A
+ * request is admitted when a slot is free and its projected join memory (planner estimates of
+ * the two largest consecutive tables) fits the pool shared by all in-flight requests; it is
+ * answered with DM_E_CAPACITY when the projection exceeds the pool or max_rows, or when a
+ * step's candidate rows exceed max_rows while it runs. Results equal dm_score_topk on the
+ * same plan alone. Every graph is loaded into every slot. */
+typedef struct dm_server dm_server;
+typedef struct dm_server_opts {
+    int32_t n_slots;            /* concurrent requests (default 4, at most 64) */
+    uint64_t mem_budget_bytes;  /* pool for projected join memory (0 = 16 GiB) */
+    int64_t max_rows;           /* work cap per request step (0 = none) */
+    int32_t order;              /* DM_ORDER_* of request plans */
+    const int32_t *motifs;      /* motif set of request plans (NULL = presets) */
+    int32_t n_motifs;
+} dm_server_opts;
+typedef struct dm_server_stats {
+    int64_t submitted, completed, rejected, failed, queued, in_flight;
+    uint64_t pool_used, pool_total;
+} dm_server_stats;
+
+int dm_server_create(dm_server **out, int device, const dm_server_opts *opts);
+/* Load a data graph into every slot (no request may be queued or running); same arguments
+ * and errors as dm_load_data_graph. */
+int dm_server_load_graph(dm_server *s, int32_t n_vertices, const int32_t *row_ptr,
+                         const int32_t *col_idx, const float *edge_err, const float *qubit_err,
+                         dm_graph *out);
+/* Install trained model parameters (dm_model_weights layout) in every slot. */
+int dm_server_set_model(dm_server *s, const float *w, int64_t n_floats);
+/* Enqueue a top-k request (pattern CSR copied; the arrival time is now); out_id identifies it. */
+int dm_server_submit(dm_server *s, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
+                     const int32_t *p_col_idx, int32_t k, uint64_t *out_id);
+/* Block until request `id` is answered: rows (k x n_p) and scores (k) as dm_score_topk,
+ * n_out rows written, status (DM_OK or a DM_E_* code), latency = answer time - arrival,
+ * queue = start of its device work - arrival (ms). Each id can be waited for once. */
+int dm_server_wait(dm_server *s, uint64_t id, int32_t *rows, float *scores, int32_t *n_out,
+                   int32_t *status, double *latency_ms, double *queue_ms);
+int dm_server_stats_get(dm_server *s, dm_server_stats *out);
+/* Finish the queued requests, stop the workers, release every slot. */
+int dm_server_destroy(dm_server *s);
+
 /* ------------------------------------------------------------------ no-allocation sort */
 /* No counterpart in the paper: a library service for callers that cannot allocate device
  * memory when they need it (cudaMalloc/cudaFree synchronise the device, which a latency-bound

@@ -56,6 +56,17 @@ class dm_stats(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
 
+class dm_server_opts(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_uint64), ("max_rows", ctypes.c_int64),
+                ("order", ctypes.c_int32), ("motifs", ctypes.POINTER(ctypes.c_int32)), ("n_motifs", ctypes.c_int32)]
+
+
+class dm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("pool_used", ctypes.c_uint64), ("pool_total", ctypes.c_uint64)]
+
+
 DM_CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int32)
 
@@ -99,6 +110,14 @@ _SIGS = {
     "dm_model_set_weights": (ctypes.c_int, [_vp, _fp, _i64]),
     "dm_step_log": (ctypes.c_int, [_vp, _fp, _fp, _i64, ctypes.POINTER(_i64), ctypes.c_int]),
     "dm_plan_estimates": (_i32, [_vp, _fp, _fp, _i32]),
+    "dm_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(dm_server_opts)]),
+    "dm_server_load_graph": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32p]),
+    "dm_server_set_model": (ctypes.c_int, [_vp, _fp, _i64]),
+    "dm_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, _i32, _u64p]),
+    "dm_server_wait": (ctypes.c_int, [_vp, _u64, _i32p, _fp, _i32p, _i32p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "dm_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(dm_server_stats)]),
+    "dm_server_destroy": (ctypes.c_int, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -367,6 +386,63 @@ def dm_plan_estimates(plan):
     h = np.zeros(n, dtype=np.float32)
     _lib.dm_plan_estimates(plan, _pf(f), _pf(h), n)
     return f, h
+
+
+def dm_server_create(device: int = 0, n_slots: int = 4, mem_budget_bytes: int = 0, max_rows: int = 0,
+                     order: int = DM_ORDER_PAPER, motifs=None):
+    o = dm_server_opts()
+    o.n_slots, o.mem_budget_bytes, o.max_rows, o.order = int(n_slots), int(mem_budget_bytes), int(max_rows), int(order)
+    keep = None
+    if motifs:
+        keep = _arr_i32(list(motifs))
+        o.motifs, o.n_motifs = _p32(keep), len(keep)
+    h = _vp()
+    _check(_lib.dm_server_create(ctypes.byref(h), int(device), ctypes.byref(o)), "dm_server_create")
+    return h
+
+
+def dm_server_load_graph(srv, n_vertices: int, row_ptr, col_idx, edge_err=None, qubit_err=None) -> int:
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    ee = None if edge_err is None else _f32(edge_err)
+    qe = None if qubit_err is None else _f32(qubit_err)
+    out = _i32()
+    _check(_lib.dm_server_load_graph(srv, int(n_vertices), _p32(rp), _p32(ci), None if ee is None else _pf(ee),
+                                     None if qe is None else _pf(qe), ctypes.byref(out)), "dm_server_load_graph")
+    return out.value
+
+
+def dm_server_set_model(srv, w) -> None:
+    w = _f32(w)
+    _check(_lib.dm_server_set_model(srv, _pf(w), len(w)), "dm_server_set_model")
+
+
+def dm_server_submit(srv, graph: int, n_p: int, row_ptr, col_idx, k: int) -> int:
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    rid = _u64()
+    _check(_lib.dm_server_submit(srv, int(graph), int(n_p), _p32(rp), _p32(ci), int(k), ctypes.byref(rid)),
+           "dm_server_submit")
+    return rid.value
+
+
+def dm_server_wait(srv, rid: int, k: int, n_p: int) -> dict:
+    rows = np.zeros((k, n_p), dtype=np.int32)
+    scores = np.zeros(k, dtype=np.float32)
+    n, st = _i32(), _i32()
+    lat, q = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.dm_server_wait(srv, int(rid), _p32(rows), _pf(scores), ctypes.byref(n), ctypes.byref(st),
+                               ctypes.byref(lat), ctypes.byref(q)), "dm_server_wait")
+    return {"rows": rows[:n.value], "scores": scores[:n.value], "status": st.value, "latency_ms": lat.value,
+            "queue_ms": q.value}
+
+
+def dm_server_stats_get(srv) -> dict:
+    s = dm_server_stats()
+    _check(_lib.dm_server_stats_get(srv, ctypes.byref(s)), "dm_server_stats_get")
+    return {f: getattr(s, f) for f, _ in dm_server_stats._fields_}
+
+
+def dm_server_destroy(srv) -> None:
+    _check(_lib.dm_server_destroy(srv), "dm_server_destroy")
 
 
 def dm_score_topk(ctx, plan, k: int, n_p: int):
