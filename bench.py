@@ -51,7 +51,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--rates", default="250,500,1000,2000", help="c5: Poisson arrival rates (requests/s)")
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
     ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
@@ -166,9 +167,15 @@ WORKLOAD_C4 = ("C4 batched: heavy-hex 12x6 (V=431), 512 seeded patterns of 5-40 
                "subdivided 2xk grids), count + checksum, one persistent launch per step")
 
 
+WORKLOAD_C5 = ("C5 serving: Poisson arrivals of top-10 layout requests (patterns of 5-60 vertices, trees / "
+               "cycles / subdivided grids) over heavy-hex 4x6, grid 32x32 and random 3-regular V=2048, 8 slots")
+
+
 def wl_name(args):
     if args.workload == "c2":
         return WORKLOAD
+    if args.workload == "c5":
+        return WORKLOAD_C5
     if args.workload == "c4":
         return WORKLOAD_C4
     m, n = (int(x) for x in args.hh.split(","))
@@ -395,8 +402,10 @@ def run_c4(args):
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in ev]
         emb = int(counts.sum())
+        done = list(B.dm_batch_latency(ctx.h, len(plans)))  # completion of each pattern, last step
         return {"value": emb * len(ms) / (sum(ms) / 1e3), "ms_per_step": sum(ms) / len(ms),
-                "p50_ms_per_pattern": pct(ms, 0.5), "p99_ms_per_pattern": pct(ms, 0.99),
+                "p50_ms_per_pattern": pct(done, 0.5), "p99_ms_per_pattern": pct(done, 0.99),
+                "latency": "completion time of each pattern from the start of the batch (all arrive together)",
                 "launch": B.dm_batch_config(ctx.h), "embeddings_per_step": emb}, launches, ms
 
     paper_plans, paper_plan_ms = make(B.DM_ORDER_PAPER)
@@ -407,8 +416,14 @@ def run_c4(args):
         c, _ = B.dm_match(ctx.h, p, B.DM_COUNT)
         lat.append(1e3 * (time.perf_counter() - s0))
         plain_emb += c
-    plain = {"value": plain_emb / (sum(lat) / 1e3), "ms_total": sum(lat), "p50_ms_per_pattern": pct(lat, 0.5),
-             "p99_ms_per_pattern": pct(lat, 0.99), "plan_ms_total": paper_plan_ms}
+    done, acc = [], 0.0
+    for x in lat:  # the same arrival model as the batch: all patterns at once, served in order
+        acc += x
+        done.append(acc)
+    plain = {"value": plain_emb / (sum(lat) / 1e3), "ms_total": sum(lat), "p50_ms_per_pattern": pct(done, 0.5),
+             "p99_ms_per_pattern": pct(done, 0.99),
+             "latency": "completion time of each pattern when all arrive together and are served one by one",
+             "p50_service_ms": pct(lat, 0.5), "p99_service_ms": pct(lat, 0.99), "plan_ms_total": paper_plan_ms}
     bat, _, _ = batched(paper_plans)
     model = train_model(B, ctx, gid, g)
     learned_plans, learned_plan_ms = make(B.DM_ORDER_LEARNED)
@@ -434,8 +449,77 @@ def run_c4(args):
     return 0
 
 
+def run_c5(args):
+    """Serving: requests arrive as a Poisson process and are answered by the library's server
+    (continuous admission onto 8 slots by projected join memory); per rate, completed
+    requests/s, p50/p99 latency (arrival to answer) and the fraction rejected by the caps."""
+    import numpy as np
+    import threading as th
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2508_21287_gb300 import build
+    build.build()
+    from paper_2508_21287_gb300 import binding as B
+    from paper_2508_21287_gb300 import inputs as I
+    graphs = [I.lognormal_weights(I.heavy_hex(4, 6), seed=11), I.lognormal_weights(I.grid(32, 32), seed=12),
+              I.lognormal_weights(I.random_regular3(2048, 13), seed=13)]
+    srv = B.dm_server_create(local, n_slots=8, mem_budget_bytes=32 << 30, max_rows=4_000_000)
+    gids = [B.dm_server_load_graph(srv, g.n, g.row_ptr, g.col_idx, g.edge_err) for g in graphs]
+    rates = [float(x) for x in args.rates.split(",")]
+    n_req = 400
+
+    def make(seed0):
+        return [(i % 3, I.mixed_pattern(seed0 + i, 5, 60)) for i in range(n_req)]
+
+    for gi, p in make(900000)[:60]:  # warm-up: motif tables and indices in every slot
+        B.dm_server_wait(srv, B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10), 10, p.n)
+    sweep = []
+    with ClockSampler(local) as clk:
+        reqs = make(rank * 1000000)  # the same requests at every rate
+        for ri, lam in enumerate(rates):
+            gaps = np.random.default_rng(ri).exponential(1.0 / lam, n_req)
+            ids = [None] * n_req
+            t0 = time.perf_counter()
+
+            def feeder():
+                t = t0
+                for i, (gi, p) in enumerate(reqs):
+                    t += gaps[i]
+                    d = t - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    ids[i] = B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10)
+
+            f = th.Thread(target=feeder)
+            f.start()
+            f.join()
+            ans = [B.dm_server_wait(srv, ids[i], 10, reqs[i][1].n) for i in range(n_req)]
+            wall = time.perf_counter() - t0
+            ok = [a for a in ans if a["status"] == 0]
+            lat = sorted(a["latency_ms"] for a in ok)
+            pick = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
+            sweep.append({"rate": lam, "completed_per_s": len(ok) / wall, "p50_ms": pick(0.5), "p99_ms": pick(0.99),
+                          "rejected": sum(a["status"] == B.DM_E_CAPACITY for a in ans) / n_req,
+                          "failed": sum(a["status"] not in (0, B.DM_E_CAPACITY) for a in ans), "wall_s": wall})
+    B.dm_server_destroy(srv)
+    top = sweep[-1]
+    line = {"metric": "requests/sec", "value": top["completed_per_s"], "unit": "requests/s", "n_gpus": world,
+            "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_C5, "requests_per_rate": n_req, "slots": 8, "max_rows": 4_000_000,
+                       "pool_bytes": 32 << 30, "parallelism": "replicas"},
+            "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "rejected_fraction": top["rejected"],
+            "sweep": sweep, "clocks": clk.summary(), "e2e": None}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "c5" and args.impl != "reference":
+        return run_c5(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":

@@ -65,7 +65,7 @@ typedef int32_t dm_graph;
 /* ------------------------------------------------------------------ plan options ---- */
 #define DM_ORDER_PAPER 0      /* Sec. 3.2: largest motif first, first match found */
 #define DM_ORDER_HEURISTIC 1  /* greedy: smallest estimated intermediate table next */
-#define DM_ORDER_LEARNED 2    /* greedy on the trained cardinality model (falls back to heuristic if none) */
+#define DM_ORDER_LEARNED 2    /* cheapest of several candidate plans under the trained cardinality model (heuristic order if none) */
 
 #define DM_JOIN_AUTO 0
 #define DM_JOIN_HASH 1        /* probe a per-key index of the motif table (direct or hashed packed key) */
@@ -168,15 +168,26 @@ int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void 
 int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, int mode,
                    uint64_t *out_counts, uint64_t *out_checksums);
 
-/* Launch shape of the last dm_match_batch (tile rows per CTA step, root rows per work item,
- * CTAs of the persistent launch), as picked by the autotuner. */
-int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid);
+/* Launch shape of the last dm_match_batch, as picked by the autotuner: tile rows per CTA
+ * step, root rows per work item, CTAs of the persistent launch, and how many plans (those
+ * whose predicted largest table exceeds heavy_rows) ran step by step over the whole GPU
+ * after the persistent launch instead of inside it. */
+int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid,
+                    int32_t *n_stepwise, double *heavy_rows);
 
-/* Tuning knobs: autotune (1 = time the candidate launch shapes on the first dm_match_batch
- * of a new set of plans and keep the fastest), hash_load_factor (fill of two-key hash
- * indices, 0 < f <= 0.95; changing it rebuilds those indices). Plans made before a change
- * of the load factor must be made again. */
-int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor);
+/* Completion time of each plan of the last dm_match_batch (all plans taken to arrive
+ * together), in ms: for plans in the persistent launch, from the launch's start to the end
+ * of the plan's last work item (GPU global timer); for plans run step by step, from the
+ * start of the call to their end (host clock). n must equal that call's n_plans. */
+int dm_batch_latency(dm_ctx *ctx, double *out_ms, int32_t n);
+
+/* Tuning knobs: autotune (1 = time the candidate launch shapes and the split between the
+ * persistent launch and step-by-step execution on the first dm_match_batch of a new set of
+ * plans, and keep the fastest), hash_load_factor (fill of two-key hash indices,
+ * 0 < f <= 0.95; changing it rebuilds those indices; plans made before must be made again),
+ * heavy_rows (without autotuning: plans whose predicted largest table exceeds it run step by
+ * step; <= 0 = none). */
+int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor, double heavy_rows);
 
 /* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,
  * row) key, in that order. out_rows: k x n_p int32 host buffer; out_scores: k floats
@@ -195,9 +206,10 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
 /* No counterpart in the paper (which notes that motif choice and ordering matter, Sec. 5.2):
  * a 3-layer MLP (32 -> 128 -> 128 -> 1, ReLU; BF16 tensor-core matmuls with FP32
  * accumulation) predicts, for a candidate join step, the log growth of the intermediate
- * table, log(1 + rows after) - log(1 + rows before). DM_ORDER_LEARNED plans pick, at each
- * decomposition step, the candidate slice with the smallest predicted growth per newly
- * mapped vertex; without a trained model they fall back to the independence heuristic.
+ * table, log(1 + rows after) - log(1 + rows before). DM_ORDER_LEARNED plans are the cheapest,
+ * under the model's predicted cardinalities, of several candidate decompositions (the
+ * paper's rule and the greedy heuristic order, with the given motif set and with larger
+ * motifs typical of the topology); without a trained model they use the heuristic order.
  * The output set never depends on the order. Feature vectors are DM_MODEL_FEATURES floats
  * (dm_plan_estimates / dm_step_log give them); parameters are FP32, flat, in the order
  * W1[128][32] b1[128] W2[128][128] b2[128] w3[128] b3, followed by the 32 input means and
@@ -229,6 +241,11 @@ int dm_model_set_weights(dm_ctx *ctx, const float *w, int64_t n_floats);
 /* The (features, observed log growth) samples logged by every dm_match so far: up to cap of
  * them are copied out, out_n receives how many exist, clear != 0 empties the log. */
 int dm_step_log(dm_ctx *ctx, float *feats, float *targets, int64_t cap, int64_t *out_n, int clear);
+
+/* Predicted cost of a plan (bytes its joins write, plus a fixed per-step overhead) and its
+ * largest predicted intermediate table, from the trained model for DM_ORDER_LEARNED plans
+ * and from the independence heuristic otherwise. */
+int dm_plan_cost(const dm_plan_t *plan, double *cost, double *max_rows);
 
 /* The model inputs of a plan's steps (cap rows of DM_MODEL_FEATURES) and the independence
  * heuristic's log growth of each; returns the number of steps. */

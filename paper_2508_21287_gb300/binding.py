@@ -100,8 +100,9 @@ _SIGS = {
     "dm_last_error": (ctypes.c_char_p, [_vp]),
     "dm_decompose": (_i32, [_i32, _i32p, _i32p, _i32p, _i32, _i32, _i32p, _i32]),
     "dm_sort_rows_static": (ctypes.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp]),
-    "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p]),
-    "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+    "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p, _i32p, ctypes.POINTER(ctypes.c_double)]),
+    "dm_batch_latency": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
+    "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "dm_model_init": (ctypes.c_int, [_vp, _u64]),
     "dm_model_train": (ctypes.c_int, [_vp, _fp, _fp, _i32, _i32, _i32, ctypes.c_float, _u64, _fp]),
     "dm_model_predict": (ctypes.c_int, [_vp, _fp, _i32, _fp]),
@@ -110,6 +111,7 @@ _SIGS = {
     "dm_model_set_weights": (ctypes.c_int, [_vp, _fp, _i64]),
     "dm_step_log": (ctypes.c_int, [_vp, _fp, _fp, _i64, ctypes.POINTER(_i64), ctypes.c_int]),
     "dm_plan_estimates": (_i32, [_vp, _fp, _fp, _i32]),
+    "dm_plan_cost": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "dm_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(dm_server_opts)]),
     "dm_server_load_graph": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32p]),
     "dm_server_set_model": (ctypes.c_int, [_vp, _fp, _i64]),
@@ -306,13 +308,23 @@ def dm_match_batch(ctx, plans, mode: int = DM_COUNT):
 
 
 def dm_batch_config(ctx) -> dict:
-    tr, ch, gr = _i32(), _i64(), _i32()
-    _check(_lib.dm_batch_config(ctx, ctypes.byref(tr), ctypes.byref(ch), ctypes.byref(gr)), "dm_batch_config", ctx)
-    return {"tile_rows": tr.value, "root_chunk": ch.value, "grid": gr.value}
+    tr, ch, gr, nh, hv = _i32(), _i64(), _i32(), _i32(), ctypes.c_double()
+    _check(_lib.dm_batch_config(ctx, ctypes.byref(tr), ctypes.byref(ch), ctypes.byref(gr), ctypes.byref(nh),
+                                ctypes.byref(hv)), "dm_batch_config", ctx)
+    return {"tile_rows": tr.value, "root_chunk": ch.value, "grid": gr.value, "stepwise_plans": nh.value,
+            "heavy_rows": hv.value if hv.value < 1e300 else None}
 
 
-def dm_set_tuning(ctx, autotune: bool = True, hash_load_factor: float = 0.5) -> None:
-    _check(_lib.dm_set_tuning(ctx, int(bool(autotune)), float(hash_load_factor)), "dm_set_tuning", ctx)
+def dm_batch_latency(ctx, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float64)
+    _check(_lib.dm_batch_latency(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n)),
+           "dm_batch_latency", ctx)
+    return out
+
+
+def dm_set_tuning(ctx, autotune: bool = True, hash_load_factor: float = 0.5, heavy_rows: float = 0.0) -> None:
+    _check(_lib.dm_set_tuning(ctx, int(bool(autotune)), float(hash_load_factor), float(heavy_rows)),
+           "dm_set_tuning", ctx)
 
 
 DM_MODEL_FEATURES = 32
@@ -378,6 +390,12 @@ def dm_step_log(ctx, clear: bool = False):
     t = np.zeros(n.value, dtype=np.float32)
     _check(_lib.dm_step_log(ctx, _pf(f), _pf(t), n.value, ctypes.byref(n), int(bool(clear))), "dm_step_log", ctx)
     return f, t
+
+
+def dm_plan_cost(plan):
+    c, m = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.dm_plan_cost(plan, ctypes.byref(c), ctypes.byref(m)), "dm_plan_cost")
+    return c.value, m.value
 
 
 def dm_plan_estimates(plan):

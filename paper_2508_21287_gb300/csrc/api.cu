@@ -84,6 +84,8 @@ struct dm_ctx {
   std::vector<float> log_feat, log_target;
   int autotune = 1;
   double hash_lf = 0.5;               // load factor of two-key hash indices
+  double heavy_rows = 1e300;          // plans predicted to hold more rows run step by step
+  std::vector<double> batch_latency;  // per plan, ms from the start of the last dm_match_batch
 };
 
 struct dm_plan_s {
@@ -1036,9 +1038,11 @@ int ensure_motif(dm_ctx *c, DevGraph *g, int id) {
 // and the CUDA graph that replays memsets + launch + result copy.
 struct BatchState {
   std::vector<const dm_plan_t *> key;
-  double hash_lf = 0;
+  double hash_lf = 0, heavy_rows = 0;
+  std::vector<int32_t> light, heavy;  // plans in the persistent launch / run step by step
   int TR = 64;
   int64_t root_chunk = 16;
+  void *d_left0 = nullptr;            // items per plan (copied into the live counters each run)
   dmk::BatchParams prm{};
   int grid = 0;
   void *d_args = nullptr, *d_plans = nullptr, *d_items = nullptr, *d_work = nullptr, *scratch = nullptr;
@@ -1060,13 +1064,14 @@ void batch_release(dm_ctx *c, BatchState *b) {
   cudaFree(b->d_plans);
   cudaFree(b->d_items);
   cudaFree(b->d_work);
+  cudaFree(b->d_left0);
   cudaFree(b->scratch);
   if (b->h_out) cudaFreeHost(b->h_out);
   delete b;
 }
 
 int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
-                BatchState **out);
+                double heavy_rows, BatchState **out);
 
 DevGraph *get_graph(dm_ctx *c, dm_graph g) {
   if (!c || g < 0 || g >= (int)c->graphs.size()) return nullptr;
@@ -1074,19 +1079,26 @@ DevGraph *get_graph(dm_ctx *c, dm_graph g) {
 }
 
 int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
-                BatchState **out) {
+                double heavy_rows, BatchState **out) {
   std::unique_ptr<BatchState> b(new BatchState());
   b->key.assign(plans, plans + n);
   b->hash_lf = c->hash_lf;
+  b->heavy_rows = heavy_rows;
   b->TR = TR;
   b->root_chunk = root_chunk;
   b->n_plans = n;
+  std::vector<uint64_t> items_per(n, 0);
   std::vector<JoinArgs> args;
   std::vector<dmk::BatchPlan> bplans(n);
   std::vector<std::pair<double, dmk::BatchItem>> items;
   std::vector<int64_t> cap(MAXSTEPS, 0), maxw(MAXSTEPS, 0);
   int ws_max = 1;
   for (int32_t i = 0; i < n; i++) {
+    if (plans[i]->p.pred_max_rows > heavy_rows) {  // runs step by step after the launch
+      b->heavy.push_back(i);
+      continue;
+    }
+    b->light.push_back(i);
     Exec ex;
     ex.c = c;
     ex.g = g;
@@ -1120,6 +1132,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
       it.lo = lo;
       it.hi = std::min(n0, lo + root_chunk);
       items.push_back({cost / std::max<double>(1.0, (double)(n0 + root_chunk - 1) / root_chunk), it});
+      items_per[i]++;
     }
   }
   // expensive chunks first: the tail of the persistent loop is made of cheap ones
@@ -1152,15 +1165,18 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   RET(up(&b->d_args, args.data(), sizeof(JoinArgs) * args.size()));
   RET(up(&b->d_plans, bplans.data(), sizeof(dmk::BatchPlan) * bplans.size()));
   RET(up(&b->d_items, hitems.data(), sizeof(dmk::BatchItem) * hitems.size()));
-  if (cudaMalloc(&b->d_work, sizeof(unsigned long long) * (2 + 2 * (size_t)n)) != cudaSuccess) {
+  // work counter, overflow flag, (count, checksum) per plan, items left per plan, done times,
+  // start time
+  if (cudaMalloc(&b->d_work, sizeof(unsigned long long) * (3 + 4 * (size_t)n)) != cudaSuccess) {
     cudaGetLastError();
     return DM_E_NOMEM;
   }
+  RET(up(&b->d_left0, items_per.data(), sizeof(uint64_t) * n));
   if (cudaMalloc(&b->scratch, std::max<size_t>(16, (size_t)b->grid * P.cta_bytes)) != cudaSuccess) {
     cudaGetLastError();
     return DM_E_NOMEM;
   }
-  if (cudaMallocHost(&b->h_out, sizeof(unsigned long long) * (2 + 2 * (size_t)n)) != cudaSuccess) return DM_E_NOMEM;
+  if (cudaMallocHost(&b->h_out, sizeof(unsigned long long) * (3 + 4 * (size_t)n)) != cudaSuccess) return DM_E_NOMEM;
   unsigned long long *work = (unsigned long long *)b->d_work;
   P.args = (const JoinArgs *)b->d_args;
   P.plans = (const dmk::BatchPlan *)b->d_plans;
@@ -1168,6 +1184,9 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   P.next_item = work;
   P.ovf = work + 1;
   P.out = work + 2;
+  P.plan_left = work + 2 + 2 * n;
+  P.plan_done = work + 2 + 3 * n;
+  P.start_ns = work + 2 + 4 * n;
   P.scratch = (unsigned char *)b->scratch;
   *out = b.release();
   return DM_OK;
@@ -1175,29 +1194,57 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
 
 // One execution of a built batch: reset counters, run the persistent kernel, copy the results
 // back. The sequence is captured once into a CUDA graph and replayed afterwards.
-int batch_run(dm_ctx *c, BatchState *b) {
-  size_t wbytes = sizeof(unsigned long long) * (2 + 2 * (size_t)b->n_plans);
-  if (!b->exec) {
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaMemsetAsync(b->d_work, 0, wbytes, cs);
-      dmk::launch_batch(b->prm, b->grid, cs);
-      cudaMemcpyAsync(b->h_out, b->d_work, wbytes, cudaMemcpyDeviceToHost, cs);
-      e = cudaStreamEndCapture(cs, &b->graph);
+int batch_run(dm_ctx *c, DevGraph *g, BatchState *b) {
+  const size_t n = (size_t)b->n_plans;
+  size_t wbytes = sizeof(unsigned long long) * (3 + 4 * n);
+  auto t0 = std::chrono::steady_clock::now();
+  c->batch_latency.assign(n, 0.0);
+  if (!b->light.empty()) {
+    if (!b->exec) {
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long) * (2 + 2 * n), cs);
+        cudaMemcpyAsync((unsigned long long *)b->d_work + 2 + 2 * n, b->d_left0, sizeof(unsigned long long) * n,
+                        cudaMemcpyDeviceToDevice, cs);
+        dmk::launch_batch(b->prm, b->grid, cs);
+        cudaMemcpyAsync(b->h_out, b->d_work, wbytes, cudaMemcpyDeviceToHost, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batch graph capture");
+    } else {
+      dmk::g_launches++;  // the replayed graph holds one launch of the batch kernel
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return cuda_fail(c, e, "batch graph capture");
-  } else {
-    dmk::g_launches++;  // the replayed graph holds one launch of the batch kernel
+    CK(cudaGraphLaunch(b->exec, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (b->h_out[1]) {
+      c->last_error = "batch level buffer overflow";
+      return DM_E_CAPACITY;
+    }
+    // GPU global-timer offset of each plan's last item from the start of the launch
+    unsigned long long st = b->h_out[2 + 4 * n];
+    for (int32_t i : b->light) {
+      unsigned long long d = b->h_out[2 + 3 * n + i];
+      c->batch_latency[i] = d > st ? (double)(d - st) * 1e-6 : 0.0;
+    }
   }
-  CK(cudaGraphLaunch(b->exec, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (b->h_out[1]) {
-    c->last_error = "batch level buffer overflow";
-    return DM_E_CAPACITY;
+  for (int32_t i : b->heavy) {  // expensive plans: every step over the whole GPU
+    Exec ex;
+    ex.c = c;
+    ex.g = g;
+    ex.p = &b->key[i]->p;
+    ex.mode = DM_COUNT;
+    ex.use_qerr = false;
+    c->inflight = 0;
+    dm_stats saved = c->stats;
+    RET(ex.run());
+    c->stats = saved;
+    b->h_out[2 + 2 * i] = ex.count;
+    b->h_out[3 + 2 * i] = ex.checksum;
+    c->batch_latency[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return DM_OK;
 }
@@ -1282,6 +1329,33 @@ int model_predict_plan(void *self, const float *feats, int n, float *out) {
   normalise(c, x.data(), n, xn);
   RET(model_run(c, xn.data(), nullptr, n, y.data(), nullptr, nullptr));
   for (int i = 0; i < n; i++) out[i] = feats[(size_t)i * NFEAT] + y[i];
+  return DM_OK;
+}
+
+// Predicted cost of a plan: bytes of every intermediate table it writes (rows from the chain
+// of predicted log growths, model or heuristic) plus 64 KiB per step for launch and barrier
+// overheads; and its largest predicted table.
+int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, double *cost, double *max_rows) {
+  const int n = (int)steps.size();
+  std::vector<float> x((size_t)std::max(1, n) * NFEAT), growth(std::max(1, n));
+  for (int j = 0; j < n; j++) {
+    model_input(steps[j].feat, &x[(size_t)j * NFEAT]);
+    growth[j] = x[(size_t)j * NFEAT + 22];
+  }
+  if (use_model && n > 0) {
+    std::vector<float> xn;
+    normalise(c, x.data(), n, xn);
+    RET(model_run(c, xn.data(), nullptr, n, growth.data(), nullptr, nullptr));
+  }
+  double lr = 0, total = 0, mx = 0;
+  for (int j = 0; j < n; j++) {
+    lr += growth[j];
+    double rows = exp(std::min(60.0, std::max(-60.0, lr)));
+    mx = std::max(mx, rows);
+    total += rows * (4.0 * steps[j].w_out + 4.0) + 65536.0;
+  }
+  *cost = total;
+  *max_rows = mx;
   return DM_OK;
 }
 
@@ -1527,8 +1601,48 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
     gs.motifs.push_back({id, g->motifs.at(id).n});
   }
   if (n_p == 1) RET(ensure_motif(c, g, MOTIF_VERTEX));
-  CardModelFn model = (p.order == DM_ORDER_LEARNED && c->m_trained) ? model_predict_plan : nullptr;
-  RET(decompose(p, p.motifs, p.order, gs, model, c, &p.steps, p.col_vertex));
+  const bool learned = p.order == DM_ORDER_LEARNED && c->m_trained;
+  if (!learned) {
+    RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, nullptr, nullptr,
+                  &p.steps, p.col_vertex));
+    RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows));
+  } else {
+    // The trained model picks the plan: candidate decompositions (the paper's rule and the
+    // greedy heuristic, over the motif set and over topology-typical larger motifs) are
+    // costed with the model's per-step cardinalities and the cheapest is kept.
+    std::vector<std::vector<int32_t>> sets{p.motifs};
+    std::vector<int32_t> extra;
+    if (!(opts && opts->motifs && opts->n_motifs > 0)) {
+      if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12)};
+      else if (g->max_deg == 4) extra = {DM_MOTIF_M6_2O, 6};
+      else extra = {4};
+    }
+    for (int id : extra) {
+      RET(ensure_motif(c, g, id));
+      gs.motifs.push_back({id, g->motifs.at(id).n});
+      std::vector<int32_t> set{id};
+      set.insert(set.end(), p.motifs.begin(), p.motifs.end());
+      sets.push_back(set);
+    }
+    double best = 1e308;
+    for (auto &set : sets)
+      for (int ord : {DM_ORDER_PAPER, DM_ORDER_HEURISTIC}) {
+        std::vector<StepSpec> steps;
+        int32_t colv[MAXW];
+        if (decompose(p, set, ord, gs, nullptr, nullptr, &steps, colv) != DM_OK) continue;
+        double cost, maxr;
+        RET(plan_cost(c, steps, true, &cost, &maxr));
+        if (cost < best) {
+          best = cost;
+          p.steps = steps;
+          memcpy(p.col_vertex, colv, sizeof(colv));
+          p.pred_cost = cost;
+          p.pred_max_rows = maxr;
+          p.motifs = set;
+        }
+      }
+    if (p.steps.empty()) return DM_E_INVAL;
+  }
   if ((int)p.steps.size() > DM_MAX_STEPS) return DM_E_CAPACITY;
   for (size_t j = 1; j < p.steps.size(); j++) {
     Index *ix;
@@ -1646,34 +1760,39 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
     c->batch = nullptr;
     int TR = 64;
     int64_t chunk = 16;
-    if (c->autotune) {  // time each launch shape once on this batch, keep the fastest
-      double best = 1e300;
-      const int trs[] = {32, 64, 128};
-      const int64_t chunks[] = {4, 16, 64};
-      for (int tr : trs)
-        for (int64_t ch : chunks) {
-          BatchState *t = nullptr;
-          int r = batch_build(c, g, plans, n_plans, tr, ch, &t);
-          if (r != DM_OK) {
-            batch_release(c, t);
-            continue;
-          }
+    double heavy = c->heavy_rows;
+    if (c->autotune) {  // time the candidate launch shapes on this batch, keep the fastest
+      auto trial = [&](int tr, int64_t ch, double hv, double *ms) {
+        BatchState *t = nullptr;
+        int r = batch_build(c, g, plans, n_plans, tr, ch, hv, &t);
+        if (r == DM_OK) {
           auto s0 = std::chrono::steady_clock::now();
-          r = batch_run(c, t);
-          double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s0).count();
-          batch_release(c, t);
-          if (r == DM_OK && ms < best) {
+          r = batch_run(c, g, t);
+          *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s0).count();
+        }
+        batch_release(c, t);
+        return r;
+      };
+      double best = 1e300, ms = 0;
+      for (int tr : {32, 64, 128})
+        for (int64_t ch : {4, 16, 64})
+          if (trial(tr, ch, heavy, &ms) == DM_OK && ms < best) {
             best = ms;
             TR = tr;
             chunk = ch;
           }
+      // then the split between the persistent launch and step-by-step execution
+      for (double hv : {1e300, 1048576.0, 262144.0, 65536.0, 16384.0})
+        if (trial(TR, chunk, hv, &ms) == DM_OK && ms < best) {
+          best = ms;
+          heavy = hv;
         }
     }
-    RET(batch_build(c, g, plans, n_plans, TR, chunk, &b));
+    RET(batch_build(c, g, plans, n_plans, TR, chunk, heavy, &b));
     b->tuned = c->autotune != 0;
     c->batch = b;
   }
-  RET(batch_run(c, b));
+  RET(batch_run(c, g, b));
   for (int32_t i = 0; i < n_plans; i++) {
     if (out_counts) out_counts[i] = b->h_out[2 + 2 * i];
     if (out_checksums) out_checksums[i] = b->h_out[3 + 2 * i];
@@ -1682,17 +1801,31 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
   return DM_OK;
 }
 
-int dm_batch_config(dm_ctx *c, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid) {
+int dm_batch_config(dm_ctx *c, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid, int32_t *n_stepwise,
+                    double *heavy_rows) {
   if (!c || !c->batch) return DM_E_INVAL;
   if (tile_rows) *tile_rows = c->batch->TR;
   if (root_chunk) *root_chunk = c->batch->root_chunk;
   if (grid) *grid = c->batch->grid;
+  if (n_stepwise) *n_stepwise = (int32_t)c->batch->heavy.size();
+  if (heavy_rows) *heavy_rows = c->batch->heavy_rows;
   return DM_OK;
 }
 
-int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor) {
+int dm_batch_latency(dm_ctx *c, double *out_ms, int32_t n) {
+  if (!c || !out_ms || n != (int32_t)c->batch_latency.size()) return DM_E_INVAL;
+  for (int32_t i = 0; i < n; i++) out_ms[i] = c->batch_latency[i];
+  return DM_OK;
+}
+
+int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor, double heavy_rows) {
   if (!c || hash_load_factor <= 0.0 || hash_load_factor > 0.95) return DM_E_INVAL;
   c->autotune = autotune;
+  c->heavy_rows = heavy_rows > 0 ? heavy_rows : 1e300;
+  if (c->batch) {  // the next batch is rebuilt under the new settings
+    batch_release(c, c->batch);
+    c->batch = nullptr;
+  }
   if (hash_load_factor != c->hash_lf) {
     c->hash_lf = hash_load_factor;
     for (DevGraph *g : c->graphs) {  // two-key indices are rebuilt at the new load factor
@@ -1948,6 +2081,13 @@ int dm_step_log(dm_ctx *c, float *feats, float *targets, int64_t cap, int64_t *o
     c->log_feat.clear();
     c->log_target.clear();
   }
+  return DM_OK;
+}
+
+int dm_plan_cost(const dm_plan_t *pl, double *cost, double *max_rows) {
+  if (!pl) return DM_E_INVAL;
+  if (cost) *cost = pl->p.pred_cost;
+  if (max_rows) *max_rows = pl->p.pred_max_rows;
   return DM_OK;
 }
 

@@ -18,6 +18,12 @@ namespace dmk {
 
 constexpr int BATCH_BLK = 256;
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void batch_tile(const JoinArgs &a, const JoinSmem &S, int TR, const int32_t *src,
                                            int nr, int64_t m0, int seedC, const TileOut &o, int *s_warp,
                                            unsigned long long *s_red, long long *s_base, unsigned long long &ar,
@@ -57,6 +63,7 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
   __shared__ int64_t n_lvl[MAXSTEPS], cur[MAXSTEPS];
 
   const JoinSmem S = join_smem(smem, P.TR, P.ws_max, BATCH_BLK * 4);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *P.start_ns = globaltimer_ns();
   unsigned char *mine = P.scratch + (int64_t)blockIdx.x * P.cta_bytes;
   TileOut o;
   o.out_next = nullptr;
@@ -122,6 +129,8 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
         atomicAdd(P.out + 2 * item.plan, tr);
         atomicAdd(P.out + 2 * item.plan + 1, ts);
       }
+      __threadfence();
+      if (atomicAdd(P.plan_left + item.plan, ~0ull) == 1ull) P.plan_done[item.plan] = globaltimer_ns();
     }
     __syncthreads();
   }

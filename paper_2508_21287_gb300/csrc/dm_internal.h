@@ -77,6 +77,8 @@ struct Plan {
   int32_t graph = -1;
   int32_t order = 0, join_algo = 0;
   int64_t chunk_rows = 0, max_rows = 0;
+  double pred_cost = 0;      // predicted bytes moved by the joins plus a per-step overhead
+  double pred_max_rows = 0;  // predicted largest intermediate table
 };
 
 // Decompose a pattern (Sec. 3.2). Returns 0 or a DM_E_* code.

@@ -101,6 +101,9 @@ struct BatchParams {
   int64_t lvl_cap[dmi::MAXSTEPS]; // rows level j can hold
   int TR;                         // rows per tile
   int ws_max;                     // odd shared-memory row stride covering every step
+  unsigned long long *plan_left;  // work items still open per plan (set before the launch)
+  unsigned long long *plan_done;  // GPU global-timer time at which each plan's last item ended
+  unsigned long long *start_ns;   // GPU global-timer time at the start of the launch
 };
 size_t batch_smem_bytes(int tile_rows, int ws_max);
 int batch_grid(int tile_rows, int ws_max, int num_sms);

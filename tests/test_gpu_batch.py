@@ -60,6 +60,13 @@ def test_batch_paths_and_patches(B):
         B.dm_set_tuning(ctx.h, False, 0.5)
         counts, sums, single = _run(B, ctx, gid, pats)
         _check(g, pats, counts, sums, single)
+        lat = B.dm_batch_latency(ctx.h, len(pats))
+        assert np.all(lat >= 0)
+        # the heaviest plans step by step, the rest in the persistent launch: same results
+        B.dm_set_tuning(ctx.h, False, 0.5, heavy_rows=5000.0)
+        counts2, sums2, _ = _run(B, ctx, gid, pats)
+        assert B.dm_batch_config(ctx.h)["stepwise_plans"] > 0
+        assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
 
 
 @pytest.mark.parametrize("lf", [0.25, 0.9])

@@ -75,7 +75,7 @@ def test_training_beats_the_heuristic(B):
         mae_heur = float(np.mean(np.abs(fh[:, 22] - th)))
         print(f"held-out log-growth MAE: model {mae_model:.3f} vs heuristic {mae_heur:.3f}")
         assert mae_model < mae_heur
-        # learned order: identical results (counts and checksums) to the oracle
+        # learned plans: identical results (counts and checksums) to the oracle
         got = _log_steps(B, ctx, gid, held[:40], B.DM_ORDER_LEARNED)
         for p, (c, s) in zip(held[:40], got):
             ref = oracle.enumerate(g, p, rows=False, threads=8)
