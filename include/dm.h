@@ -316,6 +316,12 @@ int dm_server_destroy(dm_server *s);
 int dm_sort_rows_static(const int32_t *rows_in, const float *scores_in, int64_t n, int32_t w,
                         int32_t bits, int32_t *rows_out, float *scores_out, void *stream);
 
+/* The distinct vertex sets covered by the embeddings (the image of each map, ids ascending),
+ * in ascending lexicographic order: automorphic copies of a layout collapse into one
+ * (|images| x |Aut(G_p)| = |Emb|). Writes min(cap, count) sets of n_p ints to out_sets
+ * (host, nullable) and the count to out_n. */
+int dm_images(dm_ctx *ctx, const dm_plan_t *plan, int32_t *out_sets, int64_t cap, int64_t *out_n);
+
 /* ------------------------------------------------------------------ statistics ------ */
 #define DM_MAX_STEPS 128
 typedef struct dm_stats {

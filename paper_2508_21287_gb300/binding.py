@@ -111,6 +111,7 @@ _SIGS = {
     "dm_model_set_weights": (ctypes.c_int, [_vp, _fp, _i64]),
     "dm_step_log": (ctypes.c_int, [_vp, _fp, _fp, _i64, ctypes.POINTER(_i64), ctypes.c_int]),
     "dm_plan_estimates": (_i32, [_vp, _fp, _fp, _i32]),
+    "dm_images": (ctypes.c_int, [_vp, _vp, _i32p, _i64, ctypes.POINTER(_i64)]),
     "dm_plan_cost": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "dm_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(dm_server_opts)]),
     "dm_server_load_graph": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32p]),
@@ -390,6 +391,15 @@ def dm_step_log(ctx, clear: bool = False):
     t = np.zeros(n.value, dtype=np.float32)
     _check(_lib.dm_step_log(ctx, _pf(f), _pf(t), n.value, ctypes.byref(n), int(bool(clear))), "dm_step_log", ctx)
     return f, t
+
+
+def dm_images(ctx, plan, n_p: int) -> np.ndarray:
+    n = _i64()
+    _check(_lib.dm_images(ctx, plan, None, 0, ctypes.byref(n)), "dm_images", ctx)
+    out = np.zeros((n.value, n_p), dtype=np.int32)
+    if n.value:
+        _check(_lib.dm_images(ctx, plan, _p32(out), n.value, ctypes.byref(n)), "dm_images", ctx)
+    return out
 
 
 def dm_plan_cost(plan):

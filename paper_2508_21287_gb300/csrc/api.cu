@@ -2103,6 +2103,56 @@ int dm_plan_estimates(const dm_plan_t *pl, float *feats, float *heur_growth, int
   return n;
 }
 
+int dm_images(dm_ctx *c, const dm_plan_t *pl, int32_t *out_sets, int64_t cap, int64_t *out_n) {
+  if (!c || !pl) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &pl->p;
+  ex.mode = DM_ALL;
+  ex.use_qerr = false;
+  ex.chunk_rows = pl->p.chunk_rows;
+  ex.max_rows = pl->p.max_rows;
+  c->inflight = 0;
+  CollectSink sink;
+  ex.sink = &sink;
+  RET(ex.run());
+  DevTable t;
+  RET(sink.concat(c, pl->p.n_p, false, &t));
+  const int64_t n = t.n;
+  const int32_t w = t.w;
+  int64_t m = 0;
+  if (n > 0) {
+    CK(dmk::images_prepare(t.rows, n, w, c->stream));
+    RET(sort_canonical(c, t, graph_bits(g)));
+    int32_t *flag = nullptr, *uniq = nullptr;
+    int64_t *pos = nullptr, *tmp = nullptr;
+    RET(dalloc_t(c, &flag, n));
+    RET(dalloc_t(c, &pos, n + 1));
+    RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(n)));
+    RET(dalloc_t(c, &uniq, (size_t)n * w));
+    CK(dmk::unique_rows(t.rows, n, w, flag, pos, tmp, uniq, c->stream));
+    CK(cudaMemcpyAsync(&m, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (out_sets && cap > 0 && m > 0)
+      CK(cudaMemcpyAsync(out_sets, uniq, sizeof(int32_t) * std::min(cap, m) * w, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, flag);
+    dfree(c, pos);
+    dfree(c, tmp);
+    dfree(c, uniq);
+  }
+  free_table(c, t);
+  if (out_n) *out_n = m;
+  finish_stats(c, t0);
+  return DM_OK;
+}
+
 int dm_get_stats(dm_ctx *c, dm_stats *out) {
   if (!c || !out) return DM_E_INVAL;
   *out = c->stats;

@@ -77,6 +77,13 @@ int64_t topk_tmp_bytes(int64_t n);
 cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t w, int32_t k, void *tmp,
                         int32_t *orows, float *osc, cudaStream_t s);
 
+// Images (sort.cu): sort the ids inside each row in place; then, on canonically sorted rows,
+// keep the first row of every run of equal rows (pos[n] receives the number kept; flag holds n
+// ints, pos n + 1, tmp scan_tmp_elems(n)).
+cudaError_t images_prepare(int32_t *rows, int64_t n, int32_t w, cudaStream_t s);
+cudaError_t unique_rows(const int32_t *rows, int64_t n, int32_t w, int32_t *flag, int64_t *pos, int64_t *tmp,
+                        int32_t *out, cudaStream_t s);
+
 // Persistent batch kernel (batch.cu).
 struct BatchPlan {
   int32_t n_steps;

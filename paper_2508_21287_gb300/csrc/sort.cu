@@ -148,6 +148,66 @@ cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ images (dedup) -----
+// Sort the ids inside every row (the row becomes its vertex set), one thread per row.
+__global__ void k_sort_within_rows(int32_t *rows, int64_t n, int32_t w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t *r = rows + i * w;
+    for (int a = 1; a < w; a++) {  // insertion sort: rows are at most 64 ids
+      int32_t x = r[a];
+      int b = a - 1;
+      while (b >= 0 && r[b] > x) {
+        r[b + 1] = r[b];
+        b--;
+      }
+      r[b + 1] = x;
+    }
+  }
+}
+
+// flag[i] = 1 when sorted row i differs from row i - 1 (first of its run).
+__global__ void k_first_of_run(const int32_t *rows, int64_t n, int32_t w, int32_t *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int f = i == 0;
+    if (!f) {
+      const int32_t *a = rows + i * w, *b = a - w;
+      for (int c = 0; c < w && !f; c++) f = a[c] != b[c];
+    }
+    flag[i] = f;
+  }
+}
+
+// Copy the flagged rows to their scanned positions (order kept).
+__global__ void k_compact_rows(const int32_t *rows, int64_t n, int32_t w, const int32_t *flag, const int64_t *pos,
+                               int32_t *out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / w;
+    if (flag[i]) out[pos[i] * w + (e - i * w)] = rows[e];
+  }
+}
+
+cudaError_t images_prepare(int32_t *rows, int64_t n, int32_t w, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256 > 16384 ? 16384 : (n + 255) / 256);
+  g_launches++;
+  k_sort_within_rows<<<grid, 256, 0, s>>>(rows, n, w);
+  return cudaGetLastError();
+}
+
+cudaError_t unique_rows(const int32_t *rows, int64_t n, int32_t w, int32_t *flag, int64_t *pos, int64_t *tmp,
+                        int32_t *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)((n + 255) / 256 > 16384 ? 16384 : (n + 255) / 256);
+  k_first_of_run<<<grid, 256, 0, s>>>(rows, n, w, flag);
+  cudaError_t e = scan_i32(flag, pos, n, tmp, s);
+  if (e != cudaSuccess) return e;
+  int64_t ne = n * w;
+  int g2 = (int)((ne + 255) / 256 > 16384 ? 16384 : (ne + 255) / 256);
+  k_compact_rows<<<g2, 256, 0, s>>>(rows, n, w, flag, pos, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ top-k --------------
 constexpr int TK_BLK = 512;
 constexpr int TK_TILE = 2048;

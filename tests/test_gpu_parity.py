@@ -267,6 +267,19 @@ def test_relabelled_data_graph(ctx):
     _rows_equal(mapped, b)
 
 
+# ------------------------------------------------------------------ images (dedup) ---------
+@pytest.mark.parametrize("pat", [I.path(6), I.cycle(12), I.star(3), I.random_tree(9, 4), I.grid(2, 3)])
+def test_images_dedup(ctx, B, pat):
+    g = I.grid(7, 7) if pat.name == "grid2x3" else I.heavy_hex(3, 4)
+    gid = ctx.load(g)
+    plan = ctx.plan(gid, pat)
+    got = B.dm_images(ctx.h, plan.h, pat.n)
+    ref = oracle.enumerate(g, pat)
+    want = oracle.images(ref.rows)
+    _rows_equal(got, want)
+    assert len(got) * oracle.automorphisms(pat) == ref.count
+
+
 # ------------------------------------------------------------------ edge cases -------------
 def test_edge_cases(ctx, B):
     g = I.lognormal_weights(I.grid(4, 4), seed=1)
