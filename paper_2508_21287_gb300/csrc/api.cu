@@ -493,9 +493,9 @@ struct Exec {
       a.N = in.n;
     }
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
-    int grid = dmk::join_grid(a, st[j].tile_rows, c->num_sms);
+    int grid = dmk::wjoin_grid(a, c->num_sms);
     if (c->timing) CK(cudaEventRecord(c->ev0, c->stream));
-    CK(dmk::launch_join(a, grid, st[j].tile_rows, c->stream));
+    CK(dmk::launch_wjoin(a, grid, c->stream));
     if (c->timing) CK(cudaEventRecord(c->ev1, c->stream));
     RET(read_ctr(c));
     if (c->h_ctr[CTR_OVF]) {
@@ -651,8 +651,8 @@ struct Exec {
         a.n_dev = c->d_ctr_steps + (size_t)(j - 1) * CTR_N + CTR_ROWS;
         a.in_cap = prev_cap;
       }
-      int grid = dmk::join_grid(a, st[j].tile_rows, c->num_sms);
-      CK(dmk::launch_join(a, grid, st[j].tile_rows, c->stream));
+      int grid = dmk::wjoin_grid(a, c->num_sms);
+      CK(dmk::launch_wjoin(a, grid, c->stream));
       prev_rows = orows;
       prev_score = a.outs;
       prev_cap = cap;

@@ -30,18 +30,18 @@ __device__ __forceinline__ void batch_tile(const JoinArgs &a, const JoinSmem &S,
                                            unsigned long long &as, unsigned long long &ac) {
   if (a.mode == 1) {
     if (a.n_new <= 1)
-      join_tile<BATCH_BLK, 1, 4, 1>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, 1, 4, 1>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
     else if (a.n_new <= 4)
-      join_tile<BATCH_BLK, 4, 4, 1>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, 4, 4, 1>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
     else
-      join_tile<BATCH_BLK, MAXM, 1, 1>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, MAXM, 1, 1>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
   } else {
     if (a.n_new <= 1)
-      join_tile<BATCH_BLK, 1, 4, 0>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, 1, 4, 0>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
     else if (a.n_new <= 4)
-      join_tile<BATCH_BLK, 4, 4, 0>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, 4, 4, 0>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
     else
-      join_tile<BATCH_BLK, MAXM, 1, 0>(a, S, TR, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
+      join_tile<BATCH_BLK, MAXM, 1, 0>(a, S, TR, 0, false, src, nullptr, nr, m0, seedC, o, s_warp, s_red, s_base, ar, as, ac);
   }
 }
 
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
   __shared__ long long s_item;
   __shared__ int64_t n_lvl[MAXSTEPS], cur[MAXSTEPS];
 
-  const JoinSmem S = join_smem(smem, P.TR, P.ws_max, BATCH_BLK * 4);
+  const JoinSmem S = join_smem(smem, P.TR, P.ws_max, BATCH_BLK * 4, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.start_ns = globaltimer_ns();
   unsigned char *mine = P.scratch + (int64_t)blockIdx.x * P.cta_bytes;
   TileOut o;
@@ -137,12 +137,8 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
 }
 
 size_t batch_smem_bytes(int tile_rows, int ws_max) {
-  size_t b = (size_t)tile_rows * ws_max * 4;
-  b = (b + 15) / 16 * 16;
-  b += (size_t)tile_rows * 16 + (size_t)tile_rows * 4 * 2 + (size_t)(tile_rows + 1) * 4;
-  b = (b + 15) / 16 * 16;
-  b += (size_t)BATCH_BLK * 4 * 8 + (size_t)BATCH_BLK * 4 * 4;
-  return b;
+  size_t offs[7];
+  return join_smem_layout(tile_rows, ws_max, BATCH_BLK * 4, 1, offs);
 }
 
 int batch_grid(int tile_rows, int ws_max, int num_sms) {

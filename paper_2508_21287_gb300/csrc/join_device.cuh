@@ -3,13 +3,15 @@
 // (k_join, kernels.cu) and the persistent batch kernel (batch.cu).
 //
 // A block stages up to TR rows of R in shared memory (odd row stride: conflict-free column
-// reads across rows), computes a 128-bit signature of each row's vertex ids, looks up each
-// row's key group in the motif index, and scans the group sizes into a candidate range. The
-// candidates are then processed in rounds of BLK * CPT: each thread evaluates CPT candidates
-// (extra key equalities, injectivity against the row via the signature, back-edges in the
-// adjacency bitmap, FP32 score); survivors are compacted with a block scan, their output range
-// is reserved once per round, and the block writes the rows element by element so that
-// consecutive threads store consecutive words.
+// reads across rows; the per-step kernel prefetches the next tile with cp.async while it
+// works on the current one), computes a 256-bit two-hash signature of each row's vertex ids,
+// looks up each row's key group in the motif index, and scans the group sizes into a
+// candidate range. The candidates are then processed in rounds of BLK * CPT: each thread
+// first issues the motif-row loads of its CPT candidates, then checks them (extra key
+// equalities, injectivity against the row -- a full scan only when both signature bits of a
+// new vertex are set --, back-edges in the adjacency bitmap, FP32 score); survivors are
+// compacted with a block scan, their output range is reserved once per round, and the block
+// writes the rows element by element so that consecutive threads store consecutive words.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -138,37 +140,89 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x
   return t;  // valid in thread 0
 }
 
-// 7-bit position of a vertex id in the 128-bit row signature.
-__device__ __forceinline__ unsigned sig_bit(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> 25; }
+// Two positions of a vertex id in the 256-bit row signature (independent multiplicative hashes).
+__device__ __forceinline__ unsigned sig_h1(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> 24; }
+__device__ __forceinline__ unsigned sig_h2(int32_t v) { return ((uint32_t)v * 0x85EBCA77u) >> 24; }
 
 struct JoinSmem {
-  int32_t *tile;
-  unsigned long long *sig;
-  float *tile_s;
+  int32_t *tile_buf[2];  // R tiles (two for the prefetching per-step kernel)
+  float *ts_buf[2];
+  unsigned long long *sig;  // 4 words per row
   int32_t *gstart, *goff;
   int32_t *surv_r, *surv_m;
   int32_t *cand_row;
+  int16_t *code;  // per output position: working column (< 0x100: from the R row) or 0x100 | motif position
 };
 
-__device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int ws, int BLKCPT) {
-  JoinSmem m;
+__host__ __device__ __forceinline__ size_t join_smem_layout(int TR, int ws, int BLKCPT, int nbuf, size_t *offs) {
   size_t off = 0;
-  m.tile = (int32_t *)(smem + off);
-  off += (size_t)TR * ws * 4;
+  for (int b = 0; b < 2; b++) {
+    offs[b] = off;
+    if (b < nbuf) off += ((size_t)TR * ws * 4 + 15) / 16 * 16;
+  }
+  for (int b = 0; b < 2; b++) {
+    offs[2 + b] = off;
+    if (b < nbuf) off += ((size_t)TR * 4 + 15) / 16 * 16;
+  }
+  offs[4] = off;  // signatures
+  off += (size_t)TR * 32;
+  offs[5] = off;  // group starts, offsets
+  off += (size_t)TR * 4 + (size_t)(TR + 1) * 4;
   off = (off + 15) / 16 * 16;
-  m.sig = (unsigned long long *)(smem + off);
-  off += (size_t)TR * 16;
-  m.tile_s = (float *)(smem + off);
-  off += (size_t)TR * 4;
-  m.gstart = (int32_t *)(smem + off);
-  off += (size_t)TR * 4;
-  m.goff = (int32_t *)(smem + off);
-  off += (size_t)(TR + 1) * 4;
-  off = (off + 15) / 16 * 16;
-  m.surv_r = (int32_t *)(smem + off);
+  offs[6] = off;  // survivors, candidate rows, codes
+  off += (size_t)BLKCPT * 4 * 3 + (size_t)MAXW * 2;
+  return (off + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int ws, int BLKCPT, int nbuf) {
+  size_t o[7];
+  join_smem_layout(TR, ws, BLKCPT, nbuf, o);
+  JoinSmem m;
+  m.tile_buf[0] = (int32_t *)(smem + o[0]);
+  m.tile_buf[1] = (int32_t *)(smem + (nbuf > 1 ? o[1] : o[0]));
+  m.ts_buf[0] = (float *)(smem + o[2]);
+  m.ts_buf[1] = (float *)(smem + (nbuf > 1 ? o[3] : o[2]));
+  m.sig = (unsigned long long *)(smem + o[4]);
+  m.gstart = (int32_t *)(smem + o[5]);
+  m.goff = m.gstart + TR;
+  m.surv_r = (int32_t *)(smem + o[6]);
   m.surv_m = m.surv_r + BLKCPT;
   m.cand_row = m.surv_m + BLKCPT;
+  m.code = (int16_t *)(m.cand_row + BLKCPT);
   return m;
+}
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Copy nr rows (width w) from src into a shared tile of row stride ws, and their scores.
+// ASYNC: with cp.async (the caller commits and waits); else with plain loads and stores.
+template <int BLK, bool ASYNC>
+__device__ __forceinline__ void load_tile(int32_t *tile, float *ts, const int32_t *src, const float *srcs, int nr,
+                                          int w) {
+  const int ws = w | 1;
+  const int ne = nr * w;
+  const int dr = BLK / w, dc = BLK % w;
+  int r = threadIdx.x / w, c = threadIdx.x % w;  // element e = r * w + c, advanced with carry
+  for (int e = threadIdx.x; e < ne; e += BLK) {
+    if (ASYNC) cp_async4(tile + r * ws + c, src + e);
+    else tile[r * ws + c] = __ldg(src + e);
+    r += dr;
+    c += dc;
+    if (c >= w) {
+      c -= w;
+      r++;
+    }
+  }
+  if (srcs)
+    for (int i = threadIdx.x; i < nr; i += BLK) {
+      if (ASYNC) cp_async4(ts + i, srcs + i);
+      else ts[i] = __ldg(srcs + i);
+    }
 }
 
 // Value of working column `col` of the joined row (R row `rrow`, motif row `trow`).
@@ -176,27 +230,23 @@ __device__ __forceinline__ int32_t join_value(const JoinArgs &a, const int32_t *
   return col < a.w ? rrow[col] : __ldg(trow + a.new_mpos[col - a.w]);
 }
 
-// Join, filter and score one candidate (R row r of the tile, motif row m).
+// Join, filter and score one candidate (R row r of the tile, motif row m) whose new vertices
+// nv were loaded beforehand.
 template <int MAXNEW>
-__device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, int ws, bool seed, int r, int64_t m,
-                                          float &sc) {
-  const int32_t *rrow = S.tile + r * ws;
-  const int32_t *trow = a.ix.rows + m * a.ix.mw;
+__device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S, const int32_t *tile, const float *ts,
+                                           int ws, bool seed, int r, int m, const int32_t (&nv)[MAXNEW], float &sc) {
+  const int32_t *rrow = tile + r * ws;
+  const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
   bool ok = true;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
-  int32_t nv[MAXNEW];
-#pragma unroll
-  for (int i = 0; i < MAXNEW; i++)
-    if (i < a.n_new) nv[i] = __ldg(trow + a.new_mpos[i]);
   if (ok && !seed) {  // FilterOverlappingNodes: new vertices must not repeat a mapped one
-    const unsigned long long s0 = S.sig[2 * r], s1 = S.sig[2 * r + 1];
+    const unsigned long long *sg = S.sig + 4 * r;
 #pragma unroll
     for (int i = 0; i < MAXNEW; i++) {
-      if (i < a.n_new) {
-        unsigned b = sig_bit(nv[i]);
-        unsigned long long word = b < 64 ? s0 : s1;
-        if ((word >> (b & 63)) & 1ull)  // likely collisions are recent columns: scan backwards
-          for (int c = a.w - 1; c >= 0; c--)
+      if (i < a.n_new && ok) {
+        const unsigned h1 = sig_h1(nv[i]), h2 = sig_h2(nv[i]);
+        if (((sg[h1 >> 6] >> (h1 & 63)) & (sg[h2 >> 6] >> (h2 & 63)) & 1ull))
+          for (int c = a.w - 1; c >= 0; c--)  // likely collisions are recent columns
             if (rrow[c] == nv[i]) {
               ok = false;
               break;
@@ -206,7 +256,7 @@ __device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, 
   }
   sc = 0.f;
   if (a.scored) {
-    sc = (!seed && a.Rs) ? S.tile_s[r] : 0.f;
+    sc = (!seed && a.Rs) ? ts[r] : 0.f;
     if (a.ix.score) sc += __ldg(a.ix.score + m);
     if (a.qerr) {
 #pragma unroll
@@ -224,7 +274,6 @@ __device__ __forceinline__ bool join_eval(const JoinArgs &a, const JoinSmem &S, 
   return ok;
 }
 
-
 // Where the rows of a tile go: a global table with an atomic row counter (k_join) or a
 // block-private buffer with a shared-memory counter (batch kernel).
 struct TileOut {
@@ -238,49 +287,56 @@ struct TileOut {
   unsigned long long *next_ctr;  // total next-step candidates of the written rows (nullable)
 };
 
-// Process one tile: rows src[0 .. nr) of R (width a.w), or, in seed mode (src == nullptr),
-// motif rows [seed_m0, seed_m0 + seed_C) as candidates. MODE 0 writes survivors through `o`;
-// MODE 1 adds their count and checksum hashes to acc_rows / acc_sum (per thread).
+// Process one tile: rows src[0 .. nr) of R (width a.w) -- already in shared buffer `buf` when
+// `loaded` --, or, in seed mode (src == nullptr), motif rows [seed_m0, seed_m0 + seed_C) as
+// candidates. MODE 0 writes survivors through `o`; MODE 1 adds their count and checksum hashes
+// to acc_rows / acc_sum (per thread).
 template <int BLK, int MAXNEW, int CPT, int MODE>
-__device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, int TR, const int32_t *src,
-                                          const float *srcs, int nr, int64_t seed_m0, int seed_C, const TileOut &o,
-                                          int *s_warp, unsigned long long *s_red, long long *s_base,
+__device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, int TR, int buf, bool loaded,
+                                          const int32_t *src, const float *srcs, int nr, int64_t seed_m0, int seed_C,
+                                          const TileOut &o, int *s_warp, unsigned long long *s_red, long long *s_base,
                                           unsigned long long &acc_rows, unsigned long long &acc_sum,
                                           unsigned long long &acc_cand) {
   const bool seed = src == nullptr;
   const int w = a.w, wo = a.wo;
   const int ws = w > 0 ? (w | 1) : 1;
   const int tid = threadIdx.x;
+  int32_t *tile = S.tile_buf[buf];
+  float *ts = S.ts_buf[buf];
+  // output position -> source, in shared memory: lanes look it up with different indices,
+  // which the constant bank would serialise
+  for (int q = tid; q < wo; q += BLK) {
+    const int col = a.src_col[q];
+    S.code[q] = (int16_t)(col < w ? col : (0x100 | a.new_mpos[col - w]));
+  }
   int C;
+  if (seed) __syncthreads();
   if (!seed) {
-    const int ne = nr * w;
-    {  // element e = r * w + c of the tile; (r, c) advance by (BLK / w, BLK % w) with carry
-      const int dr = BLK / w, dc = BLK % w;
-      int r = tid / w, c = tid % w;
-      for (int e = tid; e < ne; e += BLK) {
-        S.tile[r * ws + c] = __ldg(src + e);
-        r += dr;
-        c += dc;
-        if (c >= w) {
-          c -= w;
-          r++;
-        }
-      }
+    if (!loaded) {
+      load_tile<BLK, false>(tile, ts, src, srcs, nr, w);
+      __syncthreads();
     }
-    if (srcs)
-      for (int r = tid; r < nr; r += BLK) S.tile_s[r] = __ldg(srcs + r);
-    __syncthreads();
     int len = 0, start = 0;
     if (tid < nr) {
-      const int32_t *row = S.tile + tid * ws;
-      unsigned long long s0 = 0, s1 = 0;
+      const int32_t *row = tile + tid * ws;
+      unsigned long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
       for (int c = 0; c < w; c++) {
-        unsigned b = sig_bit(row[c]);
-        if (b < 64) s0 |= 1ull << b;
-        else s1 |= 1ull << (b - 64);
+        const unsigned h1 = sig_h1(row[c]), h2 = sig_h2(row[c]);
+        const unsigned long long b1 = 1ull << (h1 & 63), b2 = 1ull << (h2 & 63);
+        s0 |= (h1 >> 6) == 0 ? b1 : 0ull;
+        s1 |= (h1 >> 6) == 1 ? b1 : 0ull;
+        s2 |= (h1 >> 6) == 2 ? b1 : 0ull;
+        s3 |= (h1 >> 6) == 3 ? b1 : 0ull;
+        s0 |= (h2 >> 6) == 0 ? b2 : 0ull;
+        s1 |= (h2 >> 6) == 1 ? b2 : 0ull;
+        s2 |= (h2 >> 6) == 2 ? b2 : 0ull;
+        s3 |= (h2 >> 6) == 3 ? b2 : 0ull;
       }
-      S.sig[2 * tid] = s0;
-      S.sig[2 * tid + 1] = s1;
+      unsigned long long *sg = S.sig + 4 * tid;
+      sg[0] = s0;
+      sg[1] = s1;
+      sg[2] = s2;
+      sg[3] = s3;
       ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
     }
     int total;
@@ -297,6 +353,8 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
   }
   acc_cand += tid == 0 ? (unsigned long long)C : 0ull;
   const int st_s0 = tid / wo, st_q0 = tid % wo, st_ds = BLK / wo, st_dq = BLK % wo;
+  const int32_t *mrows = a.ix.rows;
+  const int mw = a.ix.mw;
 
   for (int rb = 0; rb < C; rb += BLK * CPT) {
     if (!seed) {  // tile row of every candidate of this round
@@ -309,36 +367,48 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
       __syncthreads();
     }
     int myr[CPT];
-    int64_t mym[CPT];
+    int mym[CPT];  // motif tables hold fewer than 2^31 rows
     float mys[CPT];
+    int32_t nv[CPT][MAXNEW];
+    // all motif-row loads of the thread's candidates first, then the dependent checks
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+      const int c = rb + k * BLK + tid;
+      int r = 0, m = 0;
+      if (c < C) {
+        if (seed) {
+          m = (int)(seed_m0 + c);
+        } else {
+          r = S.cand_row[c - rb];
+          m = S.gstart[r] + (c - S.goff[r]);
+        }
+      }
+      myr[k] = r;
+      mym[k] = m;
+      const int32_t *trow = mrows + (int64_t)m * mw;  // row 0 for idle lanes: a valid address
+#pragma unroll
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new) nv[k][i] = __ldg(trow + a.new_mpos[i]);
+    }
     unsigned pass = 0;
 #pragma unroll
     for (int k = 0; k < CPT; k++) {
       const int c = rb + k * BLK + tid;
-      myr[k] = 0;
-      mym[k] = 0;
       mys[k] = 0.f;
       if (c < C) {
-        int r = 0;
-        int64_t m;
-        if (seed) {
-          m = seed_m0 + c;
-        } else {
-          r = S.cand_row[c - rb];
-          m = (int64_t)S.gstart[r] + (c - S.goff[r]);
-        }
         float sc;
-        if (join_eval<MAXNEW>(a, S, ws, seed, r, m, sc)) {
+        if (join_check<MAXNEW>(a, S, tile, ts, ws, seed, myr[k], mym[k], nv[k], sc)) {
           pass |= 1u << k;
-          myr[k] = r;
-          mym[k] = m;
           mys[k] = sc;
           if (MODE == 1) {
-            const int32_t *rrow = S.tile + r * ws;
-            const int32_t *trow = a.ix.rows + m * a.ix.mw;
+            const int32_t *rrow = tile + myr[k] * ws;
+            const int32_t *trow = mrows + (int64_t)mym[k] * mw;
             unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
-            for (int q = 0; q < wo; q++)
-              h = dmix64(h ^ (unsigned long long)(uint32_t)join_value(a, rrow, trow, a.src_col[q]));
+            for (int q = 0; q < wo; q++) {
+              const int cd = S.code[q];
+              const int32_t v = cd < 0x100 ? rrow[cd] : __ldg(trow + (cd & 0xff));
+              h = dmix64(h ^ (unsigned long long)(uint32_t)v);
+            }
             acc_sum += h;
             acc_rows++;
           }
@@ -370,12 +440,12 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
     for (int k = 0; k < CPT; k++) {
       if (pass >> k & 1u) {
         S.surv_r[pos] = myr[k];
-        S.surv_m[pos] = (int32_t)mym[k];
+        S.surv_m[pos] = mym[k];
         if (pos < Kc) {
           if (o.outs) o.outs[base + pos] = mys[k];
           if (o.out_next) {
-            const int32_t *rrow = S.tile + myr[k] * ws;
-            const int32_t *trow = a.ix.rows + mym[k] * a.ix.mw;
+            const int32_t *rrow = tile + myr[k] * ws;
+            const int32_t *trow = mrows + (int64_t)mym[k] * mw;
             int32_t st, ln;
             ix_lookup(a.nx, join_value(a, rrow, trow, a.nx_key_col[0]),
                       a.nx.nkeys == 2 ? join_value(a, rrow, trow, a.nx_key_col[1]) : 0, st, ln);
@@ -392,9 +462,9 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
     {  // element e = sidx * wo + q; (sidx, q) advance by (BLK / wo, BLK % wo) with carry
       int sidx = st_s0, q = st_q0;
       for (int e = tid; e < ne; e += BLK) {
-        const int col = a.src_col[q];
-        const int32_t *rrow = S.tile + S.surv_r[sidx] * ws;
-        dst[e] = col < w ? rrow[col] : __ldg(a.ix.rows + (int64_t)S.surv_m[sidx] * a.ix.mw + a.new_mpos[col - w]);
+        const int cd = S.code[q];
+        dst[e] = cd < 0x100 ? tile[S.surv_r[sidx] * ws + cd]
+                            : __ldg(mrows + (int64_t)S.surv_m[sidx] * mw + (cd & 0xff));
         sidx += st_ds;
         q += st_dq;
         if (q >= wo) {

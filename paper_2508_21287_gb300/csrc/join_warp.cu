@@ -1,0 +1,346 @@
+// Per-step join kernel, warp-centric: one iteration of Alg. 1 over R with no block barriers.
+//
+// Every warp owns 32-row tiles of R: it copies a tile into its own slice of shared memory,
+// builds each row's 256-bit vertex signature and key group (one row per lane), scans the group
+// sizes with shuffles, and walks the candidates 32 at a time (one per lane): motif-row loads,
+// extra key equalities, injectivity against the row (full scan only when both signature bits
+// of a new vertex are set), back-edge bitmap tests, FP32 score. Survivors are appended to the
+// warp's staging list with a ballot; when it fills, and at the end of the tile, the warp
+// reserves its output range with one atomic and writes the rows element by element, lanes on
+// consecutive words. Count mode hashes the survivors in registers instead. Warps never wait
+// for each other, so the latency of one warp's dependent loads is hidden by the others.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "join_device.cuh"
+#include "kernels.h"
+
+namespace dmk {
+
+constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 128;
+
+struct WarpSmem {
+  int32_t *rows;              // WT x ws
+  unsigned long long *sig;    // WT x 4
+  float *rs;                  // WT scores
+  int32_t *gstart, *goff;     // WT, WT + 1
+  int32_t *cand_row;          // 32
+  int32_t *st_r, *st_m;       // WSTAGE
+  float *st_s;                // WSTAGE
+};
+
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int ws) {
+  size_t b = (size_t)WT * ws * 4;
+  b = (b + 15) / 16 * 16;
+  b += (size_t)WT * 32 + (size_t)WT * 4 + (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
+  b += (size_t)WSTAGE * 12;
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int ws) {
+  WarpSmem m;
+  size_t off = 0;
+  m.rows = (int32_t *)(base + off);
+  off += ((size_t)WT * ws * 4 + 15) / 16 * 16;
+  m.sig = (unsigned long long *)(base + off);
+  off += (size_t)WT * 32;
+  m.rs = (float *)(base + off);
+  off += (size_t)WT * 4;
+  m.gstart = (int32_t *)(base + off);
+  m.goff = m.gstart + WT;
+  m.cand_row = m.goff + WT + 1;
+  m.st_r = m.cand_row + 32;
+  m.st_m = m.st_r + WSTAGE;
+  m.st_s = (float *)(m.st_m + WSTAGE);
+  return m;
+}
+
+// Check one candidate against row r of the warp tile (new vertices preloaded).
+template <int MAXNEW>
+__device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int ws, bool seed, int r, int m,
+                                       const int32_t (&nv)[MAXNEW], float &sc) {
+  const int32_t *rrow = W.rows + r * ws;
+  const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
+  bool ok = true;
+  for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
+  if (ok && !seed) {
+    const unsigned long long *sg = W.sig + 4 * r;
+#pragma unroll
+    for (int i = 0; i < MAXNEW; i++) {
+      if (i < a.n_new && ok) {
+        const unsigned h1 = sig_h1(nv[i]), h2 = sig_h2(nv[i]);
+        if ((sg[h1 >> 6] >> (h1 & 63)) & (sg[h2 >> 6] >> (h2 & 63)) & 1ull)
+          for (int c = a.w - 1; c >= 0; c--)
+            if (rrow[c] == nv[i]) {
+              ok = false;
+              break;
+            }
+      }
+    }
+  }
+  sc = 0.f;
+  if (a.scored) {
+    sc = (!seed && a.Rs) ? W.rs[r] : 0.f;
+    if (a.ix.score) sc += __ldg(a.ix.score + m);
+    if (a.qerr) {
+#pragma unroll
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new) sc += __ldg(a.qerr + nv[i]);
+    }
+  }
+  for (int e = 0; e < a.n_be && ok; e++) {
+    int32_t va = join_value(a, rrow, trow, a.be_a[e]);
+    int32_t vb = join_value(a, rrow, trow, a.be_b[e]);
+    ok = adjacent(a, va, vb);
+    if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
+  }
+  if (sc > a.prune) ok = false;
+  return ok;
+}
+
+// Write the warp's staged survivors: one reservation, then coalesced element-parallel stores.
+__device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int ws, int n,
+                                       unsigned long long &nsum) {
+  const int lane = threadIdx.x & 31;
+  const int wo = a.wo;
+  long long base = 0;
+  if (lane == 0) base = (long long)atomicAdd(a.ctr + CTR_ROWS, (unsigned long long)n);
+  base = __shfl_sync(FULL_MASK, base, 0);
+  int Kc = n;
+  if (base + n > a.out_cap) {
+    Kc = (int)imax64(0, a.out_cap - base);
+    if (lane == 0) atomicOr(a.ctr + CTR_OVF, 1ull);
+  }
+  const int32_t *mrows = a.ix.rows;
+  const int mw = a.ix.mw;
+  for (int i = lane; i < Kc; i += 32) {
+    if (a.outs) a.outs[base + i] = W.st_s[i];
+    if (a.out_next) {
+      const int32_t *rrow = W.rows + W.st_r[i] * ws;
+      const int32_t *trow = mrows + (int64_t)W.st_m[i] * mw;
+      int32_t st, ln;
+      ix_lookup(a.nx, join_value(a, rrow, trow, a.nx_key_col[0]),
+                a.nx.nkeys == 2 ? join_value(a, rrow, trow, a.nx_key_col[1]) : 0, st, ln);
+      a.out_next[base + i] = ln;
+      nsum += (unsigned long long)ln;
+    }
+  }
+  int32_t *dst = a.out + base * wo;
+  const int ne = Kc * wo;
+  int s = lane / wo, q = lane % wo;
+  const int ds = 32 / wo, dq = 32 % wo;
+  for (int e = lane; e < ne; e += 32) {
+    const int cd = code[q];
+    dst[e] = cd < 0x100 ? W.rows[W.st_r[s] * ws + cd] : __ldg(mrows + (int64_t)W.st_m[s] * mw + (cd & 0xff));
+    s += ds;
+    q += dq;
+    if (q >= wo) {
+      q -= wo;
+      s++;
+    }
+  }
+  __syncwarp();
+}
+
+template <int MAXNEW, int MODE>
+__global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ JoinArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int16_t code[MAXW];
+  __shared__ unsigned long long s_red[WJ_WARPS];
+  const bool seed = a.R == nullptr;
+  const int w = a.w, wo = a.wo;
+  const int ws = w > 0 ? (w | 1) : 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const WarpSmem W = warp_smem(smem + (size_t)wid * warp_smem_bytes(ws), ws);
+  for (int q = threadIdx.x; q < wo; q += WJ_BLK) {
+    const int col = a.src_col[q];
+    code[q] = (int16_t)(col < w ? col : (0x100 | a.new_mpos[col - w]));
+  }
+  __syncthreads();
+  const int64_t N = seed ? (a.seed_hi - a.seed_lo) : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
+  const int64_t ntiles = (N + WT - 1) / WT;
+  const int64_t gw = (int64_t)blockIdx.x * WJ_WARPS + wid, nw = (int64_t)gridDim.x * WJ_WARPS;
+  const int32_t *mrows = a.ix.rows;
+  const int mw = a.ix.mw;
+  unsigned long long acc_rows = 0, acc_sum = 0, acc_cand = 0, nsum = 0;
+
+  for (int64_t t = gw; t < ntiles; t += nw) {
+    const int64_t r0 = t * WT;
+    const int nr = (int)imin64(WT, N - r0);
+    int C;
+    if (!seed) {
+      const int32_t *src = a.R + r0 * w;
+      const int ne = nr * w;
+      int r = lane / w, c = lane % w;
+      const int dr = 32 / w, dc = 32 % w;
+      for (int e = lane; e < ne; e += 32) {
+        W.rows[r * ws + c] = __ldg(src + e);
+        r += dr;
+        c += dc;
+        if (c >= w) {
+          c -= w;
+          r++;
+        }
+      }
+      if (a.Rs && lane < nr) W.rs[lane] = __ldg(a.Rs + r0 + lane);
+      __syncwarp();
+      int start = 0, len = 0;
+      if (lane < nr) {
+        const int32_t *row = W.rows + lane * ws;
+        unsigned long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int cc = 0; cc < w; cc++) {
+          const unsigned h1 = sig_h1(row[cc]), h2 = sig_h2(row[cc]);
+          const unsigned long long b1 = 1ull << (h1 & 63), b2 = 1ull << (h2 & 63);
+          s0 |= (h1 >> 6) == 0 ? b1 : 0ull;
+          s1 |= (h1 >> 6) == 1 ? b1 : 0ull;
+          s2 |= (h1 >> 6) == 2 ? b1 : 0ull;
+          s3 |= (h1 >> 6) == 3 ? b1 : 0ull;
+          s0 |= (h2 >> 6) == 0 ? b2 : 0ull;
+          s1 |= (h2 >> 6) == 1 ? b2 : 0ull;
+          s2 |= (h2 >> 6) == 2 ? b2 : 0ull;
+          s3 |= (h2 >> 6) == 3 ? b2 : 0ull;
+        }
+        unsigned long long *sg = W.sig + 4 * lane;
+        sg[0] = s0;
+        sg[1] = s1;
+        sg[2] = s2;
+        sg[3] = s3;
+        ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += v;
+      }
+      C = __shfl_sync(FULL_MASK, incl, 31);
+      W.gstart[lane] = start;
+      W.goff[lane] = incl - len;
+      if (lane == 0) W.goff[WT] = C;
+      __syncwarp();
+    } else {
+      C = nr;
+    }
+    acc_cand += lane == 0 ? (unsigned long long)C : 0ull;
+    int nst = 0;
+    for (int cb = 0; cb < C; cb += 32) {
+      if (!seed) {  // tile row of each candidate of this chunk
+        if (lane < nr) {
+          int lo = max(W.goff[lane], cb), hi = min(W.goff[lane + 1], cb + 32);
+          for (int c = lo; c < hi; c++) W.cand_row[c - cb] = lane;
+        }
+        __syncwarp();
+      }
+      const int c = cb + lane;
+      const bool valid = c < C;
+      int r = 0, m = 0;
+      if (valid) {
+        if (seed) m = (int)(a.seed_lo + r0 + c);
+        else {
+          r = W.cand_row[lane];
+          m = W.gstart[r] + (c - W.goff[r]);
+        }
+      }
+      int32_t nv[MAXNEW];
+      const int32_t *trow = mrows + (int64_t)m * mw;
+#pragma unroll
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new) nv[i] = __ldg(trow + a.new_mpos[i]);
+      float sc = 0.f;
+      const bool ok = valid && wcheck<MAXNEW>(a, W, ws, seed, r, m, nv, sc);
+      if (MODE == 1) {
+        if (ok) {
+          const int32_t *rrow = W.rows + r * ws;
+          unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
+          for (int q = 0; q < wo; q++) {
+            const int cd = code[q];
+            const int32_t v = cd < 0x100 ? rrow[cd] : __ldg(trow + (cd & 0xff));
+            h = dmix64(h ^ (unsigned long long)(uint32_t)v);
+          }
+          acc_sum += h;
+          acc_rows++;
+        }
+      } else {
+        const unsigned bal = __ballot_sync(FULL_MASK, ok);
+        if (ok) {
+          const int pos = nst + __popc(bal & lanemask_lt());
+          W.st_r[pos] = r;
+          W.st_m[pos] = m;
+          W.st_s[pos] = sc;
+        }
+        nst += __popc(bal);
+        __syncwarp();
+        if (nst > WSTAGE - 32) {
+          wflush(a, W, code, ws, nst, nsum);
+          nst = 0;
+        }
+      }
+      __syncwarp();  // cand_row is rewritten by the next chunk
+    }
+    if (MODE == 0 && nst > 0) wflush(a, W, code, ws, nst, nsum);
+    __syncwarp();  // the next tile overwrites this warp's rows
+  }
+  unsigned long long tc = block_sum_u64<WJ_BLK>(acc_cand, s_red);
+  if (threadIdx.x == 0 && tc) atomicAdd(a.ctr + CTR_CAND, tc);
+  if (a.out_next) {
+    unsigned long long tn = block_sum_u64<WJ_BLK>(nsum, s_red);
+    if (threadIdx.x == 0 && tn) atomicAdd(a.ctr + CTR_NEXT, tn);
+  }
+  if (MODE == 1) {
+    unsigned long long tr = block_sum_u64<WJ_BLK>(acc_rows, s_red);
+    unsigned long long ts = block_sum_u64<WJ_BLK>(acc_sum, s_red);
+    if (threadIdx.x == 0) {
+      if (tr) atomicAdd(a.ctr + CTR_ROWS, tr);
+      atomicAdd(a.ctr + CTR_SUM, ts);
+    }
+  }
+}
+
+typedef void (*WJoinKernel)(JoinArgs);
+
+static WJoinKernel pick_wjoin(const JoinArgs &a) {
+  if (a.mode == 1) {
+    if (a.n_new <= 1) return k_joinw<1, 1>;
+    if (a.n_new <= 4) return k_joinw<4, 1>;
+    return k_joinw<MAXM, 1>;
+  }
+  if (a.n_new <= 1) return k_joinw<1, 0>;
+  if (a.n_new <= 4) return k_joinw<4, 0>;
+  return k_joinw<MAXM, 0>;
+}
+
+static size_t wjoin_smem(const JoinArgs &a) {
+  const int ws = a.w > 0 ? (a.w | 1) : 1;
+  return (size_t)WJ_WARPS * warp_smem_bytes(ws);
+}
+
+static void set_wjoin_attrs() {
+  static bool done = false;
+  if (done) return;
+  WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>, k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
+  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  done = true;
+}
+
+int wjoin_grid(const JoinArgs &a, int num_sms) {
+  set_wjoin_attrs();
+  WJoinKernel k = pick_wjoin(a);
+  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? INT64_MAX / 2 : a.N);
+  int64_t blocks_needed = (rows + (int64_t)WT * WJ_WARPS - 1) / ((int64_t)WT * WJ_WARPS);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WJ_BLK, wjoin_smem(a));
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)num_sms * per_sm;
+  if (blocks_needed < g) g = blocks_needed;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_wjoin(const JoinArgs &a, int grid, cudaStream_t s) {
+  set_wjoin_attrs();
+  WJoinKernel k = pick_wjoin(a);
+  g_launches++;
+  k<<<grid < 1 ? 1 : grid, WJ_BLK, wjoin_smem(a), s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dmk

@@ -39,7 +39,7 @@ int64_t launch_count() { return g_launches.load(); }
 int join_tile_rows(int w) {
   if (w <= 0) return JOIN_BLK;
   int ws = w | 1;
-  int tr = 32768 / (ws * 4);
+  int tr = 24576 / (ws * 4);
   tr = tr / 32 * 32;
   if (tr < 32) tr = 32;
   if (tr > JOIN_BLK) tr = JOIN_BLK;
@@ -50,28 +50,19 @@ static int join_cpt(int n_new) { return n_new <= 4 ? 4 : 1; }
 
 size_t join_smem_bytes(int w, int wo, int tile_rows) {
   (void)wo;
-  int ws = w > 0 ? (w | 1) : 1;
-  size_t b = (size_t)tile_rows * ws * 4;  // tile
-  b = (b + 15) / 16 * 16;
-  b += (size_t)tile_rows * 16;            // 128-bit vertex signature per row
-  b += (size_t)tile_rows * 4;             // tile scores
-  b += (size_t)tile_rows * 4;             // group starts
-  b += (size_t)(tile_rows + 1) * 4;       // group offsets
-  b = (b + 15) / 16 * 16;
-  b += (size_t)JOIN_BLK * 4 * 8;          // survivor (row, motif row) pairs of one round
-  b += (size_t)JOIN_BLK * 4 * 4;          // tile row of each candidate of one round
-  return b;
+  size_t offs[7];
+  return join_smem_layout(tile_rows, w > 0 ? (w | 1) : 1, JOIN_BLK * 4, 2, offs);
 }
 
 template <int BLK, int MAXNEW, int CPT, int MODE>
-__global__ void __launch_bounds__(BLK, 4) k_join(const __grid_constant__ JoinArgs a, int TR) {
+__global__ void __launch_bounds__(BLK, 3) k_join(const __grid_constant__ JoinArgs a, int TR) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_warp[BLK / 32];
   __shared__ unsigned long long s_red[BLK / 32];
   __shared__ long long s_base;
   const bool seed = a.R == nullptr;
   const int ws = a.w > 0 ? (a.w | 1) : 1;
-  const JoinSmem S = join_smem(smem, TR, ws, BLK * CPT);
+  const JoinSmem S = join_smem(smem, TR, ws, BLK * CPT, 2);
   const int64_t N = seed ? 0 : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
   const int64_t per = seed ? (int64_t)BLK * CPT : TR;
   const int64_t nt = seed ? (a.seed_hi - a.seed_lo + per - 1) / per : (N + TR - 1) / TR;
@@ -85,17 +76,37 @@ __global__ void __launch_bounds__(BLK, 4) k_join(const __grid_constant__ JoinArg
   o.ovf = a.ctr + CTR_OVF;
   o.next_ctr = a.ctr + CTR_NEXT;
   unsigned long long acc_rows = 0, acc_sum = 0, acc_cand = 0;
-  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
-    if (seed) {
+  if (seed) {
+    for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
       const int64_t m0 = a.seed_lo + t * per;
-      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, nullptr, nullptr, 0, m0, (int)imin64(per, a.seed_hi - m0), o,
-                                        s_warp, s_red, &s_base, acc_rows, acc_sum, acc_cand);
-    } else {
-      const int64_t r0 = t * TR;
-      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, a.R + r0 * a.w, a.Rs ? a.Rs + r0 : nullptr,
-                                        (int)imin64(TR, N - r0), 0, 0, o, s_warp, s_red, &s_base, acc_rows,
+      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, 0, false, nullptr, nullptr, 0, m0,
+                                        (int)imin64(per, a.seed_hi - m0), o, s_warp, s_red, &s_base, acc_rows,
                                         acc_sum, acc_cand);
     }
+  } else {
+    // double buffering: the next tile of this block streams into the other buffer (cp.async)
+    // while the current one is joined
+    int buf = 0;
+    int64_t t = blockIdx.x;
+    if (t < nt)
+      load_tile<BLK, true>(S.tile_buf[0], S.ts_buf[0], a.R + t * TR * a.w, a.Rs ? a.Rs + t * TR : nullptr,
+                           (int)imin64(TR, N - t * TR), a.w);
+    cp_async_commit();
+    for (; t < nt; t += gridDim.x) {
+      const int64_t tn = t + gridDim.x;
+      if (tn < nt)
+        load_tile<BLK, true>(S.tile_buf[buf ^ 1], S.ts_buf[buf ^ 1], a.R + tn * TR * a.w,
+                             a.Rs ? a.Rs + tn * TR : nullptr, (int)imin64(TR, N - tn * TR), a.w);
+      cp_async_commit();
+      cp_async_wait_all_but_one();
+      __syncthreads();
+      const int64_t r0 = t * TR;
+      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, buf, true, a.R + r0 * a.w, a.Rs ? a.Rs + r0 : nullptr,
+                                        (int)imin64(TR, N - r0), 0, 0, o, s_warp, s_red, &s_base, acc_rows, acc_sum,
+                                        acc_cand);
+      buf ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
   }
   unsigned long long tc = block_sum_u64<BLK>(acc_cand, s_red);
   if (threadIdx.x == 0 && tc) atomicAdd(a.ctr + CTR_CAND, tc);

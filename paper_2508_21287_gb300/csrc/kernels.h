@@ -22,6 +22,9 @@ size_t join_smem_bytes(int w, int wo, int tile_rows);
 int join_tile_rows(int w);
 cudaError_t launch_join(const dmi::JoinArgs &a, int grid, int tile_rows, cudaStream_t s);
 int join_grid(const dmi::JoinArgs &a, int tile_rows, int num_sms);
+// Warp-centric variant (join_warp.cu): same arguments and results, no block barriers.
+cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s);
+int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
 
 // Data-graph preparation.
 cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, const float *eerr,
