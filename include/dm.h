@@ -156,7 +156,9 @@ typedef int (*dm_chunk_cb)(void *user, const int32_t *rows, const float *scores,
  *     chunks follow the depth-first order of the streamed join.
  *   DM_COUNT: nothing is delivered; cb may be NULL.
  * out_count / out_checksum (nullable) receive |Emb| and the checksum: the sum mod 2^64 over
- * rows of H(row), H = fold of the SplitMix64 finaliser over (n_p, f(0), ..., f(n_p - 1)).
+ * rows of H(row) = mix64(n_p + sum_j mix64(((j + 1) << 32) | f(j))), sums mod 2^64, mix64 the
+ * SplitMix64 finaliser. The library's own digest (the paper has none); it binds each vertex
+ * id to its pattern position and does not depend on row order.
  * Scores (when the graph has error weights) are the sum of edge errors over pattern edges
  * plus vertex errors, FP32 (Sec. 5.4, log-domain form of the fidelity product). */
 int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void *user,

@@ -22,9 +22,11 @@
  * lexicographically, without duplicates.
  *
  * Checksum of a row set: sum over rows of H(row) mod 2^64 where
- *   h = mix64(n_p); for j in 0..n_p-1: h = mix64(h ^ (uint32)f(j));  H(row) = h
- * and mix64 is the SplitMix64 output finaliser (Steele, Lea, Flood 2014). The sum does not
- * depend on row order. (The paper has no checksum; this is the library's own definition.)
+ *   H(row) = mix64(n_p + sum_{j=0}^{n_p-1} mix64(((j + 1) << 32) | (uint32)f(j)))   (mod 2^64)
+ * and mix64 is the SplitMix64 output finaliser (Steele, Lea, Flood 2014). Each term binds a
+ * vertex id to its pattern position, so H depends on every position; neither H's inner sum
+ * nor the outer sum depends on order. (The paper has no checksum; this is the library's own
+ * definition.)
  *
  * Score of a row (layout fidelity, Sec. 5.4): sum over pattern edges {u, v} of the edge
  * error w_e(f(u), f(v)) plus sum over pattern vertices of the vertex error w_q(f(u)),
@@ -52,9 +54,9 @@ static uint64_t mix64(uint64_t z) {
 uint64_t or_mix64(uint64_t z) { return mix64(z); }
 
 uint64_t or_row_hash(const int32_t *row, int32_t n) {
-    uint64_t h = mix64((uint64_t)(uint32_t)n);
-    for (int32_t j = 0; j < n; j++) h = mix64(h ^ (uint64_t)(uint32_t)row[j]);
-    return h;
+    uint64_t s = (uint64_t)(uint32_t)n;
+    for (int32_t j = 0; j < n; j++) s += mix64(((uint64_t)(uint32_t)(j + 1) << 32) | (uint64_t)(uint32_t)row[j]);
+    return mix64(s);
 }
 
 uint64_t or_checksum(const int32_t *rows, int64_t nrows, int32_t n) {

@@ -376,7 +376,6 @@ struct StepRT {
   JoinArgs base{};
   Index *ix = nullptr;
   DevTable *seed_table = nullptr;
-  int tile_rows = 32;
   int64_t max_group = 1;
   int64_t motif_bytes = 0;
 };
@@ -447,7 +446,6 @@ struct Exec {
       a.prune = prune;
       a.mode = (j == S - 1 && mode == DM_COUNT) ? 1 : 0;
       a.nx.nkeys = -1;
-      r.tile_rows = dmk::join_tile_rows(a.w);
     }
     for (int j = 0; j + 1 < S; j++) {
       st[j].base.nx = st[j + 1].base.ix;
@@ -1119,7 +1117,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
       a.nx.nkeys = -1;
       a.prune = INFINITY;
       args.push_back(a);
-      ws_max = std::max(ws_max, a.w > 0 ? (a.w | 1) : 1);
+      ws_max = std::max(ws_max, join_row_stride(a.w));
       maxw[j] = std::max<int64_t>(maxw[j], a.wo);
       if (j > 0) cap[j] = std::max<int64_t>(cap[j], (int64_t)TR * ex.st[j].max_group);
       cost += ex.p->steps[j].est_rows;

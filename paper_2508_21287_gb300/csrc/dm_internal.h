@@ -13,6 +13,20 @@ constexpr int MAXM = 20;   // motif vertices
 constexpr int MAXBE = 64;  // back-edge checks in one step
 constexpr int MAXSTEPS = 128;
 
+// Shared-memory row stride (in int32 words) of an R tile of width w: a multiple of 4 so that a
+// row can be read as int4 vectors, with an odd number of int4s so that the rows read by the 8
+// lanes of one 128-bit shared-memory phase fall on distinct banks. Padding words hold -1,
+// which matches no vertex id.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int join_row_stride(int w) {
+  int s = (w + 3) / 4 * 4;
+  if (s == 0) s = 4;
+  if (((s / 4) & 1) == 0) s += 4;
+  return s;
+}
+
 constexpr int MOTIF_VERTEX = 1;  // the one-vertex "motif" (degenerate single-vertex pattern)
 
 // ------------------------------------------------------------------- motifs (host) -----

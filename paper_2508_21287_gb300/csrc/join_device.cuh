@@ -1,17 +1,20 @@
 // Device side of one join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge test
-// + score + compaction) on one tile of the intermediate table R. Shared by the per-step kernel
-// (k_join, kernels.cu) and the persistent batch kernel (batch.cu).
+// + score + compaction) on one tile of the intermediate table R, as a whole block: the tile
+// routine of the persistent batch kernel (batch.cu). The per-step kernel (join_warp.cu) uses
+// the helpers here with one warp per tile instead.
 //
-// A block stages up to TR rows of R in shared memory (odd row stride: conflict-free column
-// reads across rows; the per-step kernel prefetches the next tile with cp.async while it
-// works on the current one), computes a 256-bit two-hash signature of each row's vertex ids,
-// looks up each row's key group in the motif index, and scans the group sizes into a
-// candidate range. The candidates are then processed in rounds of BLK * CPT: each thread
-// first issues the motif-row loads of its CPT candidates, then checks them (extra key
-// equalities, injectivity against the row -- a full scan only when both signature bits of a
-// new vertex are set --, back-edges in the adjacency bitmap, FP32 score); survivors are
-// compacted with a block scan, their output range is reserved once per round, and the block
-// writes the rows element by element so that consecutive threads store consecutive words.
+// A block stages up to TR rows of R in shared memory (row stride join_row_stride(w): int4
+// reads, padding words -1), looks up each row's key group in the motif index, and scans the
+// group sizes into a candidate range. The candidates are then processed in rounds of BLK *
+// CPT: each thread first issues the motif-row loads of its CPT candidates, then checks them
+// (extra key equalities, injectivity of the new vertices against the whole row with int4
+// compares, back-edges in the adjacency bitmap, FP32 score); survivors are compacted with a
+// block scan, their output range is reserved once per round, and the block writes the rows
+// element by element so that consecutive threads store consecutive words.
+//
+// Checksum of a row (count mode): H = mix64(n + sum_q mix64(((q + 1) << 32) | f(q))) over the
+// output positions q, sums mod 2^64. The terms of the columns that come from the R row are
+// summed once per tile row; each surviving candidate adds the terms of its new vertices.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -140,18 +143,50 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x
   return t;  // valid in thread 0
 }
 
-// Two positions of a vertex id in the 256-bit row signature (independent multiplicative hashes).
-__device__ __forceinline__ unsigned sig_h1(int32_t v) { return ((uint32_t)v * 0x9E3779B1u) >> 24; }
-__device__ __forceinline__ unsigned sig_h2(int32_t v) { return ((uint32_t)v * 0x85EBCA77u) >> 24; }
+// Checksum term of vertex v at output position q.
+__device__ __forceinline__ unsigned long long col_term(int q, int32_t v) {
+  return dmix64(((unsigned long long)(uint32_t)(q + 1) << 32) | (uint32_t)v);
+}
+
+// true when v equals one of the first w words of a shared-memory row (stride join_row_stride,
+// padding -1, so whole int4s can be compared)
+__device__ __forceinline__ bool row_has(const int32_t *row, int w, int32_t v) {
+  const int4 *r4 = (const int4 *)row;
+  bool hit = false;
+#pragma unroll 2
+  for (int c4 = 0; c4 < (w + 3) >> 2; c4++) {
+    const int4 x = r4[c4];
+    hit |= (x.x == v) | (x.y == v) | (x.z == v) | (x.w == v);
+  }
+  return hit;
+}
+
+// Sum of the checksum terms of the first w words of a shared-memory row; ipos[c] is the output
+// position of column c (-1: not output), defined for c < 4 * ceil(w / 4) <= MAXW.
+__device__ __forceinline__ unsigned long long row_terms(const int32_t *row, int w, const int8_t *ipos) {
+  const int4 *r4 = (const int4 *)row;
+  unsigned long long p = 0;
+  for (int c4 = 0; c4 < (w + 3) >> 2; c4++) {
+    const int4 x = r4[c4];
+    const int c = 4 * c4;
+    if (ipos[c] >= 0) p += col_term(ipos[c], x.x);
+    if (ipos[c + 1] >= 0) p += col_term(ipos[c + 1], x.y);
+    if (ipos[c + 2] >= 0) p += col_term(ipos[c + 2], x.z);
+    if (ipos[c + 3] >= 0) p += col_term(ipos[c + 3], x.w);
+  }
+  return p;
+}
 
 struct JoinSmem {
-  int32_t *tile_buf[2];  // R tiles (two for the prefetching per-step kernel)
+  int32_t *tile_buf[2];  // R tiles
   float *ts_buf[2];
-  unsigned long long *sig;  // 4 words per row
+  unsigned long long *part;  // per row: checksum terms of its columns (count mode)
   int32_t *gstart, *goff;
   int32_t *surv_r, *surv_m;
   int32_t *cand_row;
   int16_t *code;  // per output position: working column (< 0x100: from the R row) or 0x100 | motif position
+  int8_t *ipos;   // per R column: its output position (-1: none)
+  int8_t *npos;   // per new vertex: its output position
 };
 
 __host__ __device__ __forceinline__ size_t join_smem_layout(int TR, int ws, int BLKCPT, int nbuf, size_t *offs) {
@@ -164,13 +199,13 @@ __host__ __device__ __forceinline__ size_t join_smem_layout(int TR, int ws, int 
     offs[2 + b] = off;
     if (b < nbuf) off += ((size_t)TR * 4 + 15) / 16 * 16;
   }
-  offs[4] = off;  // signatures
-  off += (size_t)TR * 32;
+  offs[4] = off;  // partial checksums
+  off += (size_t)TR * 8;
   offs[5] = off;  // group starts, offsets
   off += (size_t)TR * 4 + (size_t)(TR + 1) * 4;
   off = (off + 15) / 16 * 16;
   offs[6] = off;  // survivors, candidate rows, codes
-  off += (size_t)BLKCPT * 4 * 3 + (size_t)MAXW * 2;
+  off += (size_t)BLKCPT * 4 * 3 + (size_t)MAXW * 3 + MAXM;
   return (off + 15) / 16 * 16;
 }
 
@@ -182,35 +217,29 @@ __device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int w
   m.tile_buf[1] = (int32_t *)(smem + (nbuf > 1 ? o[1] : o[0]));
   m.ts_buf[0] = (float *)(smem + o[2]);
   m.ts_buf[1] = (float *)(smem + (nbuf > 1 ? o[3] : o[2]));
-  m.sig = (unsigned long long *)(smem + o[4]);
+  m.part = (unsigned long long *)(smem + o[4]);
   m.gstart = (int32_t *)(smem + o[5]);
   m.goff = m.gstart + TR;
   m.surv_r = (int32_t *)(smem + o[6]);
   m.surv_m = m.surv_r + BLKCPT;
   m.cand_row = m.surv_m + BLKCPT;
   m.code = (int16_t *)(m.cand_row + BLKCPT);
+  m.ipos = (int8_t *)(m.code + MAXW);
+  m.npos = m.ipos + MAXW;
   return m;
 }
 
-__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
-  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-// Copy nr rows (width w) from src into a shared tile of row stride ws, and their scores.
-// ASYNC: with cp.async (the caller commits and waits); else with plain loads and stores.
-template <int BLK, bool ASYNC>
+// Copy nr rows (width w) from src into a shared tile of row stride join_row_stride(w), with
+// -1 in the padding words, and their scores.
+template <int BLK>
 __device__ __forceinline__ void load_tile(int32_t *tile, float *ts, const int32_t *src, const float *srcs, int nr,
                                           int w) {
-  const int ws = w | 1;
+  const int ws = join_row_stride(w);
   const int ne = nr * w;
   const int dr = BLK / w, dc = BLK % w;
   int r = threadIdx.x / w, c = threadIdx.x % w;  // element e = r * w + c, advanced with carry
   for (int e = threadIdx.x; e < ne; e += BLK) {
-    if (ASYNC) cp_async4(tile + r * ws + c, src + e);
-    else tile[r * ws + c] = __ldg(src + e);
+    tile[r * ws + c] = __ldg(src + e);
     r += dr;
     c += dc;
     if (c >= w) {
@@ -218,11 +247,10 @@ __device__ __forceinline__ void load_tile(int32_t *tile, float *ts, const int32_
       r++;
     }
   }
+  const int np = ws - w;
+  for (int e = threadIdx.x; e < nr * np; e += BLK) tile[(e / np) * ws + w + e % np] = -1;
   if (srcs)
-    for (int i = threadIdx.x; i < nr; i += BLK) {
-      if (ASYNC) cp_async4(ts + i, srcs + i);
-      else ts[i] = __ldg(srcs + i);
-    }
+    for (int i = threadIdx.x; i < nr; i += BLK) ts[i] = __ldg(srcs + i);
 }
 
 // Value of working column `col` of the joined row (R row `rrow`, motif row `trow`).
@@ -240,19 +268,9 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
   bool ok = true;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
   if (ok && !seed) {  // FilterOverlappingNodes: new vertices must not repeat a mapped one
-    const unsigned long long *sg = S.sig + 4 * r;
 #pragma unroll
-    for (int i = 0; i < MAXNEW; i++) {
-      if (i < a.n_new && ok) {
-        const unsigned h1 = sig_h1(nv[i]), h2 = sig_h2(nv[i]);
-        if (((sg[h1 >> 6] >> (h1 & 63)) & (sg[h2 >> 6] >> (h2 & 63)) & 1ull))
-          for (int c = a.w - 1; c >= 0; c--)  // likely collisions are recent columns
-            if (rrow[c] == nv[i]) {
-              ok = false;
-              break;
-            }
-      }
-    }
+    for (int i = 0; i < MAXNEW; i++)
+      if (i < a.n_new && ok) ok = !row_has(rrow, a.w, nv[i]);
   }
   sc = 0.f;
   if (a.scored) {
@@ -299,44 +317,37 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
                                           unsigned long long &acc_cand) {
   const bool seed = src == nullptr;
   const int w = a.w, wo = a.wo;
-  const int ws = w > 0 ? (w | 1) : 1;
+  const int ws = join_row_stride(w);
   const int tid = threadIdx.x;
   int32_t *tile = S.tile_buf[buf];
   float *ts = S.ts_buf[buf];
   // output position -> source, in shared memory: lanes look it up with different indices,
   // which the constant bank would serialise
+  if (MODE == 1)
+    for (int q = tid; q < MAXW; q += BLK) S.ipos[q] = -1;
   for (int q = tid; q < wo; q += BLK) {
     const int col = a.src_col[q];
     S.code[q] = (int16_t)(col < w ? col : (0x100 | a.new_mpos[col - w]));
+    if (MODE == 1 && col >= w) S.npos[col - w] = (int8_t)q;
+  }
+  if (MODE == 1) {
+    __syncthreads();
+    for (int q = tid; q < wo; q += BLK) {
+      const int col = a.src_col[q];
+      if (col < w) S.ipos[col] = (int8_t)q;
+    }
   }
   int C;
   if (seed) __syncthreads();
   if (!seed) {
-    if (!loaded) {
-      load_tile<BLK, false>(tile, ts, src, srcs, nr, w);
-      __syncthreads();
-    }
+    if (!loaded) load_tile<BLK>(tile, ts, src, srcs, nr, w);
+    __syncthreads();
     int len = 0, start = 0;
     if (tid < nr) {
       const int32_t *row = tile + tid * ws;
-      unsigned long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      for (int c = 0; c < w; c++) {
-        const unsigned h1 = sig_h1(row[c]), h2 = sig_h2(row[c]);
-        const unsigned long long b1 = 1ull << (h1 & 63), b2 = 1ull << (h2 & 63);
-        s0 |= (h1 >> 6) == 0 ? b1 : 0ull;
-        s1 |= (h1 >> 6) == 1 ? b1 : 0ull;
-        s2 |= (h1 >> 6) == 2 ? b1 : 0ull;
-        s3 |= (h1 >> 6) == 3 ? b1 : 0ull;
-        s0 |= (h2 >> 6) == 0 ? b2 : 0ull;
-        s1 |= (h2 >> 6) == 1 ? b2 : 0ull;
-        s2 |= (h2 >> 6) == 2 ? b2 : 0ull;
-        s3 |= (h2 >> 6) == 3 ? b2 : 0ull;
+      if (MODE == 1) {  // checksum terms of the row's own columns
+        S.part[tid] = row_terms(row, w, S.ipos);
       }
-      unsigned long long *sg = S.sig + 4 * tid;
-      sg[0] = s0;
-      sg[1] = s1;
-      sg[2] = s2;
-      sg[3] = s3;
       ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
     }
     int total;
@@ -401,15 +412,11 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
           pass |= 1u << k;
           mys[k] = sc;
           if (MODE == 1) {
-            const int32_t *rrow = tile + myr[k] * ws;
-            const int32_t *trow = mrows + (int64_t)mym[k] * mw;
-            unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
-            for (int q = 0; q < wo; q++) {
-              const int cd = S.code[q];
-              const int32_t v = cd < 0x100 ? rrow[cd] : __ldg(trow + (cd & 0xff));
-              h = dmix64(h ^ (unsigned long long)(uint32_t)v);
-            }
-            acc_sum += h;
+            unsigned long long p = seed ? 0ull : S.part[myr[k]];
+#pragma unroll
+            for (int i = 0; i < MAXNEW; i++)
+              if (i < a.n_new) p += col_term(S.npos[i], nv[k][i]);
+            acc_sum += dmix64(p + (unsigned long long)(uint32_t)wo);
             acc_rows++;
           }
         }

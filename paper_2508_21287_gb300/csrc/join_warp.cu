@@ -1,14 +1,16 @@
 // Per-step join kernel, warp-centric: one iteration of Alg. 1 over R with no block barriers.
 //
-// Every warp owns 32-row tiles of R: it copies a tile into its own slice of shared memory,
-// builds each row's 256-bit vertex signature and key group (one row per lane), scans the group
-// sizes with shuffles, and walks the candidates 32 at a time (one per lane): motif-row loads,
-// extra key equalities, injectivity against the row (full scan only when both signature bits
-// of a new vertex are set), back-edge bitmap tests, FP32 score. Survivors are appended to the
-// warp's staging list with a ballot; when it fills, and at the end of the tile, the warp
-// reserves its output range with one atomic and writes the rows element by element, lanes on
-// consecutive words. Count mode hashes the survivors in registers instead. Warps never wait
-// for each other, so the latency of one warp's dependent loads is hidden by the others.
+// Every warp owns 32-row tiles of R: it copies a tile into its own slice of shared memory
+// (row stride join_row_stride(w), padding -1), looks up each row's key group (one row per lane),
+// scans the group sizes with shuffles, and walks the candidates 32 at a time (one per lane):
+// motif-row loads, extra key equalities, injectivity of the new vertices against the whole row
+// with int4 compares, back-edge bitmap tests, FP32 score. Survivors are appended to the warp's
+// staging list with a ballot, new vertices included; when it fills, and at the end of the
+// tile, the warp reserves its output range with one atomic and writes the rows element by
+// element from shared memory, lanes on consecutive words. Count mode adds each survivor's
+// checksum instead: the terms of the row's own columns are summed once per tile row, so a
+// survivor hashes only its new vertices. Warps never wait for each other, so the latency of
+// one warp's dependent loads is hidden by the others.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,66 +19,67 @@
 
 namespace dmk {
 
-constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 128;
+constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 128, STAGE_NV = 4;
 
 struct WarpSmem {
-  int32_t *rows;              // WT x ws
-  unsigned long long *sig;    // WT x 4
+  int32_t *rows;              // WT x wsv
+  unsigned long long *part;   // WT checksum partial sums (count mode)
   float *rs;                  // WT scores
   int32_t *gstart, *goff;     // WT, WT + 1
   int32_t *cand_row;          // 32
-  int32_t *st_r, *st_m;       // WSTAGE
-  float *st_s;                // WSTAGE
+  int32_t *st_r, *st_m;       // WSTAGE survivors: tile row, motif row
+  float *st_s;                // WSTAGE scores
+  int32_t *st_nv;             // WSTAGE x STAGE_NV new vertices
 };
 
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int ws) {
-  size_t b = (size_t)WT * ws * 4;
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int wsv) {
+  size_t b = (size_t)WT * wsv * 4;
+  b += (size_t)WT * 8 + (size_t)WT * 4 + (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
   b = (b + 15) / 16 * 16;
-  b += (size_t)WT * 32 + (size_t)WT * 4 + (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
-  b += (size_t)WSTAGE * 12;
+  b += (size_t)WSTAGE * 12 + (size_t)WSTAGE * STAGE_NV * 4;
   return (b + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int ws) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int wsv) {
   WarpSmem m;
   size_t off = 0;
   m.rows = (int32_t *)(base + off);
-  off += ((size_t)WT * ws * 4 + 15) / 16 * 16;
-  m.sig = (unsigned long long *)(base + off);
-  off += (size_t)WT * 32;
+  off += (size_t)WT * wsv * 4;
+  m.part = (unsigned long long *)(base + off);
+  off += (size_t)WT * 8;
   m.rs = (float *)(base + off);
   off += (size_t)WT * 4;
   m.gstart = (int32_t *)(base + off);
   m.goff = m.gstart + WT;
   m.cand_row = m.goff + WT + 1;
-  m.st_r = m.cand_row + 32;
+  off += (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
+  off = (off + 15) / 16 * 16;
+  m.st_r = (int32_t *)(base + off);
   m.st_m = m.st_r + WSTAGE;
   m.st_s = (float *)(m.st_m + WSTAGE);
+  m.st_nv = (int32_t *)(m.st_s + WSTAGE);
   return m;
 }
 
 // Check one candidate against row r of the warp tile (new vertices preloaded).
 template <int MAXNEW>
-__device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int ws, bool seed, int r, int m,
+__device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int wsv, bool seed, int r, int m,
                                        const int32_t (&nv)[MAXNEW], float &sc) {
-  const int32_t *rrow = W.rows + r * ws;
+  const int32_t *rrow = W.rows + r * wsv;
   const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
   bool ok = true;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
-  if (ok && !seed) {
-    const unsigned long long *sg = W.sig + 4 * r;
+  if (ok && !seed) {  // FilterOverlappingNodes: one pass over the row for all new vertices
+    const int4 *r4 = (const int4 *)rrow;
+    bool hit = false;
+#pragma unroll 2
+    for (int c4 = 0; c4 < (a.w + 3) >> 2; c4++) {
+      const int4 x = r4[c4];
 #pragma unroll
-    for (int i = 0; i < MAXNEW; i++) {
-      if (i < a.n_new && ok) {
-        const unsigned h1 = sig_h1(nv[i]), h2 = sig_h2(nv[i]);
-        if ((sg[h1 >> 6] >> (h1 & 63)) & (sg[h2 >> 6] >> (h2 & 63)) & 1ull)
-          for (int c = a.w - 1; c >= 0; c--)
-            if (rrow[c] == nv[i]) {
-              ok = false;
-              break;
-            }
-      }
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new) hit |= (x.x == nv[i]) | (x.y == nv[i]) | (x.z == nv[i]) | (x.w == nv[i]);
     }
+    ok = !hit;
   }
   sc = 0.f;
   if (a.scored) {
@@ -99,7 +102,10 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
 }
 
 // Write the warp's staged survivors: one reservation, then coalesced element-parallel stores.
-__device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int ws, int n,
+// code[q] < 0x100: working column of the R row; else 0x100 | index of the new vertex (read
+// from the staging area when STG, else from the motif row).
+template <bool STG>
+__device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int wsv, int n,
                                        unsigned long long &nsum) {
   const int lane = threadIdx.x & 31;
   const int wo = a.wo;
@@ -116,7 +122,7 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
   for (int i = lane; i < Kc; i += 32) {
     if (a.outs) a.outs[base + i] = W.st_s[i];
     if (a.out_next) {
-      const int32_t *rrow = W.rows + W.st_r[i] * ws;
+      const int32_t *rrow = W.rows + W.st_r[i] * wsv;
       const int32_t *trow = mrows + (int64_t)W.st_m[i] * mw;
       int32_t st, ln;
       ix_lookup(a.nx, join_value(a, rrow, trow, a.nx_key_col[0]),
@@ -131,7 +137,11 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
   const int ds = 32 / wo, dq = 32 % wo;
   for (int e = lane; e < ne; e += 32) {
     const int cd = code[q];
-    dst[e] = cd < 0x100 ? W.rows[W.st_r[s] * ws + cd] : __ldg(mrows + (int64_t)W.st_m[s] * mw + (cd & 0xff));
+    int32_t v;
+    if (cd < 0x100) v = W.rows[W.st_r[s] * wsv + cd];
+    else if (STG) v = W.st_nv[s * STAGE_NV + (cd & 0xff)];
+    else v = __ldg(mrows + (int64_t)W.st_m[s] * mw + a.new_mpos[cd & 0xff]);
+    dst[e] = v;
     s += ds;
     q += dq;
     if (q >= wo) {
@@ -144,18 +154,27 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
 
 template <int MAXNEW, int MODE>
 __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ JoinArgs a) {
+  constexpr bool STG = MAXNEW <= STAGE_NV;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int16_t code[MAXW];
+  __shared__ int8_t ipos[MAXW];  // R column -> output position (-1: none)
+  __shared__ int8_t npos[MAXM];  // new vertex -> output position
   __shared__ unsigned long long s_red[WJ_WARPS];
   const bool seed = a.R == nullptr;
   const int w = a.w, wo = a.wo;
-  const int ws = w > 0 ? (w | 1) : 1;
+  const int wsv = join_row_stride(w);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const WarpSmem W = warp_smem(smem + (size_t)wid * warp_smem_bytes(ws), ws);
+  const WarpSmem W = warp_smem(smem + (size_t)wid * warp_smem_bytes(wsv), wsv);
+  for (int q = threadIdx.x; q < MAXW; q += WJ_BLK) ipos[q] = -1;
+  __syncthreads();
   for (int q = threadIdx.x; q < wo; q += WJ_BLK) {
     const int col = a.src_col[q];
-    code[q] = (int16_t)(col < w ? col : (0x100 | a.new_mpos[col - w]));
+    code[q] = (int16_t)(col < w ? col : (0x100 | (col - w)));
+    if (col < w) ipos[col] = (int8_t)q;
+    else npos[col - w] = (int8_t)q;
   }
+  for (int e = lane; e < WT * wsv; e += 32)  // padding words never change afterwards
+    if (e % wsv >= w) W.rows[e] = -1;
   __syncthreads();
   const int64_t N = seed ? (a.seed_hi - a.seed_lo) : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
   const int64_t ntiles = (N + WT - 1) / WT;
@@ -171,10 +190,10 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     if (!seed) {
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
-      int r = lane / w, c = lane % w;
+      int r = lane / w, c = lane % w;  // element e = r * w + c, advanced with carry
       const int dr = 32 / w, dc = 32 % w;
       for (int e = lane; e < ne; e += 32) {
-        W.rows[r * ws + c] = __ldg(src + e);
+        W.rows[r * wsv + c] = __ldg(src + e);
         r += dr;
         c += dc;
         if (c >= w) {
@@ -186,25 +205,8 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
       __syncwarp();
       int start = 0, len = 0;
       if (lane < nr) {
-        const int32_t *row = W.rows + lane * ws;
-        unsigned long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int cc = 0; cc < w; cc++) {
-          const unsigned h1 = sig_h1(row[cc]), h2 = sig_h2(row[cc]);
-          const unsigned long long b1 = 1ull << (h1 & 63), b2 = 1ull << (h2 & 63);
-          s0 |= (h1 >> 6) == 0 ? b1 : 0ull;
-          s1 |= (h1 >> 6) == 1 ? b1 : 0ull;
-          s2 |= (h1 >> 6) == 2 ? b1 : 0ull;
-          s3 |= (h1 >> 6) == 3 ? b1 : 0ull;
-          s0 |= (h2 >> 6) == 0 ? b2 : 0ull;
-          s1 |= (h2 >> 6) == 1 ? b2 : 0ull;
-          s2 |= (h2 >> 6) == 2 ? b2 : 0ull;
-          s3 |= (h2 >> 6) == 3 ? b2 : 0ull;
-        }
-        unsigned long long *sg = W.sig + 4 * lane;
-        sg[0] = s0;
-        sg[1] = s1;
-        sg[2] = s2;
-        sg[3] = s3;
+        const int32_t *row = W.rows + lane * wsv;
+        if (MODE == 1) W.part[lane] = row_terms(row, w, ipos);
         ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
       }
       int incl = len;
@@ -242,22 +244,19 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
         }
       }
       int32_t nv[MAXNEW];
-      const int32_t *trow = mrows + (int64_t)m * mw;
+      const int32_t *trow = mrows + (int64_t)m * mw;  // row 0 for idle lanes: a valid address
 #pragma unroll
       for (int i = 0; i < MAXNEW; i++)
         if (i < a.n_new) nv[i] = __ldg(trow + a.new_mpos[i]);
       float sc = 0.f;
-      const bool ok = valid && wcheck<MAXNEW>(a, W, ws, seed, r, m, nv, sc);
+      const bool ok = valid && wcheck<MAXNEW>(a, W, wsv, seed, r, m, nv, sc);
       if (MODE == 1) {
         if (ok) {
-          const int32_t *rrow = W.rows + r * ws;
-          unsigned long long h = dmix64((unsigned long long)(uint32_t)wo);
-          for (int q = 0; q < wo; q++) {
-            const int cd = code[q];
-            const int32_t v = cd < 0x100 ? rrow[cd] : __ldg(trow + (cd & 0xff));
-            h = dmix64(h ^ (unsigned long long)(uint32_t)v);
-          }
-          acc_sum += h;
+          unsigned long long p = seed ? 0ull : W.part[r];
+#pragma unroll
+          for (int i = 0; i < MAXNEW; i++)
+            if (i < a.n_new) p += col_term(npos[i], nv[i]);
+          acc_sum += dmix64(p + (unsigned long long)(uint32_t)wo);
           acc_rows++;
         }
       } else {
@@ -267,17 +266,20 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
           W.st_r[pos] = r;
           W.st_m[pos] = m;
           W.st_s[pos] = sc;
+#pragma unroll
+          for (int i = 0; i < (STG ? MAXNEW : 0); i++)
+            if (i < a.n_new) W.st_nv[pos * STAGE_NV + i] = nv[i];
         }
         nst += __popc(bal);
         __syncwarp();
         if (nst > WSTAGE - 32) {
-          wflush(a, W, code, ws, nst, nsum);
+          wflush<STG>(a, W, code, wsv, nst, nsum);
           nst = 0;
         }
       }
       __syncwarp();  // cand_row is rewritten by the next chunk
     }
-    if (MODE == 0 && nst > 0) wflush(a, W, code, ws, nst, nsum);
+    if (MODE == 0 && nst > 0) wflush<STG>(a, W, code, wsv, nst, nsum);
     __syncwarp();  // the next tile overwrites this warp's rows
   }
   unsigned long long tc = block_sum_u64<WJ_BLK>(acc_cand, s_red);
@@ -309,10 +311,7 @@ static WJoinKernel pick_wjoin(const JoinArgs &a) {
   return k_joinw<MAXM, 0>;
 }
 
-static size_t wjoin_smem(const JoinArgs &a) {
-  const int ws = a.w > 0 ? (a.w | 1) : 1;
-  return (size_t)WJ_WARPS * warp_smem_bytes(ws);
-}
+static size_t wjoin_smem(const JoinArgs &a) { return (size_t)WJ_WARPS * warp_smem_bytes(join_row_stride(a.w)); }
 
 static void set_wjoin_attrs() {
   static bool done = false;

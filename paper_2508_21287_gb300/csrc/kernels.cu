@@ -1,24 +1,8 @@
-// sm_103a kernels of the Delta-Motif library.
-//
-// The hot kernel is k_join: one launch performs one iteration of Alg. 1 over a tile-
-// partitioned intermediate table R (row-major, width w):
-//   InnerJoin(R, Res(M), C)   - every R row looks up its key (the R columns that the slice
-//                               shares with earlier slices, Sec. 3.2) in an index of the
-//                               motif table: direct offsets for one key column, an
-//                               open-addressing hash on the packed 64-bit key for two;
-//   FilterOverlappingNodes    - a joined row survives only if the motif's new vertices are
-//                               distinct from every vertex already in the row (Sec. 3.2:
-//                               duplicates beyond the join constraints are invalid);
-//   back-edge filter          - pattern edges between mapped vertices that no slice covers
-//                               are tested in the data graph's adjacency bitmap;
-//   score                     - FP32 layout score += motif-row edge errors + vertex errors
-//                               of the new vertices + back-edge errors (Sec. 5.4);
-//   compaction                - warp ballots + a block scan place survivors contiguously in
-//                               shared memory; one atomic per block chunk reserves the output
-//                               range, then the block writes it with coalesced stores.
-// The R tile is staged in shared memory once; every candidate row of the tile reads it
-// there. The same kernel also emits the candidate count of every written row for the next
-// step, which sizes the next output and drives chunked streaming.
+// sm_103a kernels of the Delta-Motif library besides the join: data-graph preparation (CSR
+// to M2 table, adjacency bitmap), motif-table indexes (direct offsets, open-addressing hash on
+// packed 64-bit keys), scans, LSD radix passes, row gathers, score histograms and selection,
+// and the row checksum. The join of Alg. 1 is in join_warp.cu (per step) and batch.cu
+// (persistent, all steps of many plans), on the device code of join_device.cuh.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -34,142 +18,6 @@ namespace dmk {
 
 std::atomic<int64_t> g_launches{0};
 int64_t launch_count() { return g_launches.load(); }
-
-// ------------------------------------------------------------------ join kernel --------
-int join_tile_rows(int w) {
-  if (w <= 0) return JOIN_BLK;
-  int ws = w | 1;
-  int tr = 24576 / (ws * 4);
-  tr = tr / 32 * 32;
-  if (tr < 32) tr = 32;
-  if (tr > JOIN_BLK) tr = JOIN_BLK;
-  return tr;
-}
-
-static int join_cpt(int n_new) { return n_new <= 4 ? 4 : 1; }
-
-size_t join_smem_bytes(int w, int wo, int tile_rows) {
-  (void)wo;
-  size_t offs[7];
-  return join_smem_layout(tile_rows, w > 0 ? (w | 1) : 1, JOIN_BLK * 4, 2, offs);
-}
-
-template <int BLK, int MAXNEW, int CPT, int MODE>
-__global__ void __launch_bounds__(BLK, 3) k_join(const __grid_constant__ JoinArgs a, int TR) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_warp[BLK / 32];
-  __shared__ unsigned long long s_red[BLK / 32];
-  __shared__ long long s_base;
-  const bool seed = a.R == nullptr;
-  const int ws = a.w > 0 ? (a.w | 1) : 1;
-  const JoinSmem S = join_smem(smem, TR, ws, BLK * CPT, 2);
-  const int64_t N = seed ? 0 : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
-  const int64_t per = seed ? (int64_t)BLK * CPT : TR;
-  const int64_t nt = seed ? (a.seed_hi - a.seed_lo + per - 1) / per : (N + TR - 1) / TR;
-  TileOut o;
-  o.out = a.out;
-  o.outs = a.outs;
-  o.out_next = a.out_next;
-  o.cap = a.out_cap;
-  o.gctr = a.ctr + CTR_ROWS;
-  o.lctr = nullptr;
-  o.ovf = a.ctr + CTR_OVF;
-  o.next_ctr = a.ctr + CTR_NEXT;
-  unsigned long long acc_rows = 0, acc_sum = 0, acc_cand = 0;
-  if (seed) {
-    for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
-      const int64_t m0 = a.seed_lo + t * per;
-      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, 0, false, nullptr, nullptr, 0, m0,
-                                        (int)imin64(per, a.seed_hi - m0), o, s_warp, s_red, &s_base, acc_rows,
-                                        acc_sum, acc_cand);
-    }
-  } else {
-    // double buffering: the next tile of this block streams into the other buffer (cp.async)
-    // while the current one is joined
-    int buf = 0;
-    int64_t t = blockIdx.x;
-    if (t < nt)
-      load_tile<BLK, true>(S.tile_buf[0], S.ts_buf[0], a.R + t * TR * a.w, a.Rs ? a.Rs + t * TR : nullptr,
-                           (int)imin64(TR, N - t * TR), a.w);
-    cp_async_commit();
-    for (; t < nt; t += gridDim.x) {
-      const int64_t tn = t + gridDim.x;
-      if (tn < nt)
-        load_tile<BLK, true>(S.tile_buf[buf ^ 1], S.ts_buf[buf ^ 1], a.R + tn * TR * a.w,
-                             a.Rs ? a.Rs + tn * TR : nullptr, (int)imin64(TR, N - tn * TR), a.w);
-      cp_async_commit();
-      cp_async_wait_all_but_one();
-      __syncthreads();
-      const int64_t r0 = t * TR;
-      join_tile<BLK, MAXNEW, CPT, MODE>(a, S, TR, buf, true, a.R + r0 * a.w, a.Rs ? a.Rs + r0 : nullptr,
-                                        (int)imin64(TR, N - r0), 0, 0, o, s_warp, s_red, &s_base, acc_rows, acc_sum,
-                                        acc_cand);
-      buf ^= 1;
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::);
-  }
-  unsigned long long tc = block_sum_u64<BLK>(acc_cand, s_red);
-  if (threadIdx.x == 0 && tc) atomicAdd(a.ctr + CTR_CAND, tc);
-  if (MODE == 1) {
-    unsigned long long tr = block_sum_u64<BLK>(acc_rows, s_red);
-    unsigned long long ts = block_sum_u64<BLK>(acc_sum, s_red);
-    if (threadIdx.x == 0) {
-      if (tr) atomicAdd(a.ctr + CTR_ROWS, tr);
-      atomicAdd(a.ctr + CTR_SUM, ts);
-    }
-  }
-}
-
-typedef void (*JoinKernel)(JoinArgs, int);
-
-static JoinKernel pick_join(const JoinArgs &a, int *cpt) {
-  *cpt = join_cpt(a.n_new);
-  if (a.mode == 1) {
-    if (a.n_new <= 1) return k_join<JOIN_BLK, 1, 4, 1>;
-    if (a.n_new <= 4) return k_join<JOIN_BLK, 4, 4, 1>;
-    return k_join<JOIN_BLK, MAXM, 1, 1>;
-  }
-  if (a.n_new <= 1) return k_join<JOIN_BLK, 1, 4, 0>;
-  if (a.n_new <= 4) return k_join<JOIN_BLK, 4, 4, 0>;
-  return k_join<JOIN_BLK, MAXM, 1, 0>;
-}
-
-static void set_join_attrs() {
-  static bool done = false;
-  if (done) return;
-  JoinKernel ks[] = {k_join<JOIN_BLK, 1, 4, 1>, k_join<JOIN_BLK, 4, 4, 1>, k_join<JOIN_BLK, MAXM, 1, 1>,
-                     k_join<JOIN_BLK, 1, 4, 0>, k_join<JOIN_BLK, 4, 4, 0>, k_join<JOIN_BLK, MAXM, 1, 0>};
-  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  done = true;
-}
-
-cudaError_t launch_join(const JoinArgs &a, int grid, int tile_rows, cudaStream_t s) {
-  set_join_attrs();
-  int cpt;
-  JoinKernel k = pick_join(a, &cpt);
-  size_t smem = join_smem_bytes(a.w, a.wo, tile_rows);
-  if (grid < 1) grid = 1;
-  g_launches++;
-  k<<<grid, JOIN_BLK, smem, s>>>(a, tile_rows);
-  return cudaGetLastError();
-}
-
-int join_grid(const JoinArgs &a, int tile_rows, int num_sms) {
-  set_join_attrs();
-  int cpt;
-  JoinKernel k = pick_join(a, &cpt);
-  int64_t nt;
-  if (a.R == nullptr) nt = (a.seed_hi - a.seed_lo + (int64_t)JOIN_BLK * cpt - 1) / ((int64_t)JOIN_BLK * cpt);
-  else if (a.n_dev) nt = INT64_MAX;  // row count known only on the device: fill the GPU
-  else nt = (a.N + tile_rows - 1) / tile_rows;
-  size_t smem = join_smem_bytes(a.w, a.wo, tile_rows);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, JOIN_BLK, smem);
-  if (per_sm < 1) per_sm = 1;
-  int64_t g = (int64_t)num_sms * per_sm;
-  if (nt < g) g = nt;
-  return (int)(g < 1 ? 1 : g);
-}
 
 // ------------------------------------------------------------------ graph prep ---------
 __device__ __forceinline__ int32_t slot_source(const int32_t *row_ptr, int32_t V, int64_t e) {
@@ -528,9 +376,9 @@ __global__ void k_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned 
   unsigned long long hs = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t *row = rows + i * w;
-    unsigned long long h = dmix64((unsigned long long)(uint32_t)w);
-    for (int c = 0; c < w; c++) h = dmix64(h ^ (unsigned long long)(uint32_t)__ldg(row + c));
-    hs += h;
+    unsigned long long p = 0;
+    for (int c = 0; c < w; c++) p += col_term(c, __ldg(row + c));
+    hs += dmix64(p + (unsigned long long)(uint32_t)w);
   }
   unsigned long long t = block_sum_u64<256>(hs, s_red);
   if (threadIdx.x == 0 && t) atomicAdd(ctr + CTR_SUM, t);

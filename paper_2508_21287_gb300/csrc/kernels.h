@@ -10,19 +10,13 @@
 
 namespace dmk {
 
-constexpr int JOIN_BLK = 256;
-
 // Number of kernels launched by this library in the process so far.
 int64_t launch_count();
 extern std::atomic<int64_t> g_launches;
 
 // Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
-// + compaction). Returns the dynamic shared memory it needs for the given widths.
-size_t join_smem_bytes(int w, int wo, int tile_rows);
-int join_tile_rows(int w);
-cudaError_t launch_join(const dmi::JoinArgs &a, int grid, int tile_rows, cudaStream_t s);
-int join_grid(const dmi::JoinArgs &a, int tile_rows, int num_sms);
-// Warp-centric variant (join_warp.cu): same arguments and results, no block barriers.
+// + compaction, or count + checksum in the last step), warp-centric (join_warp.cu). The grid
+// fills the GPU at the kernel's occupancy, or covers the rows of R when they are fewer.
 cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s);
 int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
 

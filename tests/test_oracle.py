@@ -201,6 +201,23 @@ def test_checksum_order_independent_and_matches_enumerator():
     assert oracle.row_hash([1, 2]) != oracle.row_hash([1, 2, 0])
 
 
+def test_row_hash_binds_every_position():
+    # a changed value at any single position, or two swapped positions, changes H(row)
+    row = [int(x) for x in np.random.default_rng(3).permutation(1000)[:12]]
+    h = oracle.row_hash(row)
+    for j in range(len(row)):
+        r2 = list(row)
+        r2[j] += 1
+        assert oracle.row_hash(r2) != h
+        for k in range(j + 1, len(row)):
+            r3 = list(row)
+            r3[j], r3[k] = r3[k], r3[j]
+            assert oracle.row_hash(r3) != h
+    # the sum over rows is taken mod 2^64: duplicated rows add up, nothing saturates
+    rows = np.array([row, row], dtype=np.int32)
+    assert oracle.checksum(rows) == (2 * h) % (1 << 64)
+
+
 def test_scores_unit_weights_equal_edge_count():
     g = I.heavy_hex(2, 3)
     g.edge_err = np.ones(len(g.col_idx), dtype=np.float32)
