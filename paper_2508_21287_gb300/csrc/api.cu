@@ -268,8 +268,11 @@ int gather_table(dm_ctx *c, const DevTable &t, const int32_t *perm, int64_t n, D
 }
 
 // Replace t by its rows in canonical (lexicographic) order.
-int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
+// Sort a table into canonical order; when ctr is set, the rows' checksum is added to
+// ctr[CTR_SUM] on the way.
+int sort_canonical(dm_ctx *c, DevTable &t, int bits, unsigned long long *ctr = nullptr) {
   if (t.n <= 1) {
+    if (ctr && t.n == 1) CK(dmk::launch_hash_rows(t.rows, 1, t.w, ctr, c->stream));
     if (t.borrowed && t.n == 1) {  // take a private copy so the holder may free it
       DevTable o;
       int32_t *one = nullptr;
@@ -284,7 +287,7 @@ int sort_canonical(dm_ctx *c, DevTable &t, int bits) {
   void *tmp = nullptr;
   RET(dalloc(c, &tmp, (size_t)dmk::msort_tmp_bytes(t.n)));
   int32_t *perm = nullptr;
-  CK(dmk::msort_rows(t.rows, t.n, t.w, bits, tmp, &perm, c->stream));
+  CK(dmk::msort_rows(t.rows, t.n, t.w, bits, tmp, &perm, ctr ? ctr + CTR_SUM : nullptr, c->stream));
   DevTable o;
   RET(gather_table(c, t, perm, t.n, &o));
   dfree(c, tmp);
@@ -650,7 +653,7 @@ struct Exec {
         a.in_cap = prev_cap;
       }
       int grid = dmk::wjoin_grid(a, c->num_sms);
-      CK(dmk::launch_wjoin(a, grid, c->stream));
+      CK(dmk::launch_wjoin(a, grid, c->stream, j > 0));  // steps chain kernel to kernel
       prev_rows = orows;
       prev_score = a.outs;
       prev_cap = cap;
@@ -778,10 +781,12 @@ struct CollectSink : Sink {
   }
 };
 
-int deliver(dm_ctx *c, const DevTable &t, int flags, dm_chunk_cb cb, void *user) {
+// Hand a finished table to the user callback (device pointers, or host copies in staging-sized
+// pieces). synced: the caller has just synchronised the stream after the table was produced.
+int deliver(dm_ctx *c, const DevTable &t, int flags, dm_chunk_cb cb, void *user, bool synced = false) {
   if (!cb || t.n == 0) return DM_OK;
   if (flags & DM_DEVICE_ROWS) {
-    CK(cudaStreamSynchronize(c->stream));
+    if (!synced) CK(cudaStreamSynchronize(c->stream));
     return cb(user, t.rows, t.score, t.n, t.w) ? DM_E_CANCELLED : DM_OK;
   }
   const int64_t rb = 4ll * t.w + (t.score ? 4 : 0);
@@ -811,14 +816,15 @@ struct AllSink : Sink {
   int64_t held_bytes = 0;
   bool streaming = false;
   uint64_t count = 0, checksum = 0;
+  // sort (checksum fused into the key packing), one synchronisation, delivery, then the top-k
+  // tap (which takes the table over)
   int flush_one(dm_ctx *c, DevTable &t) {
-    RET(sort_canonical(c, t, bits));
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
-    CK(dmk::launch_hash_rows(t.rows, t.n, t.w, c->d_ctr, c->stream));
+    RET(sort_canonical(c, t, bits, c->d_ctr));
     RET(read_ctr(c));
     count += (uint64_t)t.n;
     checksum += c->h_ctr[CTR_SUM];
-    int r = deliver(c, t, flags, cb, user);
+    int r = deliver(c, t, flags, cb, user, true);
     if (r == DM_OK && tap) return topk_take(c, tap, t);  // the tap takes ownership
     free_table(c, t);
     return r;
@@ -838,6 +844,11 @@ struct AllSink : Sink {
   }
   int finish(dm_ctx *c, int32_t w, bool scored) {
     if (held.empty()) return DM_OK;
+    if (held.size() == 1) {  // sorting makes its own copy: no concatenation needed
+      DevTable t = held[0];
+      held.clear();
+      return flush_one(c, t);
+    }
     CollectSink cs;
     cs.parts = held;
     held.clear();

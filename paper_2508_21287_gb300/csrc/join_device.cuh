@@ -36,6 +36,12 @@ __device__ __forceinline__ unsigned long long dmix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// Programmatic dependent launch: wait until the previous grid in the stream has completed and
+// its writes are visible (a no-op when the kernel was launched without the attribute), and
+// allow the next grid to be scheduled.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -19,7 +19,7 @@
 
 namespace dmk {
 
-constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 128, STAGE_NV = 4;
+constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 64, STAGE_NV = 4;
 
 struct WarpSmem {
   int32_t *rows;              // WT x wsv
@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
   for (int e = lane; e < WT * wsv; e += 32)  // padding words never change afterwards
     if (e % wsv >= w) W.rows[e] = -1;
   __syncthreads();
+  griddep_wait();  // everything above touched shared memory only
+  griddep_launch_dependents();
   const int64_t N = seed ? (a.seed_hi - a.seed_lo) : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
   const int64_t ntiles = (N + WT - 1) / WT;
   const int64_t gw = (int64_t)blockIdx.x * WJ_WARPS + wid, nw = (int64_t)gridDim.x * WJ_WARPS;
@@ -334,10 +336,11 @@ int wjoin_grid(const JoinArgs &a, int num_sms) {
   return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_wjoin(const JoinArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_wjoin(const JoinArgs &a, int grid, cudaStream_t s, bool pdl) {
   set_wjoin_attrs();
   WJoinKernel k = pick_wjoin(a);
   g_launches++;
+  if (pdl) return launch_pdl(k, dim3(grid < 1 ? 1 : grid), dim3(WJ_BLK), wjoin_smem(a), s, a);
   k<<<grid < 1 ? 1 : grid, WJ_BLK, wjoin_smem(a), s>>>(a);
   return cudaGetLastError();
 }

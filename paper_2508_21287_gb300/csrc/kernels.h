@@ -10,6 +10,26 @@
 
 namespace dmk {
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while the previous
+// kernel in the stream is finishing; it must execute griddep_wait() (join_device.cuh) before
+// touching global memory that the previous kernel reads or writes. Used only where the
+// previous stream operation is itself a kernel of the same chain.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Number of kernels launched by this library in the process so far.
 int64_t launch_count();
 extern std::atomic<int64_t> g_launches;
@@ -17,7 +37,9 @@ extern std::atomic<int64_t> g_launches;
 // Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
 // + compaction, or count + checksum in the last step), warp-centric (join_warp.cu). The grid
 // fills the GPU at the kernel's occupancy, or covers the rows of R when they are fewer.
-cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s);
+// pdl: launched with programmatic dependent launch (the previous stream operation must be a
+// kernel of the same chain).
+cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s, bool pdl = false);
 int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
 
 // Data-graph preparation.
@@ -65,8 +87,9 @@ cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned
 // row indices in ascending lexicographic order; ids are below 2^bits. tmp holds
 // msort_tmp_bytes(n) bytes.
 int64_t msort_tmp_bytes(int64_t n);
+// When sum is set, the row checksums (sum of H(row), as the count-mode join) are added to it.
 cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
-                       cudaStream_t s);
+                       unsigned long long *sum, cudaStream_t s);
 
 // The min(k, n) smallest (score bits, row index) of a canonically sorted table, k <= 1024,
 // gathered into orows / osc in that order. tmp holds topk_tmp_bytes(n) bytes.

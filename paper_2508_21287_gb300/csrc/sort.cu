@@ -1,11 +1,15 @@
 // Canonical (lexicographic) order of embedding rows, and top-k by (score, row).
 //
-// Rows are sorted by comparison rather than digit by digit: a row's first two ids are packed
-// into one 64-bit key (most rows of an embedding table already differ there), ties fall back
-// to the remaining columns read from the row itself. Tiles of 1024 rows are sorted by a
+// Rows are sorted by comparison on packed keys: every row's ids are packed, bits(V) bits each
+// and most significant first, into up to MS_KW 64-bit words (floor(64 / bits) ids per word).
+// When the whole row fits (w * bits <= MS_KW * 64 in practice) the key is exact and every
+// comparison stays in registers and shared memory; otherwise ties on the packed prefix fall
+// back to the remaining columns of the rows themselves. Tiles of 1024 rows are sorted by a
 // bitonic network in shared memory; runs are then merged pairwise, each element finding its
 // output position by a binary search in the other run (stable: ties keep run order). A sort
-// of N rows takes 3 + ceil(log2(N / 1024)) launches.
+// of N rows takes 2 + ceil(log2(N / 1024)) launches. The key-packing kernel can also add the
+// rows' checksum hashes (the same H as the join's count mode) into a counter, so that
+// delivering a table needs no separate hashing pass.
 //
 // Top-k runs on a canonically sorted table: the key of row i is (FP32 score bits, i); scores
 // are non-negative, so the bit pattern orders like the value, and i orders like the row.
@@ -16,51 +20,91 @@
 
 #include <atomic>
 
+#include "join_device.cuh"
 #include "kernels.h"
 
 namespace dmk {
 
 constexpr int MS_TILE = 1024;
 constexpr int MS_BLK = 512;
+constexpr int MS_KW = 4;
 constexpr unsigned long long KEY_INF = ~0ull;
 
+struct SortKeys {
+  const int32_t *rows;
+  int32_t w;
+  int packed;  // columns held in the key words; ties beyond them read the rows
+};
 
-// a < b for rows (key0, idx); idx < 0 is a padding element greater than every row. The key
-// packs the first kc columns (floor(64 / bits) of them), so ties compare from column kc on.
-__device__ __forceinline__ bool row_less(const int32_t *rows, int32_t w, int kc, unsigned long long ka, int32_t ia,
-                                         unsigned long long kb, int32_t ib) {
-  if (ka != kb) return ka < kb;
+// a < b for rows with packed keys ka / kb and indices ia / ib; an index < 0 is a padding
+// element greater than every row.
+template <int KW>
+__device__ __forceinline__ bool row_less(const SortKeys &S, const unsigned long long (&ka)[KW], int32_t ia,
+                                         const unsigned long long (&kb)[KW], int32_t ib) {
+#pragma unroll
+  for (int j = 0; j < KW; j++)
+    if (ka[j] != kb[j]) return ka[j] < kb[j];
   if (ia < 0 || ib < 0) return ib < 0 && ia >= 0;
-  const int32_t *ra = rows + (int64_t)ia * w, *rb = rows + (int64_t)ib * w;
-  for (int c = kc; c < w; c++) {
-    int32_t x = __ldg(ra + c), y = __ldg(rb + c);
-    if (x != y) return x < y;
+  if (S.packed < S.w) {
+    const int32_t *ra = S.rows + (int64_t)ia * S.w, *rb = S.rows + (int64_t)ib * S.w;
+    for (int c = S.packed; c < S.w; c++) {
+      int32_t x = __ldg(ra + c), y = __ldg(rb + c);
+      if (x != y) return x < y;
+    }
   }
   return ia < ib;
 }
 
-__global__ void k_pack_keys(const int32_t *rows, int64_t n, int32_t w, int bits, int kcols,
-                            unsigned long long *key, int32_t *idx) {
+// key[j * n + i]: word j of row i's packed key (structure of arrays: coalesced per word).
+template <int KW>
+__global__ void k_pack_keys(const int32_t *rows, int64_t n, int32_t w, int bits, int cpw,
+                            unsigned long long *key, int32_t *idx, unsigned long long *sum) {
+  __shared__ unsigned long long s_red[8];
+  griddep_wait();
+  griddep_launch_dependents();
+  unsigned long long hs = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t *r = rows + i * w;
-    unsigned long long k = 0;
-    for (int c = 0; c < kcols; c++) {
-      unsigned long long v = c < w ? (uint32_t)__ldg(r + c) : 0u;
-      k |= v << (64 - bits * (c + 1));
+    unsigned long long p = 0;
+#pragma unroll
+    for (int j = 0; j < KW; j++) {
+      unsigned long long k = 0;
+      for (int c = 0; c < cpw; c++) {
+        const int col = j * cpw + c;
+        unsigned long long v = 0;
+        if (col < w) {
+          const int32_t x = __ldg(r + col);
+          v = (uint32_t)x;
+          if (sum) p += col_term(col, x);
+        }
+        k |= v << (64 - bits * (c + 1));
+      }
+      key[(int64_t)j * n + i] = k;
     }
-    key[i] = k;
+    if (sum) {
+      for (int col = KW * cpw; col < w; col++) p += col_term(col, __ldg(r + col));
+      hs += dmix64(p + (unsigned long long)(uint32_t)w);
+    }
     idx[i] = (int32_t)i;
+  }
+  if (sum) {
+    unsigned long long t = block_sum_u64<256>(hs, s_red);
+    if (threadIdx.x == 0 && t) atomicAdd(sum, t);
   }
 }
 
-__global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int32_t w, int kc, int64_t n,
-                                                       unsigned long long *key, int32_t *idx) {
-  __shared__ unsigned long long sk[MS_TILE];
+template <int KW>
+__global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const SortKeys S, int64_t n, unsigned long long *key,
+                                                       int32_t *idx) {
+  __shared__ unsigned long long sk[KW][MS_TILE];
   __shared__ int32_t si[MS_TILE];
+  griddep_wait();
+  griddep_launch_dependents();
   const int64_t base = (int64_t)blockIdx.x * MS_TILE;
   for (int i = threadIdx.x; i < MS_TILE; i += MS_BLK) {
     int64_t g = base + i;
-    sk[i] = g < n ? key[g] : KEY_INF;
+#pragma unroll
+    for (int j = 0; j < KW; j++) sk[j][i] = g < n ? key[(int64_t)j * n + g] : KEY_INF;
     si[i] = g < n ? idx[g] : -1;
   }
   __syncthreads();
@@ -70,14 +114,21 @@ __global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int3
         int i = 2 * t - (t & (j - 1));
         int p = i + j;
         bool up = (i & k) == 0;
-        bool gt = row_less(rows, w, kc, sk[p], si[p], sk[i], si[i]);
-        if (gt == up) {
-          unsigned long long tk = sk[i];
-          sk[i] = sk[p];
-          sk[p] = tk;
-          int32_t ti = si[i];
-          si[i] = si[p];
-          si[p] = ti;
+        unsigned long long ki[KW], kp[KW];
+#pragma unroll
+        for (int q = 0; q < KW; q++) {
+          ki[q] = sk[q][i];
+          kp[q] = sk[q][p];
+        }
+        const int32_t ii = si[i], ip = si[p];
+        if (row_less<KW>(S, kp, ip, ki, ii) == up) {
+#pragma unroll
+          for (int q = 0; q < KW; q++) {
+            sk[q][i] = kp[q];
+            sk[q][p] = ki[q];
+          }
+          si[i] = ip;
+          si[p] = ii;
         }
       }
       __syncthreads();
@@ -86,65 +137,99 @@ __global__ void __launch_bounds__(MS_BLK) k_sort_tiles(const int32_t *rows, int3
   for (int i = threadIdx.x; i < MS_TILE; i += MS_BLK) {
     int64_t g = base + i;
     if (g < n) {
-      key[g] = sk[i];
+#pragma unroll
+      for (int j = 0; j < KW; j++) key[(int64_t)j * n + g] = sk[j][i];
       idx[g] = si[i];
     }
   }
 }
 
 // Merge the sorted runs [b, b+L) and [b+L, b+2L) of (key, idx) into (okey, oidx).
-__global__ void k_merge_pass(const int32_t *rows, int32_t w, int kc, int64_t n, int64_t L, const unsigned long long *key,
+template <int KW>
+__global__ void k_merge_pass(const SortKeys S, int64_t n, int64_t L, const unsigned long long *key,
                              const int32_t *idx, unsigned long long *okey, int32_t *oidx) {
+  griddep_wait();
+  griddep_launch_dependents();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pair = i / (2 * L);
     const int64_t b = pair * 2 * L;
     const bool inA = i < b + L;
     const int64_t ob = inA ? b + L : b;                 // the other run
     const int64_t oe = inA ? (b + 2 * L < n ? b + 2 * L : n) : b + L;
-    const unsigned long long kx = key[i];
+    unsigned long long kx[KW];
+#pragma unroll
+    for (int j = 0; j < KW; j++) kx[j] = key[(int64_t)j * n + i];
     const int32_t ix = idx[i];
     int64_t lo = ob, hi = oe > ob ? oe : ob;
     // A elements go before equal B elements: count B < x for A, A <= x for B
     while (lo < hi) {
       int64_t mid = (lo + hi) >> 1;
-      bool before = inA ? row_less(rows, w, kc, key[mid], idx[mid], kx, ix)
-                        : !row_less(rows, w, kc, kx, ix, key[mid], idx[mid]);
+      unsigned long long km[KW];
+#pragma unroll
+      for (int j = 0; j < KW; j++) km[j] = key[(int64_t)j * n + mid];
+      const int32_t im = idx[mid];
+      bool before = inA ? row_less<KW>(S, km, im, kx, ix) : !row_less<KW>(S, kx, ix, km, im);
       if (before) lo = mid + 1;
       else hi = mid;
     }
     const int64_t pos = b + (i - (inA ? b : b + L)) + (lo - ob);
-    okey[pos] = kx;
+#pragma unroll
+    for (int j = 0; j < KW; j++) okey[(int64_t)j * n + pos] = kx[j];
     oidx[pos] = ix;
   }
 }
 
-int64_t msort_tmp_bytes(int64_t n) { return n * (8 + 4) * 2 + 256; }
+int64_t msort_tmp_bytes(int64_t n) { return n * (8 * MS_KW + 4) * 2 + 256; }
 
-cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
-                       cudaStream_t s) {
-  unsigned long long *k0 = (unsigned long long *)tmp;
-  unsigned long long *k1 = k0 + n;
-  int32_t *i0 = (int32_t *)(k1 + n);
-  int32_t *i1 = i0 + n;
-  *perm_out = i0;
-  if (n <= 0) return cudaSuccess;
+template <int KW>
+static int msort_launch(const SortKeys &S, int64_t n, int bits, int cpw, unsigned long long *k0,
+                        unsigned long long *k1, int32_t *i0, int32_t *i1, unsigned long long *sum, int32_t **perm_out,
+                        cudaStream_t s) {
   int grid = (int)((n + 255) / 256);
   if (grid > 16384) grid = 16384;
-  if (bits < 1) bits = 1;
-  if (bits > 32) bits = 32;
-  int kcols = 64 / bits;
-  if (kcols > w) kcols = w;
-  k_pack_keys<<<grid, 256, 0, s>>>(rows, n, w, bits, kcols, k0, i0);
-  k_sort_tiles<<<(unsigned)((n + MS_TILE - 1) / MS_TILE), MS_BLK, 0, s>>>(rows, w, kcols, n, k0, i0);
+  k_pack_keys<KW><<<grid, 256, 0, s>>>(S.rows, n, S.w, bits, cpw, k0, i0, sum);
+  // the sort chain is kernel to kernel: each waits for its predecessor in its prologue
+  launch_pdl(k_sort_tiles<KW>, dim3((unsigned)((n + MS_TILE - 1) / MS_TILE)), dim3(MS_BLK), 0, s, S, n, k0, i0);
   int launches = 2;
   for (int64_t L = MS_TILE; L < n; L *= 2) {
-    k_merge_pass<<<grid, 256, 0, s>>>(rows, w, kcols, n, L, k0, i0, k1, i1);
+    launch_pdl(k_merge_pass<KW>, dim3(grid), dim3(256), 0, s, S, n, L, (const unsigned long long *)k0,
+               (const int32_t *)i0, k1, i1);
     launches++;
     std::swap(k0, k1);
     std::swap(i0, i1);
   }
-  g_launches += launches;
   *perm_out = i0;
+  return launches;
+}
+
+cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
+                       unsigned long long *sum, cudaStream_t s) {
+  if (n <= 0) {
+    *perm_out = (int32_t *)tmp;
+    return cudaSuccess;
+  }
+  if (bits < 1) bits = 1;
+  if (bits > 32) bits = 32;
+  const int cpw = 64 / bits;
+  int kw = (w + cpw - 1) / cpw;
+  if (kw < 1) kw = 1;
+  if (kw > MS_KW) kw = MS_KW;
+  SortKeys S;
+  S.rows = rows;
+  S.w = w;
+  S.packed = kw * cpw < w ? kw * cpw : w;
+  unsigned long long *k0 = (unsigned long long *)tmp;
+  unsigned long long *k1 = k0 + (int64_t)kw * n;
+  int32_t *i0 = (int32_t *)(k1 + (int64_t)kw * n);
+  int32_t *i1 = i0 + n;
+  int launches;
+  switch (kw) {
+    case 1: launches = msort_launch<1>(S, n, bits, cpw, k0, k1, i0, i1, sum, perm_out, s); break;
+    case 2: launches = msort_launch<2>(S, n, bits, cpw, k0, k1, i0, i1, sum, perm_out, s); break;
+    case 3: launches = msort_launch<3>(S, n, bits, cpw, k0, k1, i0, i1, sum, perm_out, s); break;
+    default: launches = msort_launch<4>(S, n, bits, cpw, k0, k1, i0, i1, sum, perm_out, s); break;
+  }
+  g_launches += launches;
   return cudaGetLastError();
 }
 
@@ -221,6 +306,8 @@ __global__ void k_topk_keys_from_scores(const float *sc, int64_t n, unsigned lon
 __global__ void __launch_bounds__(TK_BLK) k_topk_tiles(const unsigned long long *in, int64_t n, int32_t k,
                                                        unsigned long long *out) {
   __shared__ unsigned long long sk[TK_TILE];
+  griddep_wait();
+  griddep_launch_dependents();
   const int64_t base = (int64_t)blockIdx.x * TK_TILE;
   for (int i = threadIdx.x; i < TK_TILE; i += TK_BLK) sk[i] = base + i < n ? in[base + i] : KEY_INF;
   __syncthreads();
@@ -243,6 +330,8 @@ __global__ void __launch_bounds__(TK_BLK) k_topk_tiles(const unsigned long long 
 
 __global__ void k_topk_gather(const unsigned long long *keys, int32_t m, const int32_t *rows, const float *sc,
                               int32_t w, int32_t *orows, float *osc) {
+  griddep_wait();
+  griddep_launch_dependents();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * w;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / w;
@@ -273,7 +362,8 @@ cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t
   while (true) {  // every pass keeps k of each 2048 keys, so m at least halves
     int64_t blocks = (m + TK_TILE - 1) / TK_TILE;
     int32_t keep = (int32_t)(m < k ? m : k);
-    k_topk_tiles<<<(unsigned)blocks, TK_BLK, 0, s>>>(cur, m, keep, other);
+    launch_pdl(k_topk_tiles, dim3((unsigned)blocks), dim3(TK_BLK), 0, s, (const unsigned long long *)cur, m, keep,
+               other);
     launches++;
     m = blocks * keep;
     std::swap(cur, other);
@@ -282,7 +372,8 @@ cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t
   int32_t out_n = (int32_t)(m < k ? m : k);
   int64_t ne = (int64_t)out_n * w;
   int g2 = (int)((ne + 255) / 256);
-  k_topk_gather<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(cur, out_n, rows, sc, w, orows, osc);
+  launch_pdl(k_topk_gather, dim3(g2 > 0 ? g2 : 1), dim3(256), 0, s, (const unsigned long long *)cur, out_n, rows, sc,
+             w, orows, osc);
   launches++;
   g_launches += launches;
   return cudaGetLastError();
