@@ -37,9 +37,10 @@ K_TOP = 100
 BATCH = 32
 WORKLOAD = "C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 10-30 vertices, all embeddings + FP32 scores + top-100"
 
-# Per-launch DRAM traffic of k_join from the ncu capture summarised in profiles/ (None when the
-# kernel changed after the capture).
-JOIN_TRAFFIC_BYTES_PER_LAUNCH = None
+# Per-launch DRAM traffic (read + write bytes) of k_joinw from the ncu capture of the same
+# workload summarised in profiles/ (k_joinw_c2_dram_traffic.md); None where no capture of that
+# workload with the current kernel exists.
+JOIN_TRAFFIC_BYTES_PER_LAUNCH = {"c2": 555406}
 
 
 def parse_args():
@@ -303,9 +304,9 @@ def run_ours(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = acc["join_bytes"] / (acc["join_ms"] / 1e3) / 1e9 if acc["join_ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_join", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "k_joinw", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "traffic": JOIN_TRAFFIC_BYTES_PER_LAUNCH,
+                "traffic": JOIN_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload) if not args.only_path else None,
                 "algorithmic_bytes_per_launch": acc["join_bytes"] / max(1, acc["join_launches"]),
                 "avg_launch_us": 1e3 * acc["join_ms"] / max(1, acc["join_launches"]),
                 "launches": acc["join_launches"]}

@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     if (col < w) ipos[col] = (int8_t)q;
     else npos[col - w] = (int8_t)q;
   }
-  for (int e = lane; e < WT * wsv; e += 32)  // padding words never change afterwards
-    if (e % wsv >= w) W.rows[e] = -1;
+  for (int r = lane; r < WT; r += 32)  // padding words never change afterwards
+    for (int c = w; c < wsv; c++) W.rows[r * wsv + c] = -1;
   __syncthreads();
   griddep_wait();  // everything above touched shared memory only
   griddep_launch_dependents();

@@ -342,6 +342,105 @@ __global__ void k_topk_gather(const unsigned long long *keys, int32_t m, const i
   }
 }
 
+// Top-k of up to TK_SMALL keys in one block: the keys sit in shared memory, an MSD radix
+// select over their 64 bits (8 bits a pass, warp-scanned histogram) finds the k-th smallest,
+// the k keys at or below it are collected and sorted by a bitonic network, and the rows are
+// gathered. One launch instead of the tile passes.
+constexpr int TK_SMALL = 16384;
+constexpr int TK_SBLK = 1024;
+
+__global__ void __launch_bounds__(TK_SBLK) k_topk_small(const float *sc, int32_t n, int32_t k, const int32_t *rows,
+                                                       int32_t w, int32_t *orows, float *osc) {
+  extern __shared__ unsigned long long K[];  // n keys
+  __shared__ unsigned long long C[1024];
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_need, s_cnt;
+  griddep_wait();
+  griddep_launch_dependents();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += TK_SBLK) K[i] = ((unsigned long long)__float_as_uint(__ldg(sc + i)) << 32) | (uint32_t)i;
+  const int kk = k < n ? k : n;
+  if (tid == 0) {
+    s_prefix = 0;
+    s_need = kk;
+    s_cnt = 0;
+  }
+  __syncthreads();
+  unsigned long long T = KEY_INF;  // the kk-th smallest key (all keys when kk == n)
+  if (kk < n) {
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int d = tid; d < 256; d += TK_SBLK) hist[d] = 0;
+      __syncthreads();
+      const unsigned long long hi = shift == 56 ? 0ull : (~0ull << (shift + 8));
+      const unsigned long long pre = s_prefix;
+      for (int i = tid; i < n; i += TK_SBLK)
+        if ((K[i] & hi) == pre) atomicAdd(&hist[(K[i] >> shift) & 255], 1u);
+      __syncthreads();
+      if (warp == 0) {  // lane l holds bins 8l .. 8l+7
+        unsigned b[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          b[j] = hist[8 * lane + j];
+          sum += b[j];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          unsigned v = __shfl_up_sync(FULL_MASK, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const unsigned need = (unsigned)s_need;
+        const unsigned excl = incl - sum;
+        if (excl < need && need <= incl) {  // exactly one lane: the bin holding the need-th key
+          unsigned cum = excl;
+          int d = 0;
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            if (cum + b[j] >= need) {
+              d = j;
+              break;
+            }
+            cum += b[j];
+          }
+          s_prefix = pre | ((unsigned long long)(8 * lane + d) << shift);
+          s_need = (int)(need - cum);
+        }
+      }
+      __syncthreads();
+    }
+    T = s_prefix;
+  }
+  for (int i = tid; i < n; i += TK_SBLK)
+    if (K[i] <= T) C[atomicAdd(&s_cnt, 1)] = K[i];
+  __syncthreads();
+  int P = 1;
+  while (P < kk) P <<= 1;
+  for (int i = kk + tid; i < P; i += TK_SBLK) C[i] = KEY_INF;
+  __syncthreads();
+  for (int q = 2; q <= P; q <<= 1)
+    for (int j = q >> 1; j > 0; j >>= 1) {
+      for (int t = tid; t < P / 2; t += TK_SBLK) {
+        int i = 2 * t - (t & (j - 1));
+        int p = i + j;
+        bool up = (i & q) == 0;
+        if ((C[i] > C[p]) == up) {
+          unsigned long long x = C[i];
+          C[i] = C[p];
+          C[p] = x;
+        }
+      }
+      __syncthreads();
+    }
+  for (int64_t e = tid; e < (int64_t)kk * w; e += TK_SBLK) {
+    const int64_t i = e / w;
+    const int32_t c = (int32_t)(e - i * w);
+    const uint32_t src = (uint32_t)(C[i] & 0xffffffffu);
+    orows[e] = __ldg(rows + (int64_t)src * w + c);
+    if (c == 0 && osc) osc[i] = __ldg(sc + src);
+  }
+}
+
 int64_t topk_tmp_bytes(int64_t n) {
   int64_t tiles = (n + TK_TILE - 1) / TK_TILE;
   return ((n > TK_TILE ? n : TK_TILE) + tiles * TK_TILE) * 8 + 256;
@@ -351,6 +450,16 @@ cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t
                         int32_t *orows, float *osc, cudaStream_t s) {
   if (n <= 0 || k <= 0) return cudaSuccess;
   if (k > TK_TILE / 2) return cudaErrorInvalidValue;
+  if (n <= TK_SMALL) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_topk_small, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMALL * 8);
+      attr = true;
+    }
+    g_launches++;
+    k_topk_small<<<1, TK_SBLK, (size_t)n * 8, s>>>(sc, (int32_t)n, k, rows, w, orows, osc);
+    return cudaGetLastError();
+  }
   unsigned long long *a = (unsigned long long *)tmp;
   unsigned long long *b = a + (n > TK_TILE ? n : TK_TILE);
   int grid = (int)((n + 255) / 256);

@@ -137,6 +137,13 @@ def test_c2_top100(ctx, hh, seed):
     check_topk(ctx, gid, g, I.path(8 + seed), 100)
 
 
+@pytest.mark.parametrize("k_path,k", [(14, 100), (14, 1), (14, 1024), (18, 100), (22, 1024), (22, 7)])
+def test_topk_single_block_and_tiled(ctx, hh, k_path, k):
+    # 10856 rows take the single-block select, 31448 and 84724 the tile passes
+    g, gid = hh
+    check_topk(ctx, gid, g, I.path(k_path), k)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_match_topk_one_pass(ctx, hh, B, seed):
     g, gid = hh
