@@ -56,8 +56,8 @@ typedef int32_t dm_graph;
  * M4-1 has centre 0 and leaves 1, 2, 3; M6-2O is the 2 x 3 grid 0-1-2 / 3-4-5 with rungs
  * 0-3, 1-4, 2-5; M18-O-6 is the 12-cycle 0..11 plus pendant vertex 12 + i/2 on each even
  * cycle vertex i. */
-#define DM_MOTIF_PATH(k) (k)           /* k = 2..16: M_k, M2 is a single edge */
-#define DM_MOTIF_CYCLE(k) (100 + (k))  /* k = 3..16: M_{k-O} */
+#define DM_MOTIF_PATH(k) (k)           /* k = 2..24: M_k, M2 is a single edge */
+#define DM_MOTIF_CYCLE(k) (100 + (k))  /* k = 3..24: M_{k-O} */
 #define DM_MOTIF_M4_1 201              /* claw K_{1,3} */
 #define DM_MOTIF_M6_2O 202             /* two 4-cycles sharing an edge (2 x 3 grid) */
 #define DM_MOTIF_M18_O_6 203           /* 12-cycle with a pendant on every other vertex */
@@ -123,6 +123,18 @@ int dm_plan(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
             const int32_t *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out);
 
 void dm_plan_free(dm_plan_t *plan);
+
+/* The candidate decompositions that DM_ORDER_LEARNED chooses from (Sec. 3.2 decomposition
+ * with the paper's order and with the greedy heuristic order, over the motif set and, unless
+ * opts->motifs is given, over sets adding a larger motif typical of the topology or two
+ * paths of about half the pattern). Each is a runnable plan with that order fixed; running
+ * them is how a caller logs training steps for every shape the learned planner may pick.
+ * Writes up to max_out handles to out (the caller frees each with dm_plan_free) and returns
+ * the number of candidates, or a negative error (as dm_plan). out may be NULL when
+ * max_out is 0. The paper has no counterpart (its order is fixed by hand). */
+int32_t dm_plan_candidates(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
+                           const int32_t *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out,
+                           int32_t max_out);
 
 /* Flat description of a plan, for inspection and tests. Writes up to buf_len int32 words:
  *   [n_steps, then per step: motif_id, k, slice[0..k-1] (pattern vertex of each motif

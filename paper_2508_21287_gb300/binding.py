@@ -89,6 +89,7 @@ _SIGS = {
     "dm_motif_table": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i64, ctypes.POINTER(_i64), _i32p]),
     "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_free": (None, [_vp]),
+    "dm_plan_candidates": (_i32, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp), _i32]),
     "dm_plan_describe": (_i32, [_vp, _i32p, _i32]),
     "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
     "dm_match_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _u64p, _u64p]),
@@ -215,6 +216,23 @@ def dm_plan(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, order: int
 
 def dm_plan_free(plan) -> None:
     _lib.dm_plan_free(plan)
+
+
+def dm_plan_candidates(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None) -> list:
+    """The candidate plans DM_ORDER_LEARNED chooses from, as plan handles (free each)."""
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    opts = dm_plan_opts()
+    keep = None
+    if motifs:
+        keep = _arr_i32(list(motifs))
+        opts.motifs = _p32(keep)
+        opts.n_motifs = len(keep)
+    n = _lib.dm_plan_candidates(ctx, int(graph), int(n_p), _p32(rp), _p32(ci), ctypes.byref(opts), None, 0)
+    _check(min(n, 0), "dm_plan_candidates", ctx)
+    arr = (_vp * max(1, n))()
+    got = _lib.dm_plan_candidates(ctx, int(graph), int(n_p), _p32(rp), _p32(ci), ctypes.byref(opts), arr, n)
+    _check(min(got, 0), "dm_plan_candidates", ctx)
+    return [_vp(arr[i]) for i in range(got)]
 
 
 def _parse_description(words: list[int]) -> list[dict]:

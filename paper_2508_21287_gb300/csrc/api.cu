@@ -1344,6 +1344,41 @@ int model_predict_plan(void *self, const float *feats, int n, float *out) {
 // Predicted cost of a plan: bytes of every intermediate table it writes (rows from the chain
 // of predicted log growths, model or heuristic) plus 64 KiB per step for launch and barrier
 // overheads; and its largest predicted table.
+// Costs of several plans with one model evaluation over all their steps (see plan_cost).
+int plan_costs(dm_ctx *c, const std::vector<const std::vector<StepSpec> *> &plans, std::vector<double> *cost,
+               std::vector<double> *max_rows) {
+  int total = 0;
+  for (auto *st : plans) total += (int)st->size();
+  std::vector<float> x((size_t)std::max(1, total) * NFEAT), growth(std::max(1, total));
+  int k = 0;
+  for (auto *st : plans)
+    for (auto &s : *st) {
+      model_input(s.feat, &x[(size_t)k * NFEAT]);
+      growth[k] = x[(size_t)k * NFEAT + 22];
+      k++;
+    }
+  if (total > 0) {
+    std::vector<float> xn;
+    normalise(c, x.data(), total, xn);
+    RET(model_run(c, xn.data(), nullptr, total, growth.data(), nullptr, nullptr));
+  }
+  cost->assign(plans.size(), 0.0);
+  max_rows->assign(plans.size(), 0.0);
+  k = 0;
+  for (size_t i = 0; i < plans.size(); i++) {
+    double lr = 0, tot = 0, mx = 0;
+    for (auto &s : *plans[i]) {
+      lr += growth[k++];
+      double rows = exp(std::min(60.0, std::max(-60.0, lr)));
+      mx = std::max(mx, rows);
+      tot += rows * (4.0 * s.w_out + 4.0) + 65536.0;
+    }
+    (*cost)[i] = tot;
+    (*max_rows)[i] = mx;
+  }
+  return DM_OK;
+}
+
 int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, double *cost, double *max_rows) {
   const int n = (int)steps.size();
   std::vector<float> x((size_t)std::max(1, n) * NFEAT), growth(std::max(1, n));
@@ -1365,6 +1400,63 @@ int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, dou
   }
   *cost = total;
   *max_rows = mx;
+  return DM_OK;
+}
+
+// The candidate decompositions DM_ORDER_LEARNED chooses from: the paper's rule and the greedy
+// heuristic order, each over the plan's motif set and over sets with a larger motif typical
+// of the topology (M8 or M12-O at degree <= 3, M6-2O or M6 at degree 4), and, for patterns of
+// 16+ vertices, over a set with two paths of about half the pattern: a long cycle then becomes
+// one path joined with a second path on both of its end vertices (a two-key join) instead of
+// a path grown to nearly the pattern's length and closed by a back-edge. Half-length paths are
+// offered only when their tables are estimated (edges x branching^(k - 2)) at 4M rows or less.
+struct CandidatePlan {
+  std::vector<int32_t> motifs;
+  int order = DM_ORDER_PAPER;
+  std::vector<StepSpec> steps;
+  int32_t col_vertex[MAXW] = {};
+};
+
+int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, GraphStats &gs,
+                    std::vector<CandidatePlan> *out) {
+  std::vector<std::vector<int32_t>> sets{p.motifs};
+  std::vector<int32_t> extra;
+  if (!user_motifs) {
+    if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12)};
+    else if (g->max_deg == 4) extra = {DM_MOTIF_M6_2O, 6};
+    else extra = {4};
+  }
+  for (int id : extra) {
+    RET(ensure_motif(c, g, id));
+    gs.motifs.push_back({id, g->motifs.at(id).n});
+    std::vector<int32_t> set{id};
+    set.insert(set.end(), p.motifs.begin(), p.motifs.end());
+    sets.push_back(set);
+  }
+  if (!user_motifs && p.n_p >= 16) {
+    const int a = p.n_p / 2 + 1, b = (p.n_p + 1) / 2 + 1;
+    const double branch = std::max(1.0, g->avg_deg - 1.0);
+    const double est = (double)g->nnz * pow(branch, (double)(b - 2));
+    if (b <= MAXM && est <= 4.0e6) {
+      std::vector<int32_t> set{b};
+      if (a != b) set.push_back(a);
+      for (int id : set) {
+        RET(ensure_motif(c, g, id));
+        gs.motifs.push_back({id, g->motifs.at(id).n});
+      }
+      set.insert(set.end(), p.motifs.begin(), p.motifs.end());
+      sets.push_back(set);
+    }
+  }
+  out->clear();
+  for (auto &set : sets)
+    for (int ord : {DM_ORDER_PAPER, DM_ORDER_HEURISTIC}) {
+      CandidatePlan cp;
+      cp.motifs = set;
+      cp.order = ord;
+      if (decompose(p, set, ord, gs, nullptr, nullptr, &cp.steps, cp.col_vertex) != DM_OK) continue;
+      out->push_back(std::move(cp));
+    }
   return DM_OK;
 }
 
@@ -1568,9 +1660,15 @@ int dm_motif_table(dm_ctx *c, dm_graph gh, int32_t motif_id, int32_t *out_rows, 
   return DM_OK;
 }
 
-int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
-            const dm_plan_opts *opts, dm_plan_t **out) {
-  if (!c || !out) return DM_E_INVAL;
+}  // extern "C"
+
+namespace {
+
+// Validate the pattern, fill the plan's fields and motif set (preset by the data graph's degree
+// unless given), and make sure the motif tables exist.
+int plan_setup(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
+               const dm_plan_opts *opts, Plan &p, DevGraph **gout, GraphStats &gs) {
+  if (!c) return DM_E_INVAL;
   DevGraph *g = get_graph(c, gh);
   if (!g) return DM_E_NOTFOUND;
   if (n_p < 1 || n_p > MAXW) return DM_E_INVAL;
@@ -1579,8 +1677,6 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
   HostCSR h;
   RET(validate_csr(n_p, p_row_ptr, p_col_idx, nullptr, &h));
   if (!connected(h, n_p)) return DM_E_DISCONNECTED;
-  std::unique_ptr<dm_plan_t> pl(new dm_plan_t());
-  Plan &p = pl->p;
   p.n_p = n_p;
   p.rp = h.rp;
   p.ci = h.ci;
@@ -1598,7 +1694,6 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
   } else {
     p.motifs = {3, 2};
   }
-  GraphStats gs;
   gs.V = g->V;
   gs.nnz = g->nnz;
   gs.avg_deg = g->avg_deg;
@@ -1610,56 +1705,95 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
     gs.motifs.push_back({id, g->motifs.at(id).n});
   }
   if (n_p == 1) RET(ensure_motif(c, g, MOTIF_VERTEX));
-  const bool learned = p.order == DM_ORDER_LEARNED && c->m_trained;
-  if (!learned) {
-    RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, nullptr, nullptr,
-                  &p.steps, p.col_vertex));
-    RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows));
-  } else {
-    // The trained model picks the plan: candidate decompositions (the paper's rule and the
-    // greedy heuristic, over the motif set and over topology-typical larger motifs) are
-    // costed with the model's per-step cardinalities and the cheapest is kept.
-    std::vector<std::vector<int32_t>> sets{p.motifs};
-    std::vector<int32_t> extra;
-    if (!(opts && opts->motifs && opts->n_motifs > 0)) {
-      if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12)};
-      else if (g->max_deg == 4) extra = {DM_MOTIF_M6_2O, 6};
-      else extra = {4};
-    }
-    for (int id : extra) {
-      RET(ensure_motif(c, g, id));
-      gs.motifs.push_back({id, g->motifs.at(id).n});
-      std::vector<int32_t> set{id};
-      set.insert(set.end(), p.motifs.begin(), p.motifs.end());
-      sets.push_back(set);
-    }
-    double best = 1e308;
-    for (auto &set : sets)
-      for (int ord : {DM_ORDER_PAPER, DM_ORDER_HEURISTIC}) {
-        std::vector<StepSpec> steps;
-        int32_t colv[MAXW];
-        if (decompose(p, set, ord, gs, nullptr, nullptr, &steps, colv) != DM_OK) continue;
-        double cost, maxr;
-        RET(plan_cost(c, steps, true, &cost, &maxr));
-        if (cost < best) {
-          best = cost;
-          p.steps = steps;
-          memcpy(p.col_vertex, colv, sizeof(colv));
-          p.pred_cost = cost;
-          p.pred_max_rows = maxr;
-          p.motifs = set;
-        }
-      }
-    if (p.steps.empty()) return DM_E_INVAL;
-  }
+  *gout = g;
+  return DM_OK;
+}
+
+// A decomposed plan is runnable once its step count fits and every step's index exists.
+int plan_finish(dm_ctx *c, DevGraph *g, const Plan &p) {
+  if (p.steps.empty()) return DM_E_INVAL;
   if ((int)p.steps.size() > DM_MAX_STEPS) return DM_E_CAPACITY;
   for (size_t j = 1; j < p.steps.size(); j++) {
     Index *ix;
     const StepSpec &s = p.steps[j];
     RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1, &ix));
   }
+  return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
+            const dm_plan_opts *opts, dm_plan_t **out) {
+  if (!c || !out) return DM_E_INVAL;
+  std::unique_ptr<dm_plan_t> pl(new dm_plan_t());
+  Plan &p = pl->p;
+  DevGraph *g = nullptr;
+  GraphStats gs;
+  RET(plan_setup(c, gh, n_p, p_row_ptr, p_col_idx, opts, p, &g, gs));
+  const bool learned = p.order == DM_ORDER_LEARNED && c->m_trained;
+  if (!learned) {
+    RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, nullptr, nullptr,
+                  &p.steps, p.col_vertex));
+    RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows));
+  } else {
+    // The trained model picks the plan among the candidate decompositions, costed with the
+    // model's per-step cardinalities.
+    std::vector<CandidatePlan> cands;
+    RET(candidate_plans(c, g, p, opts && opts->motifs && opts->n_motifs > 0, gs, &cands));
+    std::vector<const std::vector<StepSpec> *> steps;
+    for (auto &cp : cands) steps.push_back(&cp.steps);
+    std::vector<double> cost, maxr;
+    RET(plan_costs(c, steps, &cost, &maxr));  // one model evaluation for every candidate
+    double best = 1e308;
+    for (size_t i = 0; i < cands.size(); i++) {
+      if (cost[i] < best) {
+        best = cost[i];
+        p.steps = cands[i].steps;
+        memcpy(p.col_vertex, cands[i].col_vertex, sizeof(cands[i].col_vertex));
+        p.pred_cost = cost[i];
+        p.pred_max_rows = maxr[i];
+        p.motifs = cands[i].motifs;
+      }
+    }
+  }
+  RET(plan_finish(c, g, p));
   *out = pl.release();
   return DM_OK;
+}
+
+int32_t dm_plan_candidates(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col_idx,
+                           const dm_plan_opts *opts, dm_plan_t **out, int32_t max_out) {
+  if (!c || max_out < 0 || (max_out > 0 && !out)) return DM_E_INVAL;
+  Plan base;
+  DevGraph *g = nullptr;
+  GraphStats gs;
+  RET(plan_setup(c, gh, n_p, p_row_ptr, p_col_idx, opts, base, &g, gs));
+  std::vector<CandidatePlan> cands;
+  RET(candidate_plans(c, g, base, opts && opts->motifs && opts->n_motifs > 0, gs, &cands));
+  const int32_t n = (int32_t)cands.size();
+  for (int32_t i = 0; i < n && i < max_out; i++) {
+    std::unique_ptr<dm_plan_t> pl(new dm_plan_t());
+    Plan &p = pl->p;
+    p = base;
+    p.order = cands[i].order;
+    p.motifs = cands[i].motifs;
+    p.steps = cands[i].steps;
+    memcpy(p.col_vertex, cands[i].col_vertex, sizeof(p.col_vertex));
+    int r = plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows);
+    if (r == DM_OK) r = plan_finish(c, g, p);
+    if (r != DM_OK) {
+      for (int32_t j = 0; j < i; j++) {
+        delete out[j];
+        out[j] = nullptr;
+      }
+      return r;
+    }
+    out[i] = pl.release();
+  }
+  return n;
 }
 
 void dm_plan_free(dm_plan_t *p) { delete p; }

@@ -9,7 +9,7 @@
 namespace dmi {
 
 constexpr int MAXW = 64;   // pattern vertices = maximum row width of an intermediate table
-constexpr int MAXM = 20;   // motif vertices
+constexpr int MAXM = 24;   // motif vertices
 constexpr int MAXBE = 64;  // back-edge checks in one step
 constexpr int MAXSTEPS = 128;
 

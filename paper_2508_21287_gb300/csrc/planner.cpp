@@ -41,11 +41,11 @@ bool motif_def(int id, MotifDef *out) {
   if (id == MOTIF_VERTEX) {
     m.k = 1;
     m.name = "M1";
-  } else if (id >= 2 && id <= 16) {  // M_k: path on k vertices
+  } else if (id >= 2 && id <= MAXM) {  // M_k: path on k vertices
     m.k = id;
     for (int i = 0; i + 1 < id; i++) add_edge(&m, i, i + 1);
     m.name = "M" + std::to_string(id);
-  } else if (id >= 103 && id <= 116) {  // M_{k-O}: k-cycle
+  } else if (id >= 103 && id <= 100 + MAXM) {  // M_{k-O}: k-cycle
     m.k = id - 100;
     for (int i = 0; i < m.k; i++) add_edge(&m, i, (i + 1) % m.k);
     m.name = "M" + std::to_string(m.k) + "-O";

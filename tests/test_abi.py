@@ -55,6 +55,19 @@ def test_six_cycle_example(B):
     assert set(s0) | set(s1) == set(range(6))
 
 
+@pytest.mark.parametrize("n", [16, 31, 40, 46])
+def test_long_cycle_as_two_half_paths(B, n):
+    # the 6-cycle example scaled up: with paths of about half the cycle in the motif set the
+    # cycle is one path slice joined with a second path on both end vertices
+    from paper_2508_21287_gb300 import inputs as I
+    c = I.cycle(n)
+    a, b = n // 2 + 1, (n + 1) // 2 + 1
+    d = B.dm_decompose(n, c.row_ptr, c.col_idx, sorted({a, b}, reverse=True) + [4])
+    assert [s["motif"] for s in d] == [b, a]
+    assert d[1]["n_keys"] == 2 and not d[0]["backedges"] and not d[1]["backedges"]
+    assert set(d[0]["slice"]) | set(d[1]["slice"]) == set(range(n))
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_m2_only_iterations_equal_edge_count(B, seed):
     # Sec. 4.2: with M2 alone the number of join-and-filter iterations equals |E_p|; here a

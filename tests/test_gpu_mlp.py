@@ -59,8 +59,10 @@ def test_training_beats_the_heuristic(B):
     with B.Context(0) as ctx:
         gid = ctx.load(g)
         B.dm_step_log(ctx.h, clear=True)
-        _log_steps(B, ctx, gid, train, B.DM_ORDER_HEURISTIC)
-        _log_steps(B, ctx, gid, train, B.DM_ORDER_PAPER)
+        for p in train:  # every candidate plan the learned planner weighs
+            for pl in B.dm_plan_candidates(ctx.h, gid, p.n, p.row_ptr, p.col_idx):
+                B.dm_match(ctx.h, pl, B.DM_COUNT)
+                B.dm_plan_free(pl)
         f, t = B.dm_step_log(ctx.h, clear=True)
         assert len(t) > 1000
         B.dm_model_init(ctx.h, 3)
@@ -80,6 +82,12 @@ def test_training_beats_the_heuristic(B):
         for p, (c, s) in zip(held[:40], got):
             ref = oracle.enumerate(g, p, rows=False, threads=8)
             assert (c, s) == (ref.count, ref.checksum)
+        # long cycles: whichever candidate the model picks, the result is the oracle's
+        for n in (36, 40):
+            c = I.cycle(n)
+            got = _log_steps(B, ctx, gid, [c], B.DM_ORDER_LEARNED)[0]
+            ref = oracle.enumerate(g, c, rows=False, threads=8)
+            assert got == (ref.count, ref.checksum)
         # checkpoint: weights out and back in give the same predictions
         w = B.dm_model_weights(ctx.h)
         B.dm_model_init(ctx.h, 99)

@@ -210,6 +210,23 @@ def test_small_budget_streams(B, hh):
         assert c.stats()["chunks"] > c.stats()["n_steps"]
 
 
+@pytest.mark.parametrize("n", [24, 36])
+def test_long_cycle_two_key_path_join(ctx, hh, n):
+    # a cycle as two half-length path slices joined on both end vertices (hashed 2-key index)
+    g, gid = hh
+    check_all(ctx, gid, g, I.cycle(n), motifs=sorted({(n + 1) // 2 + 1, n // 2 + 1}, reverse=True) + [4])
+
+
+def test_cycle40_half_paths_count(ctx):
+    g = I.heavy_hex(12, 6)
+    gid = ctx.load(g)
+    plan = ctx.plan(gid, I.cycle(40), motifs=[21, 4])
+    assert [s["motif"] for s in plan.describe()][:2] == [21, 21]
+    cnt, cs = plan.count()
+    ref = oracle.enumerate(g, I.cycle(40), rows=False, threads=8)
+    assert cnt == ref.count == 402240 and cs == ref.checksum
+
+
 # ------------------------------------------------------------------ larger heavy-hex -------
 @pytest.mark.parametrize("m,n", [(12, 15), (27, 28)])
 def test_scaling_counts(ctx, m, n):
