@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
-    ap.add_argument("--rates", default="250,500,1000,2000", help="c5: Poisson arrival rates (requests/s)")
+    ap.add_argument("--rates", default="250,500,1000,2000,4000,8000", help="c5: Poisson arrival rates (requests/s)")
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
     ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
@@ -359,6 +359,27 @@ def train_model(B, ctx, gid, g, n_train: int = 300):
             "heldout_mae_heuristic": float(np.mean(np.abs(fh[:, 22] - th)))}
 
 
+def train_model_graphs(B, ctx, gids, n_train: int = 120, max_rows: int = 4_000_000):
+    """Train the cardinality model for several graphs: every candidate plan of patterns
+    disjoint from the benchmark's (seeds 300000+) on each graph, each run under a work cap
+    (runs over the cap log nothing). Returns the model's flat weights."""
+    from paper_2508_21287_gb300 import inputs as I
+    B.dm_step_log(ctx.h, clear=True)
+    for gi, gid in enumerate(gids):
+        for s in range(300000 + 1000 * gi, 300000 + 1000 * gi + n_train):
+            p = I.mixed_pattern(s, 5, 40)
+            for pl in B.dm_plan_candidates(ctx.h, gid, p.n, p.row_ptr, p.col_idx, max_rows=max_rows):
+                try:
+                    B.dm_match(ctx.h, pl, B.DM_COUNT)
+                except B.DMError:
+                    pass
+                B.dm_plan_free(pl)
+    f, t = B.dm_step_log(ctx.h, clear=True)
+    B.dm_model_init(ctx.h, 3)
+    B.dm_model_train(ctx.h, f, t, epochs=60, batch=256, lr=2e-3, seed=3)
+    return B.dm_model_weights(ctx.h), int(len(t))
+
+
 def run_c4(args):
     """C4: 512 uneven patterns on one graph. Plain form: one dm_match per pattern, each timed
     alone. Batched: every pattern in one persistent launch (dm_match_batch). Batched+learned:
@@ -479,18 +500,33 @@ def run_c5(args):
     from paper_2508_21287_gb300 import inputs as I
     graphs = [I.lognormal_weights(I.heavy_hex(4, 6), seed=11), I.lognormal_weights(I.grid(32, 32), seed=12),
               I.lognormal_weights(I.random_regular3(2048, 13), seed=13)]
-    srv = B.dm_server_create(local, n_slots=8, mem_budget_bytes=32 << 30, max_rows=4_000_000)
-    gids = [B.dm_server_load_graph(srv, g.n, g.row_ptr, g.col_idx, g.edge_err) for g in graphs]
+    # the cardinality model for the learned order: trained once, on patterns disjoint from the
+    # requests, on a context of its own
+    tctx = B.Context(local)
+    tg = [tctx.load(g) for g in graphs]
+    t0 = time.perf_counter()
+    weights, n_samples = train_model_graphs(B, tctx, tg)
+    train_s = time.perf_counter() - t0
+    tctx.close()
     rates = [float(x) for x in args.rates.split(",")]
     n_req = 400
 
     def make(seed0):
         return [(i % 3, I.mixed_pattern(seed0 + i, 5, 60)) for i in range(n_req)]
 
-    for gi, p in make(900000)[:60]:  # warm-up: motif tables and indices in every slot
-        B.dm_server_wait(srv, B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10), 10, p.n)
-    sweep = []
-    with ClockSampler(local) as clk:
+    def serve(order):
+        srv = B.dm_server_create(local, n_slots=8, mem_budget_bytes=32 << 30, max_rows=4_000_000, order=order)
+        gids = [B.dm_server_load_graph(srv, g.n, g.row_ptr, g.col_idx, g.edge_err) for g in graphs]
+        if order == B.DM_ORDER_LEARNED:
+            B.dm_server_set_model(srv, weights)
+        for gi, p in make(900000)[:60]:  # warm-up: motif tables and indices in every slot
+            B.dm_server_wait(srv, B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10), 10, p.n)
+        sweep = sweep_rates(srv, gids)
+        B.dm_server_destroy(srv)
+        return sweep
+
+    def sweep_rates(srv, gids):
+        sweep = []
         reqs = make(rank * 1000000)  # the same requests at every rate
         for ri, lam in enumerate(rates):
             gaps = np.random.default_rng(ri).exponential(1.0 / lam, n_req)
@@ -517,7 +553,11 @@ def run_c5(args):
             sweep.append({"rate": lam, "completed_per_s": len(ok) / wall, "p50_ms": pick(0.5), "p99_ms": pick(0.99),
                           "rejected": sum(a["status"] == B.DM_E_CAPACITY for a in ans) / n_req,
                           "failed": sum(a["status"] not in (0, B.DM_E_CAPACITY) for a in ans), "wall_s": wall})
-    B.dm_server_destroy(srv)
+        return sweep
+
+    with ClockSampler(local) as clk:
+        sweep = serve(B.DM_ORDER_LEARNED)
+        sweep_paper = serve(B.DM_ORDER_PAPER)
     top = sweep[-1]
     line = {"metric": "requests/sec", "value": top["completed_per_s"], "unit": "requests/s", "n_gpus": world,
             "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True,
@@ -525,7 +565,8 @@ def run_c5(args):
             "config": {"workload": WORKLOAD_C5, "requests_per_rate": n_req, "slots": 8, "max_rows": 4_000_000,
                        "pool_bytes": 32 << 30, "parallelism": "replicas"},
             "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "rejected_fraction": top["rejected"],
-            "sweep": sweep, "clocks": clk.summary(), "e2e": None}
+            "order": "learned", "sweep": sweep, "sweep_paper_order": sweep_paper,
+            "model": {"samples": n_samples, "train_s": train_s}, "clocks": clk.summary(), "e2e": None}
     if rank == 0:
         print(json.dumps(line))
     return 0

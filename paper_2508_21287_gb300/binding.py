@@ -218,10 +218,11 @@ def dm_plan_free(plan) -> None:
     _lib.dm_plan_free(plan)
 
 
-def dm_plan_candidates(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None) -> list:
+def dm_plan_candidates(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, max_rows: int = 0) -> list:
     """The candidate plans DM_ORDER_LEARNED chooses from, as plan handles (free each)."""
     rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
     opts = dm_plan_opts()
+    opts.max_rows = int(max_rows)
     keep = None
     if motifs:
         keep = _arr_i32(list(motifs))

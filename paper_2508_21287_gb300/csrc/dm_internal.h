@@ -101,7 +101,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
               int32_t *col_vertex);
 
 // Features of a candidate step (for the heuristic and the learned model).
-void step_features(const StepSpec &s, double log_rows_prev, int n_p, int mapped_before,
+void step_features(const StepSpec &s, int n_edges, double log_rows_prev, int n_p, int mapped_before,
                    int uncovered_before, const GraphStats &gs, float *feat);
 double heuristic_log_rows(const float *feat);
 

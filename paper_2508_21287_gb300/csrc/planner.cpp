@@ -203,17 +203,15 @@ static void apply_step(const MotifDef &m, const StepSpec &s, PState *st) {
   }
 }
 
-void step_features(const StepSpec &s, double log_rows_prev, int n_p, int mapped_before,
+void step_features(const StepSpec &s, int n_edges, double log_rows_prev, int n_p, int mapped_before,
                    int uncovered_before, const GraphStats &gs, float *f) {
   memset(f, 0, sizeof(float) * NFEAT);
   double T = 1.0;
   for (auto &ms : gs.motifs)
     if (ms.id == s.motif) T = (double)std::max<int64_t>(1, ms.rows);
   double V = std::max(1, gs.V);
-  bool cyc = s.motif >= 103 && s.motif <= 116;
-  bool pth = s.motif >= 2 && s.motif <= 16;
-  MotifDef md;
-  int n_edges = motif_def(s.motif, &md) ? (int)md.edges.size() : 0;
+  bool cyc = s.motif >= 103 && s.motif <= 100 + MAXM;
+  bool pth = s.motif >= 2 && s.motif <= MAXM;
   f[0] = (float)log_rows_prev;
   f[1] = (float)log(T);
   f[2] = (float)log(V);
@@ -320,49 +318,41 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
         }
       }
       if (found) {
-        step_features(best, log_rows, pat.n_p, popc64(st.mapped), st.uncovered_edges, gs, best.feat);
+        MotifDef bd;
+        motif_def(best.motif, &bd);
+        step_features(best, (int)bd.edges.size(), log_rows, pat.n_p, popc64(st.mapped), st.uncovered_edges, gs,
+                      best.feat);
         best.est_rows = exp(heuristic_log_rows(best.feat));
       }
     } else {
-      std::vector<StepSpec> cands;
+      // greedy: the match with the smallest estimated growth per new vertex (independence
+      // estimate); ties: the larger motif, then enumeration order
+      double bscore = 1e300;
+      const int mapped_before = popc64(st.mapped);
+      StepSpec s;
+      float f[NFEAT];
       for (auto &m : defs) {
         int img[MAXM];
         long long budget = 400000;
         int taken = 0;
-        auto f = [&](const int *im) {
-          StepSpec s;
+        const int n_edges = (int)m.edges.size();
+        auto visit = [&](const int *im) {
           make_step(m, im, st, &s);
           if (s.n_be > MAXBE) return true;
-          cands.push_back(s);
+          step_features(s, n_edges, log_rows, pat.n_p, mapped_before, st.uncovered_edges, gs, f);
+          const double growth = ((double)heuristic_log_rows(f) - log_rows) / std::max(1, s.n_new);
+          if (!found || growth < bscore - 1e-9 || (fabs(growth - bscore) <= 1e-9 && s.k > best.k)) {
+            bscore = growth;
+            best = s;
+            memcpy(best.feat, f, sizeof(f));
+            found = true;
+          }
           return ++taken < 256;
         };
-        match_rec(m, st, !first, 0, img, 0, budget, f);
+        match_rec(m, st, !first, 0, img, 0, budget, visit);
       }
-      if (cands.empty()) return DM_E_INVAL;
-      std::vector<float> feats(cands.size() * NFEAT);
-      for (size_t i = 0; i < cands.size(); i++) {
-        step_features(cands[i], log_rows, pat.n_p, popc64(st.mapped), st.uncovered_edges, gs,
-                      &feats[i * NFEAT]);
-        memcpy(cands[i].feat, &feats[i * NFEAT], sizeof(float) * NFEAT);
-      }
-      std::vector<float> pred(cands.size());
-      bool learned = order == DM_ORDER_LEARNED && model &&
-                     model(model_self, feats.data(), (int)cands.size(), pred.data()) == 0;
-      if (!learned)
-        for (size_t i = 0; i < cands.size(); i++) pred[i] = (float)heuristic_log_rows(&feats[i * NFEAT]);
-      size_t bi = 0;
-      double bscore = 1e300;
-      for (size_t i = 0; i < cands.size(); i++) {
-        double growth = ((double)pred[i] - log_rows) / std::max(1, cands[i].n_new);
-        // prefer lower growth per new vertex; ties: larger motif, then enumeration order
-        if (growth < bscore - 1e-9 || (fabs(growth - bscore) <= 1e-9 && cands[i].k > cands[bi].k)) {
-          bscore = growth;
-          bi = i;
-        }
-      }
-      best = cands[bi];
-      best.est_rows = exp((double)pred[bi]);
-      found = true;
+      if (!found) return DM_E_INVAL;
+      best.est_rows = exp(heuristic_log_rows(best.feat));
     }
     if (!found) return DM_E_INVAL;
     if (best.n_be > MAXBE) return DM_E_INVAL;
