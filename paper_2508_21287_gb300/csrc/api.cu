@@ -1102,6 +1102,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   std::vector<std::pair<double, dmk::BatchItem>> items;
   std::vector<int64_t> cap(MAXSTEPS, 0), maxw(MAXSTEPS, 0);
   int ws_max = 1;
+  bool wide = false;  // some step maps more than 4 new vertices
   for (int32_t i = 0; i < n; i++) {
     if (plans[i]->p.pred_max_rows > heavy_rows) {  // runs step by step after the launch
       b->heavy.push_back(i);
@@ -1129,6 +1130,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
       a.prune = INFINITY;
       args.push_back(a);
       ws_max = std::max(ws_max, join_row_stride(a.w));
+      wide |= j > 0 && a.n_new > 4;
       maxw[j] = std::max<int64_t>(maxw[j], a.wo);
       if (j > 0) cap[j] = std::max<int64_t>(cap[j], (int64_t)TR * ex.st[j].max_group);
       cost += ex.p->steps[j].est_rows;
@@ -1159,8 +1161,14 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   P.cta_bytes = off;
   P.TR = TR;
   P.ws_max = ws_max;
+  // wide steps test injectivity in per-row id bitmaps when the graph is small enough for them
+  P.bm_words = 0;
+  if (wide && g->V <= 2048) {
+    const int bw = (g->V + 63) / 64;
+    if (dmk::batch_smem_bytes(TR, ws_max, bw) <= 160 * 1024) P.bm_words = bw;
+  }
   P.n_items = (int64_t)hitems.size();
-  b->grid = dmk::batch_grid(TR, ws_max, c->num_sms);
+  b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms);
   while (b->grid > c->num_sms && (uint64_t)b->grid * P.cta_bytes > c->budget / 2) b->grid /= 2;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) {

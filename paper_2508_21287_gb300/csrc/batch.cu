@@ -62,7 +62,12 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
   __shared__ long long s_item;
   __shared__ int64_t n_lvl[MAXSTEPS], cur[MAXSTEPS];
 
-  const JoinSmem S = join_smem(smem, P.TR, P.ws_max, BATCH_BLK * 4, 1);
+  JoinSmem S = join_smem(smem, P.TR, P.ws_max, BATCH_BLK * 4, 1);
+  if (P.bm_words > 0) {
+    size_t offs[7];
+    S.bm = (unsigned long long *)(smem + join_smem_layout(P.TR, P.ws_max, BATCH_BLK * 4, 1, offs));
+    S.bmw = P.bm_words;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.start_ns = globaltimer_ns();
   unsigned char *mine = P.scratch + (int64_t)blockIdx.x * P.cta_bytes;
   TileOut o;
@@ -136,13 +141,13 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
   }
 }
 
-size_t batch_smem_bytes(int tile_rows, int ws_max) {
+size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words) {
   size_t offs[7];
-  return join_smem_layout(tile_rows, ws_max, BATCH_BLK * 4, 1, offs);
+  return join_smem_layout(tile_rows, ws_max, BATCH_BLK * 4, 1, offs) + (size_t)tile_rows * bm_words * 8;
 }
 
-int batch_grid(int tile_rows, int ws_max, int num_sms) {
-  size_t smem = batch_smem_bytes(tile_rows, ws_max);
+int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms) {
+  size_t smem = batch_smem_bytes(tile_rows, ws_max, bm_words);
   cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_BLK, smem);
@@ -151,7 +156,7 @@ int batch_grid(int tile_rows, int ws_max, int num_sms) {
 }
 
 cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s) {
-  size_t smem = batch_smem_bytes(p.TR, p.ws_max);
+  size_t smem = batch_smem_bytes(p.TR, p.ws_max, p.bm_words);
   cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   g_launches++;
   k_batch<<<grid, BATCH_BLK, smem, s>>>(p);

@@ -193,6 +193,8 @@ struct JoinSmem {
   int16_t *code;  // per output position: working column (< 0x100: from the R row) or 0x100 | motif position
   int8_t *ipos;   // per R column: its output position (-1: none)
   int8_t *npos;   // per new vertex: its output position
+  unsigned long long *bm;  // optional: per tile row, a bitmap of its vertex ids (bmw words a row)
+  int bmw;
 };
 
 __host__ __device__ __forceinline__ size_t join_smem_layout(int TR, int ws, int BLKCPT, int nbuf, size_t *offs) {
@@ -232,6 +234,8 @@ __device__ __forceinline__ JoinSmem join_smem(unsigned char *smem, int TR, int w
   m.code = (int16_t *)(m.cand_row + BLKCPT);
   m.ipos = (int8_t *)(m.code + MAXW);
   m.npos = m.ipos + MAXW;
+  m.bm = nullptr;
+  m.bmw = 0;
   return m;
 }
 
@@ -274,9 +278,16 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
   bool ok = true;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
   if (ok && !seed) {  // FilterOverlappingNodes: new vertices must not repeat a mapped one
+    if (MAXNEW > 4 && S.bm) {  // many new vertices: one bit test each in the row's id bitmap
+      const unsigned long long *b = S.bm + (size_t)r * S.bmw;
 #pragma unroll
-    for (int i = 0; i < MAXNEW; i++)
-      if (i < a.n_new && ok) ok = !row_has(rrow, a.w, nv[i]);
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new && ok) ok = !((b[nv[i] >> 6] >> (nv[i] & 63)) & 1ull);
+    } else {
+#pragma unroll
+      for (int i = 0; i < MAXNEW; i++)
+        if (i < a.n_new && ok) ok = !row_has(rrow, a.w, nv[i]);
+    }
   }
   sc = 0.f;
   if (a.scored) {
@@ -353,6 +364,11 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
       const int32_t *row = tile + tid * ws;
       if (MODE == 1) {  // checksum terms of the row's own columns
         S.part[tid] = row_terms(row, w, S.ipos);
+      }
+      if (MAXNEW > 4 && S.bm) {  // the row's id bitmap (ids < 64 * bmw)
+        unsigned long long *b = S.bm + (size_t)tid * S.bmw;
+        for (int q = 0; q < S.bmw; q++) b[q] = 0ull;
+        for (int c = 0; c < w; c++) b[row[c] >> 6] |= 1ull << (row[c] & 63);
       }
       ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
     }

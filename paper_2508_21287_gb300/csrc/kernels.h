@@ -127,13 +127,15 @@ struct BatchParams {
   int64_t lvl_off[dmi::MAXSTEPS]; // byte offset of level j inside a CTA's scratch
   int64_t lvl_cap[dmi::MAXSTEPS]; // rows level j can hold
   int TR;                         // rows per tile
-  int ws_max;                     // odd shared-memory row stride covering every step
+  int ws_max;                     // shared-memory row stride covering every step
+  int bm_words;                   // > 0: per tile row, a bitmap of its ids (ids < 64 * bm_words) for
+                                  // the injectivity test of steps with many new vertices
   unsigned long long *plan_left;  // work items still open per plan (set before the launch)
   unsigned long long *plan_done;  // GPU global-timer time at which each plan's last item ended
   unsigned long long *start_ns;   // GPU global-timer time at the start of the launch
 };
-size_t batch_smem_bytes(int tile_rows, int ws_max);
-int batch_grid(int tile_rows, int ws_max, int num_sms);
+size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words);
+int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms);
 cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s);
 
 // Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.

@@ -51,6 +51,27 @@ def test_batch_mixed_heavy_hex(B):
         assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
 
 
+def test_batch_candidate_plans_with_wide_steps(B):
+    # every candidate plan of long cycles and mixed patterns: half-length path slices map up
+    # to 19 new vertices a step, tested in per-row id bitmaps inside the batch kernel
+    g = I.heavy_hex(12, 6)
+    pats = [I.cycle(n) for n in (24, 30, 36, 39, 40)] + [I.mixed_pattern(s, 16, 40) for s in range(20)]
+    with B.Context(0) as ctx:
+        gid = ctx.load(g)
+        plans, owner = [], []
+        for i, p in enumerate(pats):
+            for pl in B.dm_plan_candidates(ctx.h, gid, p.n, p.row_ptr, p.col_idx):
+                plans.append(pl)
+                owner.append(i)
+        assert any(max(s["motif"] for s in B.dm_plan_describe(pl)) > 8 for pl in plans)
+        counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+        refs = [oracle.enumerate(g, p, rows=False, threads=8) for p in pats]
+        for i, c, s in zip(owner, counts.tolist(), sums.tolist()):
+            assert (c, s) == (refs[i].count, refs[i].checksum), pats[i].name
+        for pl in plans:
+            B.dm_plan_free(pl)
+
+
 def test_batch_paths_and_patches(B):
     g = I.heavy_hex(8, 9)
     pats = [I.path(k) for k in (2, 3, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]
