@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
-    ap.add_argument("--rates", default="250,500,1000,2000,4000,8000", help="c5: Poisson arrival rates (requests/s)")
+    ap.add_argument("--rates", default="500,2000,8000,16000,32000", help="c5: Poisson arrival rates (requests/s)")
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
     ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
@@ -509,7 +509,7 @@ def run_c5(args):
     train_s = time.perf_counter() - t0
     tctx.close()
     rates = [float(x) for x in args.rates.split(",")]
-    n_req = 400
+    n_req = 1000
 
     def make(seed0):
         return [(i % 3, I.mixed_pattern(seed0 + i, 5, 60)) for i in range(n_req)]
