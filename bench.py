@@ -225,7 +225,8 @@ def run_ours(args):
     B.dm_enable_timing(ctx.h, True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0}
+    acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0, "chunks": 0,
+           "max_rows": 0}
 
     def step(host_rows: bool, record: bool):
         emb = 0
@@ -248,6 +249,8 @@ def run_ours(args):
                 acc["join_bytes"] += st["join_bytes"]
                 acc["join_launches"] += st["join_launches"]
                 acc["launches"] += st["kernel_launches"]
+                acc["chunks"] += st["chunks"]
+                acc["max_rows"] = max(acc["max_rows"], st["max_rows"])
             emb += cnt
         return emb
 
@@ -317,7 +320,8 @@ def run_ours(args):
             "config": {"workload": wl_name(args), "queries_per_step": len(pats), "embeddings_per_step": emb_total / args.steps / world,
                        "data_graph": f"heavy-hex {'4x6' if not count_mode else args.hh.replace(',', 'x')}", "motifs": "M4,M2",
                        "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "join_chunks_per_step": acc["chunks"] / args.steps, "largest_table_rows": acc["max_rows"]},
             "e2e": e2e, "gpu_launches": acc["launches"], "clocks": clocks, "roofline": roofline}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(g, pats, count_only=count_mode)

@@ -585,20 +585,31 @@ struct Exec {
     CK(dmk::scan_i32(in_next, pre, in.n, tmp, c->stream));
     int64_t step = std::max<int64_t>(1, lim - st[j].max_group);
     int64_t nch = (cand_total + step - 1) / step;
-    std::vector<int64_t> hpre(in.n + 1);
-    // boundaries: the last row index whose prefix is <= i * step
-    CK(cudaMemcpyAsync(hpre.data(), pre, sizeof(int64_t) * (in.n + 1), cudaMemcpyDeviceToHost, c->stream));
+    // boundaries (the last row index whose prefix is <= i * step) found on the device; only
+    // the nch + 1 boundaries and their prefixes come back
+    int64_t *dbound = nullptr;
+    RET(dalloc_t(c, &dbound, 2 * (nch + 2)));
+    CK(dmk::launch_chunk_bounds(pre, in.n, step, nch, dbound, dbound + nch + 1, c->stream));
+    std::vector<int64_t> hb(2 * (nch + 1) + 1);
+    CK(cudaMemcpyAsync(hb.data(), dbound, sizeof(int64_t) * 2 * (nch + 1), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hb.data() + 2 * (nch + 1), pre + in.n / 2, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    dfree(c, dbound);
     dfree(c, pre);
     dfree(c, tmp);
-    std::vector<int64_t> b{0};
-    for (int64_t i = 1; i < nch; i++) {
-      int64_t target = i * step;
-      int64_t idx = (int64_t)(std::upper_bound(hpre.begin(), hpre.end(), target) - hpre.begin()) - 1;
-      if (idx > b.back()) b.push_back(idx);
+    std::vector<int64_t> b{0}, bp{hb[nch + 1]};  // boundaries and the prefix at each
+    for (int64_t i = 1; i < nch; i++)
+      if (hb[i] > b.back()) {
+        b.push_back(hb[i]);
+        bp.push_back(hb[nch + 1 + i]);
+      }
+    if (b.size() == 1 && in.n > 1) {  // always make progress
+      b.push_back(in.n / 2);
+      bp.push_back(hb[2 * (nch + 1)]);
     }
-    if (b.size() == 1 && in.n > 1) b.push_back(in.n / 2);  // always make progress
     b.push_back(in.n);
+    bp.push_back(hb[nch + 1 + nch]);
     for (size_t i = 0; i + 1 < b.size(); i++) {
       int64_t lo = b[i], hi = b[i + 1];
       if (hi <= lo) continue;
@@ -607,7 +618,7 @@ struct Exec {
       sub.score = in.score ? in.score + lo : nullptr;
       sub.n = hi - lo;
       sub.w = in.w;
-      int64_t sc = hpre[hi] - hpre[lo];
+      int64_t sc = bp[i + 1] - bp[i];
       if (sc == 0) continue;
       if (sc <= limit_rows(j) || sub.n == 1) RET(run_one(j, sub, 0, 0, sc));
       else RET(process(j, sub, in_next + lo, sc));
@@ -735,6 +746,12 @@ struct Exec {
         c->stats = saved;
         if (want >= (size_t)c->budget) break;
         want *= 4;
+      }
+      if (c->arena_bytes > ((size_t)4 << 30)) {  // streaming needs the budget the arena holds
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->arena);
+        c->arena = nullptr;
+        c->arena_bytes = 0;
       }
     }
     DevTable *T = st[0].seed_table;

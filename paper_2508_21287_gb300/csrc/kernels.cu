@@ -245,6 +245,38 @@ cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm
   return cudaGetLastError();
 }
 
+// Chunk boundaries for streaming: bounds[t] = the largest row index i with pre[i] <= t * step
+// (bounds[0] = 0, bounds[nch] = n), and bpre[t] = pre[bounds[t]]; pre has n + 1 entries and is
+// non-decreasing.
+__global__ void k_chunk_bounds(const int64_t *pre, int64_t n, int64_t step, int64_t nch, int64_t *bounds,
+                               int64_t *bpre) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= nch; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t idx;
+    if (t == 0) idx = 0;
+    else if (t == nch) idx = n;
+    else {
+      const int64_t target = t * step;
+      int64_t lo = 0, hi = n + 1;  // first index with pre > target, in [0, n + 1]
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= target) lo = mid + 1;
+        else hi = mid;
+      }
+      idx = lo - 1 < 0 ? 0 : lo - 1;
+    }
+    bounds[t] = idx;
+    bpre[t] = pre[idx];
+  }
+}
+
+cudaError_t launch_chunk_bounds(const int64_t *pre, int64_t n, int64_t step, int64_t nch, int64_t *bounds,
+                                int64_t *bpre, cudaStream_t s) {
+  g_launches++;
+  const int64_t blocks = (nch + 1 + 255) / 256;
+  k_chunk_bounds<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, s>>>(pre, n, step, nch, bounds, bpre);
+  return cudaGetLastError();
+}
+
 __global__ void k_iota(int32_t *p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int32_t)i;

@@ -63,6 +63,11 @@ cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm
                        int32_t *perm_out, int64_t n, int shift, int64_t *hist, int64_t *hist_scan,
                        int64_t *tmp, cudaStream_t s);
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+// Streaming chunk boundaries over a prefix array pre[0..n] (non-decreasing): bounds[t] is the
+// largest i with pre[i] <= t * step for 0 < t < nch, bounds[0] = 0, bounds[nch] = n; bpre[t] =
+// pre[bounds[t]]. Both outputs hold nch + 1 entries.
+cudaError_t launch_chunk_bounds(const int64_t *pre, int64_t n, int64_t step, int64_t nch, int64_t *bounds,
+                                int64_t *bpre, cudaStream_t s);
 cudaError_t launch_gather_rows(const int32_t *in, const float *ins, const int32_t *perm, int64_t n,
                                int32_t w, int32_t *out, float *outs, cudaStream_t s);
 

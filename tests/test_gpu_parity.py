@@ -248,6 +248,25 @@ def test_largest_heavy_hex_p24(ctx):
     assert cnt == ref.count and cs == ref.checksum
 
 
+def test_streaming_far_beyond_the_budget_is_consistent(ctx, B):
+    # a 37-vertex path in heavy-hex 53x59: billions of embeddings, intermediate tables of
+    # hundreds of GB streamed depth-first in budget-sized chunks; two budgets (different
+    # chunkings) must give the same count and order-independent checksum
+    g = I.heavy_hex(53, 59)
+    gid = ctx.load(g)
+    plan = ctx.plan(gid, I.path(37))
+    got = []
+    try:
+        for budget in (24 << 30, 8 << 30):
+            B.dm_set_budget(ctx.h, budget)
+            got.append(plan.count())
+            st = ctx.stats()
+            assert st["chunks"] > 2 * st["n_steps"]
+    finally:
+        B.dm_set_budget(ctx.h, 0)
+    assert got[0] == got[1] and got[0][0] > 10 ** 9
+
+
 # ------------------------------------------------------------------ other graphs -----------
 def _er(n, p1000, seed):
     rng = I.SplitMix64(seed)
