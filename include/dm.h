@@ -68,8 +68,11 @@ typedef int32_t dm_graph;
 #define DM_ORDER_LEARNED 2    /* cheapest of several candidate plans under the trained cardinality model (heuristic order if none) */
 
 #define DM_JOIN_AUTO 0
-#define DM_JOIN_HASH 1        /* probe a per-key index of the motif table (direct or hashed packed key) */
-#define DM_JOIN_SORTMERGE 2   /* sort the intermediate table by key, then merge with the sorted motif table */
+#define DM_JOIN_HASH 1        /* probe a per-key index of the motif table (direct offsets for one key,
+                                 open-addressing hash of the packed 64-bit key for two) */
+#define DM_JOIN_SORTMERGE 2   /* sort the intermediate table by its key columns each step and find each
+                                 row's group by binary search in the motif table's sorted packed keys
+                                 (no offsets or hash table; plans with it always stream step by step) */
 
 typedef struct dm_plan_opts {
     const int32_t *motifs; /* motif ids to decompose with (M2 is always added); NULL = preset by data-graph degree */

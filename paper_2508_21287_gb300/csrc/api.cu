@@ -35,6 +35,7 @@ struct Index {
   float *score = nullptr;
   int32_t *offsets = nullptr;
   HashSlot *slots = nullptr;
+  unsigned long long *keys = nullptr;  // sort-merge join: sorted packed keys
   int64_t distinct = 0;
   int64_t max_group = 0;
   int64_t bytes = 0;
@@ -50,7 +51,7 @@ struct DevGraph {
   double avg_deg = 0;
   int32_t max_deg = 0;
   std::map<int, DevTable> motifs;
-  std::map<std::tuple<int, int, int>, Index> indices;
+  std::map<std::tuple<int, int, int, int>, Index> indices;  // (motif, key position 0, 1, sort-merge)
 };
 
 }  // namespace
@@ -305,8 +306,11 @@ int read_ctr(dm_ctx *c) {
   return DM_OK;
 }
 
-int ensure_index(dm_ctx *c, DevGraph *g, int motif, int kp0, int kp1, Index **out) {
-  auto key = std::make_tuple(motif, kp0, kp1);
+// Index of a motif table on its key positions: the table sorted by the key columns, plus
+// direct offsets (one key) or an open-addressing hash of the packed key (two keys), or, for the
+// sort-merge join, the sorted packed keys themselves (groups found by binary search).
+int ensure_index(dm_ctx *c, DevGraph *g, int motif, int kp0, int kp1, bool sortmerge, Index **out) {
+  auto key = std::make_tuple(motif, kp0, kp1, sortmerge ? 1 : 0);
   auto it = g->indices.find(key);
   if (it != g->indices.end()) {
     *out = &it->second;
@@ -336,7 +340,21 @@ int ensure_index(dm_ctx *c, DevGraph *g, int motif, int kp0, int kp1, Index **ou
   ix.v.rows = sorted.rows;
   ix.v.score = sorted.score;
   ix.bytes = T.n * (4 * T.w + (sorted.score ? 4 : 0));
-  if (kp1 < 0) {
+  if (sortmerge) {
+    RET(dalloc_t(c, &ix.keys, (size_t)std::max<int64_t>(1, T.n)));
+    CK(dmk::launch_join_keys(sorted.rows, T.w, kp0, kp1, T.n, ix.keys, c->stream));
+    std::vector<unsigned long long> hk((size_t)T.n);
+    if (T.n > 0)
+      CK(cudaMemcpyAsync(hk.data(), ix.keys, sizeof(unsigned long long) * T.n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0, run = 0; i < T.n; i++) {  // runs of equal keys: distinct keys, largest group
+      run = (i > 0 && hk[i] == hk[i - 1]) ? run + 1 : 1;
+      ix.distinct += run == 1;
+      ix.max_group = std::max(ix.max_group, run);
+    }
+    ix.v.keys = ix.keys;
+    ix.bytes += 8 * T.n;
+  } else if (kp1 < 0) {
     RET(dalloc_t(c, &ix.offsets, (size_t)g->V + 1));
     CK(dmk::launch_offsets_direct(sorted.rows, T.w, kp0, T.n, g->V, ix.offsets, c->stream));
     std::vector<int32_t> off(g->V + 1);
@@ -415,7 +433,8 @@ struct Exec {
         r.motif_bytes = it->second.n * (4 * it->second.w + (it->second.score ? 4 : 0));
       } else {
         if (s.n_keys < 1) return DM_E_INVAL;
-        RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1, &r.ix));
+        RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1,
+                         p->join_algo == DM_JOIN_SORTMERGE, &r.ix));
         a.ix = r.ix->v;
         r.max_group = std::max<int64_t>(1, r.ix->max_group);
         r.motif_bytes = r.ix->bytes;
@@ -493,12 +512,25 @@ struct Exec {
       a.Rs = in.score;
       a.N = in.n;
     }
+    DevTable sorted_in;  // sort-merge join: R ordered by its key columns, so that consecutive
+                         // rows probe the same or neighbouring runs of the sorted motif keys
+    if (j > 0 && p->join_algo == DM_JOIN_SORTMERGE && in.n > 1) {
+      std::vector<int> kc{a.key_col[0]};
+      if (a.ix.nkeys == 2) kc.push_back(a.key_col[1]);
+      int32_t *perm = nullptr;
+      RET(sort_perm_by_columns(c, in, kc, graph_bits(g), &perm));
+      RET(gather_table(c, in, perm, in.n, &sorted_in));
+      dfree(c, perm);
+      a.R = sorted_in.rows;
+      a.Rs = sorted_in.score;
+    }
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
     int grid = dmk::wjoin_grid(a, c->num_sms);
     if (c->timing) CK(cudaEventRecord(c->ev0, c->stream));
     CK(dmk::launch_wjoin(a, grid, c->stream));
     if (c->timing) CK(cudaEventRecord(c->ev1, c->stream));
     RET(read_ctr(c));
+    if (sorted_in.rows) free_table(c, sorted_in);
     if (c->h_ctr[CTR_OVF]) {
       c->last_error = "join output overflow";
       free_table(c, o);
@@ -733,7 +765,7 @@ struct Exec {
     RET(setup());
     const int S = (int)st.size();
     c->stats.n_steps = S;
-    if (chunk_rows == 0 && max_rows == 0 && st[0].seed_table->n > 0) {
+    if (chunk_rows == 0 && max_rows == 0 && p->join_algo != DM_JOIN_SORTMERGE && st[0].seed_table->n > 0) {
       // device-driven path first; grow the arena (up to the budget) while a step overflows
       size_t want = std::max<size_t>(c->arena_bytes, (size_t)4 << 30);
       while (true) {
@@ -1596,6 +1628,7 @@ int dm_destroy(dm_ctx *c) {
       if (kv.second.score) cudaFreeAsync(kv.second.score, c->stream);
       if (kv.second.offsets) cudaFreeAsync(kv.second.offsets, c->stream);
       if (kv.second.slots) cudaFreeAsync(kv.second.slots, c->stream);
+      if (kv.second.keys) cudaFreeAsync(kv.second.keys, c->stream);
     }
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
@@ -1741,7 +1774,8 @@ int plan_finish(dm_ctx *c, DevGraph *g, const Plan &p) {
   for (size_t j = 1; j < p.steps.size(); j++) {
     Index *ix;
     const StepSpec &s = p.steps[j];
-    RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1, &ix));
+    RET(ensure_index(c, g, s.motif, s.key_mpos[0], s.n_keys >= 2 ? s.key_mpos[1] : -1,
+                     p.join_algo == DM_JOIN_SORTMERGE, &ix));
   }
   return DM_OK;
 }
@@ -1999,7 +2033,7 @@ int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor, double heavy
     for (DevGraph *g : c->graphs) {  // two-key indices are rebuilt at the new load factor
       if (!g) continue;
       for (auto it = g->indices.begin(); it != g->indices.end();) {
-        if (it->second.v.nkeys == 2) {
+        if (it->second.v.nkeys == 2 && !it->second.keys) {
           cudaFreeAsync(it->second.rows, c->stream);
           if (it->second.score) cudaFreeAsync(it->second.score, c->stream);
           cudaFreeAsync(it->second.slots, c->stream);

@@ -123,6 +123,8 @@ struct IndexView {
   const int32_t *offsets; // nkeys == 1: [V + 1]
   const HashSlot *slots;  // nkeys == 2: 2^log2cap slots
   uint32_t log2cap;
+  const unsigned long long *keys;  // sort-merge join: packed key of every row, ascending (then
+                                   // offsets and slots are unused)
 };
 
 enum { CTR_ROWS = 0, CTR_NEXT = 1, CTR_SUM = 2, CTR_OVF = 3, CTR_CAND = 4, CTR_N = 8 };

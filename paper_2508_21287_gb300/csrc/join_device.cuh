@@ -51,7 +51,24 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // ------------------------------------------------------------------ index lookup -------
 __device__ __forceinline__ void ix_lookup(const IndexView &ix, int32_t ka, int32_t kb, int32_t &start,
                                           int32_t &len) {
-  if (ix.nkeys == 1) {
+  if (ix.keys && ix.nkeys > 0) {  // sort-merge: the key's run in the sorted key column
+    const unsigned long long key =
+        ix.nkeys == 2 ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : (unsigned long long)(uint32_t)ka;
+    int64_t lo = 0, hi = ix.n;
+    while (lo < hi) {  // first position with keys >= key
+      const int64_t mid = (lo + hi) >> 1;
+      if (__ldg(ix.keys + mid) < key) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t e = lo, h2 = ix.n;
+    while (e < h2) {  // first position with keys > key
+      const int64_t mid = (e + h2) >> 1;
+      if (__ldg(ix.keys + mid) <= key) e = mid + 1;
+      else h2 = mid;
+    }
+    start = (int32_t)lo;
+    len = (int32_t)(e - lo);
+  } else if (ix.nkeys == 1) {
     start = __ldg(ix.offsets + ka);
     len = __ldg(ix.offsets + ka + 1) - start;
   } else if (ix.nkeys == 2) {

@@ -277,6 +277,24 @@ cudaError_t launch_chunk_bounds(const int64_t *pre, int64_t n, int64_t step, int
   return cudaGetLastError();
 }
 
+// Sort-merge join keys: keys[i] = packed (row[kp0], row[kp1]) (kp1 < 0: row[kp0]) of each row.
+__global__ void k_join_keys(const int32_t *rows, int32_t w, int32_t kp0, int32_t kp1, int64_t n,
+                            unsigned long long *keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t *r = rows + i * w;
+    const unsigned long long a = (uint32_t)__ldg(r + kp0);
+    keys[i] = kp1 >= 0 ? ((a << 32) | (uint32_t)__ldg(r + kp1)) : a;
+  }
+}
+
+cudaError_t launch_join_keys(const int32_t *rows, int32_t w, int32_t kp0, int32_t kp1, int64_t n,
+                             unsigned long long *keys, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  g_launches++;
+  k_join_keys<<<(int)imin64((n + 255) / 256, 16384), 256, 0, s>>>(rows, w, kp0, kp1, n, keys);
+  return cudaGetLastError();
+}
+
 __global__ void k_iota(int32_t *p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int32_t)i;

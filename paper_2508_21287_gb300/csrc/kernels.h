@@ -63,6 +63,9 @@ cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm
                        int32_t *perm_out, int64_t n, int shift, int64_t *hist, int64_t *hist_scan,
                        int64_t *tmp, cudaStream_t s);
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+// Packed join keys of a table's rows: (row[kp0] << 32) | row[kp1], or row[kp0] when kp1 < 0.
+cudaError_t launch_join_keys(const int32_t *rows, int32_t w, int32_t kp0, int32_t kp1, int64_t n,
+                             unsigned long long *keys, cudaStream_t s);
 // Streaming chunk boundaries over a prefix array pre[0..n] (non-decreasing): bounds[t] is the
 // largest i with pre[i] <= t * step for 0 < t < nch, bounds[0] = 0, bounds[nch] = n; bpre[t] =
 // pre[bounds[t]]. Both outputs hold nch + 1 entries.

@@ -72,6 +72,15 @@ def test_batch_candidate_plans_with_wide_steps(B):
             B.dm_plan_free(pl)
 
 
+def test_batch_sort_merge_plans(B):
+    g = I.heavy_hex(12, 6)
+    pats = [I.mixed_pattern(s, 5, 30) for s in range(30)] + [I.cycle(24)]
+    with B.Context(0) as ctx:
+        gid = ctx.load(g)
+        counts, sums, single = _run(B, ctx, gid, pats, join_algo=B.DM_JOIN_SORTMERGE)
+        _check(g, pats, counts, sums, single)
+
+
 def test_batch_paths_and_patches(B):
     g = I.heavy_hex(8, 9)
     pats = [I.path(k) for k in (2, 3, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]

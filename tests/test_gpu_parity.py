@@ -35,8 +35,8 @@ def _rows_equal(a, b):
     assert np.array_equal(a, b)
 
 
-def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True):
-    plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows)
+def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, join_algo=0):
+    plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows, join_algo=join_algo)
     rows, sc, cnt, cs = plan.all()
     ref = oracle.enumerate(g, p)
     if chunk_rows:
@@ -225,6 +225,26 @@ def test_cycle40_half_paths_count(ctx):
     cnt, cs = plan.count()
     ref = oracle.enumerate(g, I.cycle(40), rows=False, threads=8)
     assert cnt == ref.count == 402240 and cs == ref.checksum
+
+
+@pytest.mark.parametrize("motifs", [None, [104], [4, 2], [202, 4]])
+def test_sort_merge_join_grid(ctx, B, motifs):
+    # the sort-merge join (R sorted by its key columns, motif groups found in the sorted packed
+    # keys) gives the same rows, scores and checksums as the oracle, for one- and two-key joins
+    g = I.lognormal_weights(I.grid(6, 6), seed=5)
+    gid = ctx.load(g)
+    for p in (I.path(5), I.cycle(4), I.grid(2, 3), I.random_tree(9, 4)):
+        check_all(ctx, gid, g, p, motifs=motifs, join_algo=B.DM_JOIN_SORTMERGE)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sort_merge_join_heavy_hex(ctx, hh, B, seed):
+    g, gid = hh
+    check_all(ctx, gid, g, I.layout_query(g, seed), join_algo=B.DM_JOIN_SORTMERGE)
+    check_all(ctx, gid, g, I.cycle(24), motifs=[13, 4], join_algo=B.DM_JOIN_SORTMERGE)
+    plan = ctx.plan(gid, I.path(12 + seed), join_algo=B.DM_JOIN_SORTMERGE, chunk_rows=500)
+    ref = oracle.enumerate(g, I.path(12 + seed), rows=False)
+    assert plan.count() == (ref.count, ref.checksum)
 
 
 # ------------------------------------------------------------------ larger heavy-hex -------
