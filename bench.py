@@ -55,16 +55,22 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
     ap.add_argument("--rates", default="500,2000,8000,16000,32000", help="c5: Poisson arrival rates (requests/s)")
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
+    ap.add_argument("--graph", default="heavyhex", choices=["heavyhex", "grid", "rr3"],
+                    help="c3: data graph family (heavy-hex m x n, square grid 60x60, random 3-regular V=4096)")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
     ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
     return ap.parse_args()
 
 
+WORKLOAD_C3_GRID = ("C3 scaling: square grid 60x60 (V=3600), seeded paths of 6-11 vertices and sub-patches of "
+                    "10-32 vertices, count + 64-bit checksum")
+WORKLOAD_C3_RR3 = ("C3 scaling: random 3-regular graph V=4096, seeded paths of 8-14 vertices and sub-patches of "
+                   "10-20 vertices, count + 64-bit checksum")
 WORKLOAD_C3 = ("C3 scaling: heavy-hex {m}x{n} (V={V}), seeded paths of 8-24 vertices and sub-patches of 12-40 "
                "vertices, count + 64-bit checksum")
 
 
-def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: int = 0):
+def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: int = 0, graph: str = "heavyhex"):
     from paper_2508_21287_gb300 import inputs as I
     if kind == "c2":
         g = I.lognormal_weights(I.heavy_hex(4, 6), seed=7)
@@ -73,16 +79,23 @@ def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: in
     if kind == "c4":
         g = I.heavy_hex(12, 6)
         return g, [I.mixed_pattern(rank * batch + i, 5, 40) for i in range(batch)]
-    g = I.heavy_hex(*hh)
+    # C3: paths and random connected sub-patches, sized so that a query has 10^5-10^8
+    # embeddings on each graph family
+    if graph == "grid":  # the paper's larger square grid (Table 1)
+        g, plen, psz = I.grid(60, 60), (6, 11), (10, 32)
+    elif graph == "rr3":
+        g, plen, psz = I.random_regular3(4096, 5), (8, 14), (10, 20)
+    else:
+        g, plen, psz = I.heavy_hex(*hh), (8, 24), (12, 40)
     if only_path:
         return g, [I.path(only_path)]
     rng = I.SplitMix64(0xC3 + rank)
     pats = []
     for i in range(batch):
         if i % 2 == 0:
-            pats.append(I.path(8 + rng.below(17)))
+            pats.append(I.path(plen[0] + rng.below(plen[1] - plen[0] + 1)))
         else:
-            pats.append(I.sub_patch(g, 12 + rng.below(29), rank * batch + i))
+            pats.append(I.sub_patch(g, psz[0] + rng.below(psz[1] - psz[0] + 1), rank * batch + i))
     return g, pats
 
 
@@ -179,6 +192,10 @@ def wl_name(args):
         return WORKLOAD_C5
     if args.workload == "c4":
         return WORKLOAD_C4
+    if args.graph == "grid":
+        return WORKLOAD_C3_GRID
+    if args.graph == "rr3":
+        return WORKLOAD_C3_RR3
     m, n = (int(x) for x in args.hh.split(","))
     return WORKLOAD_C3.format(m=m, n=n, V=5 * m * n + 4 * m + 4 * n - 1)
 
@@ -188,7 +205,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     nb = 512 if args.workload == "c4" and args.batch == BATCH else args.batch
-    g, pats = workload(0, nb, args.workload, tuple(int(x) for x in args.hh.split(",")))
+    g, pats = workload(0, nb, args.workload, tuple(int(x) for x in args.hh.split(",")), args.only_path, args.graph)
     import oracle
     oracle.build()
     cb = cpu_baseline(g, pats, budget_s=max(5.0, 3.0 * (args.steps + args.warmup)),
@@ -216,7 +233,7 @@ def run_ours(args):
     from paper_2508_21287_gb300 import binding as B
 
     hh = tuple(int(x) for x in args.hh.split(","))
-    g, pats = workload(rank, args.batch, args.workload, hh, args.only_path)
+    g, pats = workload(rank, args.batch, args.workload, hh, args.only_path, args.graph)
     count_mode = args.workload == "c3"
     ctx = B.Context(local)
     stream = torch.cuda.Stream()
@@ -318,7 +335,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": wl_name(args), "queries_per_step": len(pats), "embeddings_per_step": emb_total / args.steps / world,
-                       "data_graph": f"heavy-hex {'4x6' if not count_mode else args.hh.replace(',', 'x')}", "motifs": "M4,M2",
+                       "data_graph": ("heavy-hex 4x6" if not count_mode else
+                                      {"grid": "grid 60x60", "rr3": "random 3-regular V=4096"}.get(
+                                          args.graph, "heavy-hex " + args.hh.replace(",", "x"))),
+                       "motifs": "M4-O,M6-O,M2" if count_mode and args.graph == "grid" else "M4,M2",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}",
                        "join_chunks_per_step": acc["chunks"] / args.steps, "largest_table_rows": acc["max_rows"]},
