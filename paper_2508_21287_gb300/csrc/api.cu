@@ -993,9 +993,16 @@ struct TopkSink : Sink {
   bool have = false;
   float *prune_ptr = nullptr;
   int take(dm_ctx *c, DevTable t) override {
-    if (!input_sorted || t.borrowed) RET(sort_canonical(c, t, graph_bits(g)));
     DevTable tk;
-    RET(topk_of_sorted(c, g, t, k, &tk));
+    if (!input_sorted && t.n > 16384) {
+      // a large unsorted table: select by score first and sort only the candidates, instead
+      // of sorting every row into canonical order
+      RET(topk_table(c, g, t, k, &tk));
+      free_table(c, t);
+    } else {
+      if (!input_sorted || t.borrowed) RET(sort_canonical(c, t, graph_bits(g)));
+      RET(topk_of_sorted(c, g, t, k, &tk));
+    }
     if (have) {
       CollectSink cs;
       cs.parts = {best, tk};
