@@ -79,7 +79,9 @@ typedef struct dm_plan_opts {
     int32_t n_motifs;
     int32_t order;          /* DM_ORDER_* */
     int32_t join_algo;      /* DM_JOIN_* */
-    int32_t induced;        /* must be 0 (reserved) */
+    int32_t induced;        /* 0 = embeddings preserve pattern edges (monomorphisms, Alg. 1 as given);
+                               1 = also non-edges: pattern vertices that are not adjacent map to
+                               data vertices that are not adjacent (the literal "iff" of Sec. 3.1) */
     int64_t chunk_rows;     /* 0 = from the memory budget; else the row cap of one intermediate chunk */
     int64_t max_rows;       /* 0 = unlimited; else DM_E_CAPACITY once a step's candidate rows exceed it */
 } dm_plan_opts;

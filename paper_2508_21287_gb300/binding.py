@@ -198,7 +198,7 @@ def dm_motif_table(ctx, graph: int, motif_id: int) -> np.ndarray:
 
 
 def dm_plan(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, order: int = DM_ORDER_PAPER,
-            join_algo: int = DM_JOIN_AUTO, chunk_rows: int = 0, max_rows: int = 0):
+            join_algo: int = DM_JOIN_AUTO, chunk_rows: int = 0, max_rows: int = 0, induced: bool = False):
     rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
     opts = dm_plan_opts()
     keep = None
@@ -208,6 +208,7 @@ def dm_plan(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, order: int
         opts.n_motifs = len(keep)
     opts.order, opts.join_algo = int(order), int(join_algo)
     opts.chunk_rows, opts.max_rows = int(chunk_rows), int(max_rows)
+    opts.induced = int(bool(induced))
     h = _vp()
     _check(_lib.dm_plan(ctx, int(graph), int(n_p), _p32(rp), _p32(ci), ctypes.byref(opts), ctypes.byref(h)),
            "dm_plan", ctx)

@@ -455,6 +455,8 @@ struct Exec {
       }
       a.w = s.w_in;
       a.wo = s.w_out;
+      a.induced = p->induced;
+      for (int i = 0; i < s.n_new; i++) a.nonadj[i] = p->induced ? s.nonadj[i] : 0ull;
       for (int cc = 0; cc < a.wo; cc++) a.src_col[cc] = (int8_t)cc;
       if (j == S - 1)  // the last step writes rows in pattern-vertex order
         for (int cc = 0; cc < a.wo; cc++) a.src_col[p->col_vertex[cc]] = (int8_t)cc;
@@ -1737,7 +1739,7 @@ int plan_setup(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, co
   DevGraph *g = get_graph(c, gh);
   if (!g) return DM_E_NOTFOUND;
   if (n_p < 1 || n_p > MAXW) return DM_E_INVAL;
-  if (opts && opts->induced) return DM_E_INVAL;
+  if (opts && (opts->induced < 0 || opts->induced > 1)) return DM_E_INVAL;
   cudaSetDevice(c->device);
   HostCSR h;
   RET(validate_csr(n_p, p_row_ptr, p_col_idx, nullptr, &h));
@@ -1748,6 +1750,7 @@ int plan_setup(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, co
   p.graph = gh;
   p.order = opts ? opts->order : DM_ORDER_PAPER;
   p.join_algo = opts ? opts->join_algo : DM_JOIN_AUTO;
+  p.induced = opts ? opts->induced : 0;
   p.chunk_rows = opts ? opts->chunk_rows : 0;
   p.max_rows = opts ? opts->max_rows : 0;
   if (opts && opts->motifs && opts->n_motifs > 0) {

@@ -56,6 +56,9 @@ struct StepSpec {
   int32_t n_be = 0;            // uncovered pattern edges closed by this step (back-edges)
   int32_t be_col[MAXBE][2] = {};
   int32_t be_vtx[MAXBE][2] = {};
+  // induced matching: per new vertex i, the working columns (< w_in + i) whose pattern vertex
+  // is not adjacent to it in the pattern; their images must not be adjacent in the data graph
+  uint64_t nonadj[MAXM] = {};
   double est_rows = 0.0;       // planner's estimate of the rows after the step
   float feat[32] = {};         // features seen by the cardinality model
 };
@@ -90,6 +93,7 @@ struct Plan {
   int32_t col_vertex[MAXW] = {};        // working column -> pattern vertex
   int32_t graph = -1;
   int32_t order = 0, join_algo = 0;
+  int32_t induced = 0;                  // 1: non-adjacent pattern pairs must map to non-adjacent vertices
   int64_t chunk_rows = 0, max_rows = 0;
   double pred_cost = 0;      // predicted bytes moved by the joins plus a per-step overhead
   double pred_max_rows = 0;  // predicted largest intermediate table
@@ -148,6 +152,8 @@ struct JoinArgs {
   int32_t n_be;
   int8_t be_a[MAXBE];
   int8_t be_b[MAXBE];
+  int32_t induced;                   // 1: also require non-adjacency for the columns in nonadj
+  unsigned long long nonadj[MAXM];   // per new vertex: working columns it must not be adjacent to
   int32_t wo;                // output width = w + n_new
   int8_t src_col[MAXW];      // position q of a written row holds working column src_col[q]
   // data graph

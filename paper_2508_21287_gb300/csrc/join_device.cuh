@@ -280,6 +280,35 @@ __device__ __forceinline__ void load_tile(int32_t *tile, float *ts, const int32_
     for (int i = threadIdx.x; i < nr; i += BLK) ts[i] = __ldg(srcs + i);
 }
 
+// Induced matching: every new vertex must not be adjacent to the images of the columns its
+// pattern vertex is not adjacent to (the columns in a.nonadj[i]).
+template <int MAXNEW>
+__device__ __forceinline__ int32_t nv_pick(const int32_t (&nv)[MAXNEW], int k) {
+  int32_t v = 0;
+#pragma unroll
+  for (int i = 0; i < MAXNEW; i++)
+    if (i == k) v = nv[i];
+  return v;
+}
+
+template <int MAXNEW>
+__device__ __forceinline__ bool induced_ok(const JoinArgs &a, const int32_t *rrow, const int32_t (&nv)[MAXNEW]) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < MAXNEW; i++) {
+    if (i < a.n_new && ok) {
+      unsigned long long mk = a.nonadj[i];
+      while (mk && ok) {
+        const int c = __ffsll((long long)mk) - 1;
+        mk &= mk - 1;
+        const int32_t v = c < a.w ? rrow[c] : nv_pick<MAXNEW>(nv, c - a.w);
+        ok = !adjacent(a, nv[i], v);
+      }
+    }
+  }
+  return ok;
+}
+
 // Value of working column `col` of the joined row (R row `rrow`, motif row `trow`).
 __device__ __forceinline__ int32_t join_value(const JoinArgs &a, const int32_t *rrow, const int32_t *trow, int col) {
   return col < a.w ? rrow[col] : __ldg(trow + a.new_mpos[col - a.w]);
@@ -322,6 +351,7 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
     ok = adjacent(a, va, vb);
     if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
   }
+  if (ok && a.induced) ok = induced_ok<MAXNEW>(a, rrow, nv);
   if (sc > a.prune) ok = false;
   return ok;
 }

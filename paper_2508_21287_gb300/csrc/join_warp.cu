@@ -97,6 +97,7 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
     ok = adjacent(a, va, vb);
     if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
   }
+  if (ok && a.induced) ok = induced_ok<MAXNEW>(a, rrow, nv);
   if (sc > a.prune) ok = false;
   return ok;
 }

@@ -87,6 +87,7 @@ bool motif_def(int id, MotifDef *out) {
 // ---------------------------------------------------------------- reduced pattern -----
 struct PState {
   int n = 0;
+  uint64_t adj0[MAXW] = {}; // pattern adjacency bitmasks
   uint64_t unc[MAXW] = {};  // uncovered pattern edges, adjacency bitmasks
   uint64_t mapped = 0;
   int ncols = 0;
@@ -148,6 +149,13 @@ static void make_step(const MotifDef &m, const int *img, const PState &st, StepS
     }
   }
   s->w_out = s->w_in + s->n_new;
+  for (int i = 0; i < s->n_new; i++) {  // non-edges to check under induced matching
+    const int p = img[s->new_mpos[i]];
+    for (int c = 0; c < s->w_in + i; c++) {
+      const int q = c < s->w_in ? st.col_vertex[c] : img[s->new_mpos[c - s->w_in]];
+      if (!(st.adj0[p] >> q & 1ull)) s->nonadj[i] |= 1ull << c;
+    }
+  }
   // back-edges: uncovered pattern edges with both ends mapped after this step, that the
   // slice itself does not cover
   uint64_t after = st.mapped;
@@ -250,6 +258,7 @@ static int build_pstate(const Plan &pat, PState *st) {
     for (int k = pat.rp[u]; k < pat.rp[u + 1]; k++) {
       int v = pat.ci[k];
       st->unc[u] |= 1ull << v;
+      st->adj0[u] |= 1ull << v;
       if (u < v) st->uncovered_edges++;
     }
   for (int i = 0; i < MAXW; i++) st->col_of[i] = -1;

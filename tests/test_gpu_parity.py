@@ -35,10 +35,11 @@ def _rows_equal(a, b):
     assert np.array_equal(a, b)
 
 
-def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, join_algo=0):
-    plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows, join_algo=join_algo)
+def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, join_algo=0, induced=False):
+    plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows, join_algo=join_algo,
+                    induced=induced)
     rows, sc, cnt, cs = plan.all()
-    ref = oracle.enumerate(g, p)
+    ref = oracle.enumerate(g, p, induced=induced)
     if chunk_rows:
         rows = rows[np.lexsort(rows.T[::-1])] if len(rows) else rows
     _rows_equal(rows, ref.rows)
@@ -245,6 +246,30 @@ def test_sort_merge_join_heavy_hex(ctx, hh, B, seed):
     plan = ctx.plan(gid, I.path(12 + seed), join_algo=B.DM_JOIN_SORTMERGE, chunk_rows=500)
     ref = oracle.enumerate(g, I.path(12 + seed), rows=False)
     assert plan.count() == (ref.count, ref.checksum)
+
+
+@pytest.mark.parametrize("motifs", [None, [2], [4, 2], [104], [202, 4]])
+def test_induced_matching_grid(ctx, motifs):
+    # induced embeddings (non-adjacent pattern vertices on non-adjacent data vertices): the
+    # oracle's induced enumeration, itself pinned by brute force and closed forms
+    g = I.lognormal_weights(I.grid(6, 6), seed=9)
+    gid = ctx.load(g)
+    for p in (I.path(4), I.path(6), I.cycle(4), I.star(4), I.grid(2, 3), I.random_tree(8, 2), I.cycle(8)):
+        check_all(ctx, gid, g, p, motifs=motifs, induced=True)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_induced_matching_heavy_hex_and_random(ctx, hh, B, seed):
+    g, gid = hh
+    check_all(ctx, gid, g, I.layout_query(g, seed), induced=True)
+    check_all(ctx, gid, g, I.sub_patch(g, 14 + seed, seed), induced=True, join_algo=B.DM_JOIN_SORTMERGE)
+    r = I.random_regular3(40, seed)
+    rg = ctx.load(r)
+    for p in (I.path(5), I.cycle(5), I.random_tree(7, seed)):
+        check_all(ctx, rg, r, p, induced=True, scores=False)
+        plan = ctx.plan(rg, p, induced=True, chunk_rows=7)
+        ref = oracle.enumerate(r, p, induced=True)
+        assert plan.count() == (ref.count, ref.checksum)
 
 
 # ------------------------------------------------------------------ larger heavy-hex -------
