@@ -113,6 +113,22 @@ int dm_load_data_graph(dm_ctx *ctx, int32_t n_vertices, const int32_t *row_ptr,
                        const int32_t *col_idx, const float *edge_err, const float *qubit_err,
                        dm_graph *out);
 
+/* Score forms of a loaded graph (Sec. 5.4 ranks layouts by the product of the fidelities
+ * 1 - e of the mapped edges and qubits):
+ *   DM_SCORE_ERROR_SUM    the score of a row is the sum of its error rates e (the first-order,
+ *                         log-domain form of the product; dm_load_data_graph uses it);
+ *   DM_SCORE_LOG_FIDELITY the score is the sum of -log(1 - e) = -log(product of fidelities):
+ *                         exactly the product's order, and exp(-score) is the layout fidelity.
+ * Lower is better in both. */
+#define DM_SCORE_ERROR_SUM 0
+#define DM_SCORE_LOG_FIDELITY 1
+
+/* dm_load_data_graph with a score form. With DM_SCORE_LOG_FIDELITY every error rate must lie
+ * in [0, 1) (else DM_E_INVAL); the device keeps -log(1 - e) per edge slot and qubit. */
+int dm_load_data_graph_ex(dm_ctx *ctx, int32_t n_vertices, const int32_t *row_ptr,
+                          const int32_t *col_idx, const float *edge_err, const float *qubit_err,
+                          int32_t score_form, dm_graph *out);
+
 /* Res(M) of one motif on a loaded graph (Alg. 2 builds it by the same join-and-filter
  * loop). Writes min(cap, count) rows of k = motif size ints (row-major, host memory, in
  * canonical ascending order) to out_rows (nullable) and the count and k to out_n / out_k. */

@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -72,7 +72,7 @@ def _load():
             lib.or_checksum.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int32]
             lib.or_scores.restype = ctypes.c_int32
             lib.or_scores.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int64,
+                                      ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_double)]
             lib.or_topk.restype = ctypes.c_int64
             lib.or_topk.argtypes = [_i32p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
@@ -175,8 +175,9 @@ def checksum(rows: np.ndarray) -> int:
     return int(_load().or_checksum(_ptr(rows), rows.shape[0], rows.shape[1]))
 
 
-def scores(data, pattern, rows: np.ndarray) -> np.ndarray:
-    """FP64 layout score per row (edge errors over pattern edges + vertex errors)."""
+def scores(data, pattern, rows: np.ndarray, form: int = 0) -> np.ndarray:
+    """FP64 layout score per row over pattern edges (+ vertices): form 0 sums the error rates e,
+    form 1 sums -log(1 - e), the negative log of the product of fidelities (Sec. 5.4)."""
     lib = _load()
     if data.edge_err is None:
         raise ValueError("scores need data.edge_err")
@@ -188,7 +189,7 @@ def scores(data, pattern, rows: np.ndarray) -> np.ndarray:
     rp_p, ci_p = _i32(pattern.row_ptr), _i32(pattern.col_idx)
     rc = lib.or_scores(int(data.n), _ptr(rp_d), _ptr(ci_d), ee.ctypes.data,
                        None if qe is None else qe.ctypes.data, int(pattern.n), _ptr(rp_p), _ptr(ci_p),
-                       _ptr(rows), rows.shape[0], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                       _ptr(rows), rows.shape[0], int(form), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise ValueError("scores: a row maps a pattern edge onto a non-edge")
     return out

@@ -33,6 +33,7 @@
  * accumulated in FP64. This is the log-domain form of the paper's product of fidelities;
  * lower is better.
  */
+#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -411,9 +412,13 @@ static double edge_weight(const csr_t *d, const float *edge_err, int32_t u, int3
 /* FP64 layout score of each row: sum of w_e over pattern edges {u < v} in CSR order of the
  * pattern, then sum of w_q over pattern vertices 0..n_p-1 (w_q = 0 when qubit_err is
  * NULL). Returns 0, or -1 if some row maps a pattern edge to a non-edge. */
+/* Per-row layout score. form 0: sum of the error rates e; form 1: sum of -log(1 - e), the
+ * negative log of the product of the fidelities 1 - e (Sec. 5.4 ranks layouts by that product). */
+static double score_term(double e, int32_t form) { return form ? -log1p(-e) : e; }
+
 int32_t or_scores(int32_t nd, const int32_t *rp_d, const int32_t *ci_d, const float *edge_err,
                   const float *qubit_err, int32_t np, const int32_t *rp_p, const int32_t *ci_p,
-                  const int32_t *rows, int64_t nrows, double *out) {
+                  const int32_t *rows, int64_t nrows, int32_t form, double *out) {
     csr_t d = {nd, rp_d, ci_d};
     for (int64_t r = 0; r < nrows; r++) {
         const int32_t *f = rows + r * np;
@@ -423,12 +428,13 @@ int32_t or_scores(int32_t nd, const int32_t *rp_d, const int32_t *ci_d, const fl
                 int32_t v = ci_p[k];
                 if (u < v) {
                     int found;
-                    s += edge_weight(&d, edge_err, f[u], f[v], &found);
+                    double e = edge_weight(&d, edge_err, f[u], f[v], &found);
                     if (!found) return -1;
+                    s += score_term(e, form);
                 }
             }
         if (qubit_err)
-            for (int32_t u = 0; u < np; u++) s += (double)qubit_err[f[u]];
+            for (int32_t u = 0; u < np; u++) s += score_term((double)qubit_err[f[u]], form);
         out[r] = s;
     }
     return 0;

@@ -86,6 +86,7 @@ _SIGS = {
     "dm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "dm_set_budget": (ctypes.c_int, [_vp, _u64]),
     "dm_load_data_graph": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32p]),
+    "dm_load_data_graph_ex": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _fp, _fp, _i32, _i32p]),
     "dm_motif_table": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i64, ctypes.POINTER(_i64), _i32p]),
     "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_free": (None, [_vp]),
@@ -183,6 +184,23 @@ def dm_load_data_graph(ctx, n_vertices: int, row_ptr, col_idx, edge_err=None, qu
                                  None if ee is None else ee.ctypes.data_as(_fp),
                                  None if qe is None else qe.ctypes.data_as(_fp), ctypes.byref(out))
     _check(rc, "dm_load_data_graph", ctx)
+    return out.value
+
+
+DM_SCORE_ERROR_SUM, DM_SCORE_LOG_FIDELITY = 0, 1
+
+
+def dm_load_data_graph_ex(ctx, n_vertices: int, row_ptr, col_idx, edge_err=None, qubit_err=None,
+                          score_form: int = DM_SCORE_ERROR_SUM) -> int:
+    rp, ci = _arr_i32(row_ptr), _arr_i32(col_idx)
+    ee = None if edge_err is None else np.ascontiguousarray(edge_err, dtype=np.float32)
+    qe = None if qubit_err is None else np.ascontiguousarray(qubit_err, dtype=np.float32)
+    out = _i32()
+    rc = _lib.dm_load_data_graph_ex(ctx, int(n_vertices), _p32(rp), _p32(ci),
+                                    None if ee is None else ee.ctypes.data_as(_fp),
+                                    None if qe is None else qe.ctypes.data_as(_fp), int(score_form),
+                                    ctypes.byref(out))
+    _check(rc, "dm_load_data_graph_ex", ctx)
     return out.value
 
 
@@ -549,10 +567,10 @@ class Context:
     def __exit__(self, *exc):
         self.close()
 
-    def load(self, g, weights: bool = True) -> int:
-        return dm_load_data_graph(self.h, g.n, g.row_ptr, g.col_idx,
-                                  getattr(g, "edge_err", None) if weights else None,
-                                  getattr(g, "qubit_err", None) if weights else None)
+    def load(self, g, weights: bool = True, score_form: int = DM_SCORE_ERROR_SUM) -> int:
+        return dm_load_data_graph_ex(self.h, g.n, g.row_ptr, g.col_idx,
+                                     getattr(g, "edge_err", None) if weights else None,
+                                     getattr(g, "qubit_err", None) if weights else None, score_form)
 
     def plan(self, graph: int, pattern, **kw):
         return Plan(self, dm_plan(self.h, graph, pattern.n, pattern.row_ptr, pattern.col_idx, **kw), pattern.n)

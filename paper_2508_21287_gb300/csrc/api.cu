@@ -1666,10 +1666,23 @@ int dm_destroy(dm_ctx *c) {
 
 int dm_load_data_graph(dm_ctx *c, int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const float *edge_err,
                        const float *qubit_err, dm_graph *out) {
+  return dm_load_data_graph_ex(c, n, row_ptr, col_idx, edge_err, qubit_err, DM_SCORE_ERROR_SUM, out);
+}
+
+int dm_load_data_graph_ex(dm_ctx *c, int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const float *edge_err,
+                          const float *qubit_err, int32_t score_form, dm_graph *out) {
   if (!c || !out || n < 1) return DM_E_INVAL;
+  if (score_form != DM_SCORE_ERROR_SUM && score_form != DM_SCORE_LOG_FIDELITY) return DM_E_INVAL;
   cudaSetDevice(c->device);
   HostCSR h;
   RET(validate_csr(n, row_ptr, col_idx, edge_err, &h));
+  if (score_form == DM_SCORE_LOG_FIDELITY) {  // error rates must leave a positive fidelity
+    for (float e : h.ee)
+      if (!(e >= 0.f && e < 1.f)) return DM_E_INVAL;
+    if (qubit_err)
+      for (int32_t v = 0; v < n; v++)
+        if (!(qubit_err[v] >= 0.f && qubit_err[v] < 1.f)) return DM_E_INVAL;
+  }
   if (!connected(h, n)) return DM_E_DISCONNECTED;
   DevGraph *g = new DevGraph();
   g->V = n;
@@ -1687,6 +1700,10 @@ int dm_load_data_graph(dm_ctx *c, int32_t n, const int32_t *row_ptr, const int32
   if (r == DM_OK) r = up((void **)&g->col_idx, h.ci.data(), sizeof(int32_t) * h.ci.size());
   if (r == DM_OK && edge_err) r = up((void **)&g->eerr, h.ee.data(), sizeof(float) * h.ee.size());
   if (r == DM_OK && qubit_err) r = up((void **)&g->qerr, qubit_err, sizeof(float) * n);
+  if (r == DM_OK && score_form == DM_SCORE_LOG_FIDELITY) {  // weights -log(1 - e): scores add up
+    if (g->eerr && dmk::launch_neg_log1m(g->eerr, (int64_t)h.ee.size(), c->stream) != cudaSuccess) r = DM_E_CUDA;
+    if (g->qerr && dmk::launch_neg_log1m(g->qerr, n, c->stream) != cudaSuccess) r = DM_E_CUDA;
+  }
   if (r == DM_OK && n <= 65536) {
     g->adj_words = (n + 63) / 64;
     size_t bytes = (size_t)n * g->adj_words * 8;

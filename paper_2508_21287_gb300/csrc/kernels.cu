@@ -295,6 +295,19 @@ cudaError_t launch_join_keys(const int32_t *rows, int32_t w, int32_t kp0, int32_
   return cudaGetLastError();
 }
 
+// In place: e -> -log(1 - e), the negative log of the fidelity 1 - e.
+__global__ void k_neg_log1m(float *w, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = -log1pf(-w[i]);
+}
+
+cudaError_t launch_neg_log1m(float *w, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  g_launches++;
+  k_neg_log1m<<<(int)imin64((n + 255) / 256, 4096), 256, 0, s>>>(w, n);
+  return cudaGetLastError();
+}
+
 __global__ void k_iota(int32_t *p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int32_t)i;

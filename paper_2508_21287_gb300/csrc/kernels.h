@@ -63,6 +63,8 @@ cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm
                        int32_t *perm_out, int64_t n, int shift, int64_t *hist, int64_t *hist_scan,
                        int64_t *tmp, cudaStream_t s);
 cudaError_t launch_iota(int32_t *p, int64_t n, cudaStream_t s);
+// In place: w[i] = -log(1 - w[i]) (error rate -> negative log fidelity).
+cudaError_t launch_neg_log1m(float *w, int64_t n, cudaStream_t s);
 // Packed join keys of a table's rows: (row[kp0] << 32) | row[kp1], or row[kp0] when kp1 < 0.
 cudaError_t launch_join_keys(const int32_t *rows, int32_t w, int32_t kp0, int32_t kp1, int64_t n,
                              unsigned long long *keys, cudaStream_t s);

@@ -35,7 +35,8 @@ def _rows_equal(a, b):
     assert np.array_equal(a, b)
 
 
-def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, join_algo=0, induced=False):
+def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, join_algo=0, induced=False,
+              score_form=0):
     plan = ctx.plan(gid, p, motifs=motifs, order=order, chunk_rows=chunk_rows, join_algo=join_algo,
                     induced=induced)
     rows, sc, cnt, cs = plan.all()
@@ -47,12 +48,12 @@ def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, j
     c2, cs2 = plan.count()
     assert c2 == ref.count and cs2 == ref.checksum
     if scores and g.edge_err is not None and ref.count:
-        want = oracle.scores(g, p, rows)
+        want = oracle.scores(g, p, rows, form=score_form)
         np.testing.assert_allclose(sc, want, rtol=RTOL, atol=0)
     return ref
 
 
-def check_topk(ctx, gid, g, p, k, **kw):
+def check_topk(ctx, gid, g, p, k, score_form=0, **kw):
     plan = ctx.plan(gid, p, **kw)
     rows, scores = plan.topk(k)
     allrows = oracle.enumerate(g, p).rows
@@ -60,7 +61,7 @@ def check_topk(ctx, gid, g, p, k, **kw):
     assert rows.shape == (m, p.n)
     if m == 0:
         return
-    s = oracle.scores(g, p, allrows)
+    s = oracle.scores(g, p, allrows, form=score_form)
     order = oracle.topk(allrows, s, k)
     np.testing.assert_allclose(scores, s[order], rtol=RTOL, atol=0)
     pos = {tuple(r): i for i, r in enumerate(allrows.tolist())}
@@ -270,6 +271,22 @@ def test_induced_matching_heavy_hex_and_random(ctx, hh, B, seed):
         plan = ctx.plan(rg, p, induced=True, chunk_rows=7)
         ref = oracle.enumerate(r, p, induced=True)
         assert plan.count() == (ref.count, ref.checksum)
+
+
+def test_log_fidelity_scores(ctx, B):
+    # scores as -log(product of fidelities 1 - e): FP32 sums of -log1p(-e) against FP64
+    g = I.lognormal_weights(I.heavy_hex(4, 6), seed=21, qubits=True)
+    gid = ctx.load(g, score_form=B.DM_SCORE_LOG_FIDELITY)
+    for seed in range(4):
+        check_all(ctx, gid, g, I.layout_query(g, seed), score_form=1)
+        check_topk(ctx, gid, g, I.layout_query(g, 10 + seed), 50, score_form=1)
+    check_topk(ctx, gid, g, I.path(18), 100, score_form=1)  # the selection-first top-k
+    bad = I.lognormal_weights(I.grid(3, 3), seed=2)
+    bad.edge_err = bad.edge_err.copy()
+    bad.edge_err[:] = 1.0
+    with pytest.raises(B.DMError) as e:
+        ctx.load(bad, score_form=B.DM_SCORE_LOG_FIDELITY)
+    assert e.value.code == B.DM_E_INVAL
 
 
 # ------------------------------------------------------------------ larger heavy-hex -------

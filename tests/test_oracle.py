@@ -218,6 +218,32 @@ def test_row_hash_binds_every_position():
     assert oracle.checksum(rows) == (2 * h) % (1 << 64)
 
 
+def test_fidelity_scores_are_the_log_of_the_product():
+    # form 1: exp(-score) is the product of the fidelities 1 - e over the mapped pattern edges
+    # and vertices, computed here as a plain product
+    g = I.lognormal_weights(I.heavy_hex(2, 3), seed=4, qubits=True)
+    p = I.path(6)
+    rows = oracle.enumerate(g, p).rows
+    s = oracle.scores(g, p, rows, form=1)
+    w = {(int(u), int(g.col_idx[k])): float(g.edge_err[k]) for u in range(g.n)
+         for k in range(g.row_ptr[u], g.row_ptr[u + 1])}
+    for r, sr in zip(rows[:200], s[:200]):
+        prod = 1.0
+        for a, b in zip(r[:-1], r[1:]):
+            prod *= 1.0 - w[(int(a), int(b))]
+        for v in r:
+            prod *= 1.0 - float(g.qubit_err[v])
+        assert np.isclose(np.exp(-sr), prod, rtol=1e-12, atol=0)
+    # constant error eps on every edge: m * -log(1 - eps); small errors: close to the sum form
+    h = I.grid(4, 4)
+    h.edge_err = np.full(len(h.col_idx), 0.01, dtype=np.float32)
+    r4 = oracle.enumerate(h, I.cycle(4)).rows
+    e32 = float(np.float32(0.01))
+    assert np.allclose(oracle.scores(h, I.cycle(4), r4, form=1), -4 * np.log1p(-e32), rtol=1e-14, atol=0)
+    s0 = oracle.scores(g, p, rows, form=0)
+    assert np.all(s >= s0) and np.all(s <= s0 * 1.02)
+
+
 def test_scores_unit_weights_equal_edge_count():
     g = I.heavy_hex(2, 3)
     g.edge_err = np.ones(len(g.col_idx), dtype=np.float32)
