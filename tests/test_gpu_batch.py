@@ -81,6 +81,34 @@ def test_batch_sort_merge_plans(B):
         _check(g, pats, counts, sums, single)
 
 
+def test_c4_full_batch_matches_oracle(B):
+    # the benchmark's whole C4 batch (512 patterns of 5-40 vertices on heavy-hex 12x6) in one
+    # persistent launch, with paper plans and with the cheapest candidate plan of each pattern
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    g, pats = bench.workload(0, 512, "c4")
+    refs = [oracle.enumerate(g, p, rows=False, threads=16) for p in pats]
+    with B.Context(0) as ctx:
+        gid = ctx.load(g)
+        paper = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx) for p in pats]
+        cheap = []
+        for p in pats:
+            cands = B.dm_plan_candidates(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
+            best = min(range(len(cands)), key=lambda i: B.dm_plan_cost(cands[i])[0])
+            cheap.append(cands[best])
+            for i, c in enumerate(cands):
+                if i != best:
+                    B.dm_plan_free(c)
+        for plans in (paper, cheap):
+            counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+            for p, r, c, s in zip(pats, refs, counts.tolist(), sums.tolist()):
+                assert (c, s) == (r.count, r.checksum), p.name
+        for pl in paper + cheap:
+            B.dm_plan_free(pl)
+
+
 def test_batch_paths_and_patches(B):
     g = I.heavy_hex(8, 9)
     pats = [I.path(k) for k in (2, 3, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]
