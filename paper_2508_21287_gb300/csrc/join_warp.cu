@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "join_device.cuh"
 #include "kernels.h"
 
@@ -316,12 +318,18 @@ static WJoinKernel pick_wjoin(const JoinArgs &a) {
 
 static size_t wjoin_smem(const JoinArgs &a) { return (size_t)WJ_WARPS * warp_smem_bytes(join_row_stride(a.w)); }
 
+// The dynamic shared-memory limit is a per-device function attribute: set it once for each
+// device that launches the kernels (contexts on several threads may race here harmlessly,
+// the call is idempotent).
 static void set_wjoin_attrs() {
-  static bool done = false;
-  if (done) return;
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return;
   WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>, k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
   for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  done = true;
+  done.fetch_or(bit);
 }
 
 int wjoin_grid(const JoinArgs &a, int num_sms) {

@@ -451,10 +451,12 @@ cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t
   if (n <= 0 || k <= 0) return cudaSuccess;
   if (k > TK_TILE / 2) return cudaErrorInvalidValue;
   if (n <= TK_SMALL) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};  // per device, as for the join kernels
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!(attr.load() & (1ull << (dev & 63)))) {
       cudaFuncSetAttribute(k_topk_small, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMALL * 8);
-      attr = true;
+      attr.fetch_or(1ull << (dev & 63));
     }
     g_launches++;
     k_topk_small<<<1, TK_SBLK, (size_t)n * 8, s>>>(sc, (int32_t)n, k, rows, w, orows, osc);
