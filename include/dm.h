@@ -138,7 +138,7 @@ int dm_motif_table(dm_ctx *ctx, dm_graph g, int32_t motif_id, int32_t *out_rows,
 /* ------------------------------------------------------------------ plans ----------- */
 
 /* Decompose a pattern into motif slices (Sec. 3.2) against a loaded data graph and fix the
- * join order. opts may be NULL. Errors: DM_E_INVAL (malformed CSR, n_p outside 1..64),
+ * join order. opts may be NULL. Errors: DM_E_INVAL (malformed CSR, n_p outside 1..128),
  * DM_E_DISCONNECTED (pattern not connected). The plan owns copies of the pattern. */
 int dm_plan(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
             const int32_t *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out);

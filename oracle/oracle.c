@@ -131,7 +131,7 @@ static int csr_adjacent(const csr_t *g, int32_t u, int32_t v) {
 
 /* ---------------------------------------------------------------- backtracking ---- */
 
-#define OR_MAXP 64
+#define OR_MAXP 128
 
 typedef struct {
     const csr_t *d, *p;

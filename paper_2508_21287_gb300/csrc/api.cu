@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <set>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -27,6 +28,7 @@ struct DevTable {
   int64_t n = 0;
   int32_t w = 0;
   bool borrowed = false;  // lives in the context's arena: never freed by its holder
+  int64_t held = 0;       // bytes counted against the memory budget while it lives
 };
 
 struct Index {
@@ -115,16 +117,27 @@ int cuda_fail(dm_ctx *c, cudaError_t e, const char *what) {
   return DM_E_CUDA;
 }
 
+// Device allocations come from the stream-ordered pool (fast reuse of the large blocks that
+// streaming allocates and frees chunk after chunk); when an allocation fails, the pool's
+// cached free memory is returned to the device and the allocation is tried once more.
+static void trim_pool(dm_ctx *c) {
+  cudaStreamSynchronize(c->stream);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  cudaGetLastError();
+}
+
 int dalloc(dm_ctx *c, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
-  if (e != cudaSuccess) {
+  for (int attempt = 0; attempt < 2; attempt++) {
+    if (cudaMallocAsync(p, bytes, c->stream) == cudaSuccess) return DM_OK;
     cudaGetLastError();
     *p = nullptr;
-    c->last_error = "cudaMallocAsync failed";
-    return DM_E_NOMEM;
+    if (attempt == 0) trim_pool(c);
   }
-  return DM_OK;
+  c->last_error = "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed (budget " +
+                  std::to_string(c->budget) + ", held by the current plan " + std::to_string(c->inflight) + ")";
+  return DM_E_NOMEM;
 }
 template <class T>
 int dalloc_t(dm_ctx *c, T **p, size_t count) {
@@ -456,7 +469,8 @@ struct Exec {
       a.w = s.w_in;
       a.wo = s.w_out;
       a.induced = p->induced;
-      for (int i = 0; i < s.n_new; i++) a.nonadj[i] = p->induced ? s.nonadj[i] : 0ull;
+      for (int i = 0; i < s.n_new; i++)
+        for (int h = 0; h < 2; h++) a.nonadj[i][h] = p->induced ? s.nonadj[i][h] : 0ull;
       for (int cc = 0; cc < a.wo; cc++) a.src_col[cc] = (int8_t)cc;
       if (j == S - 1)  // the last step writes rows in pattern-vertex order
         for (int cc = 0; cc < a.wo; cc++) a.src_col[p->col_vertex[cc]] = (int8_t)cc;
@@ -494,9 +508,14 @@ struct Exec {
     o.w = a.wo;
     int32_t *nxt = nullptr;
     if (a.mode == 0) {
-      RET(dalloc_t(c, &o.rows, (size_t)std::max<int64_t>(1, cap) * a.wo));
-      if (a.scored) RET(dalloc_t(c, &o.score, std::max<int64_t>(1, cap)));
-      if (j + 1 < S) RET(dalloc_t(c, &nxt, std::max<int64_t>(1, cap)));
+      int r = dalloc_t(c, &o.rows, (size_t)std::max<int64_t>(1, cap) * a.wo);
+      if (r == DM_OK && a.scored) r = dalloc_t(c, &o.score, std::max<int64_t>(1, cap));
+      if (r == DM_OK && j + 1 < S) r = dalloc_t(c, &nxt, std::max<int64_t>(1, cap));
+      if (r != DM_OK) {  // nothing of a failed launch stays allocated
+        free_table(c, o);
+        dfree(c, nxt);
+        return r;
+      }
     }
     a.out = o.rows;
     a.outs = o.score;
@@ -582,17 +601,52 @@ struct Exec {
         dfree(c, t_next);
         return DM_OK;
       }
-      c->inflight -= t.n * row_bytes(j);
+      c->inflight -= t.held;
       int r = sink->take(c, t);
       dfree(c, t_next);
       return r;
     }
     c->stats.max_rows = std::max(c->stats.max_rows, t.n);
     int r = process(j + 1, t, t_next, next_total);
-    c->inflight -= t.n * row_bytes(j);
+    c->inflight -= t.held;
     free_table(c, t);
     dfree(c, t_next);
     return r;
+  }
+
+  // A table was allocated for `cap` rows (its candidates) and counts against the budget with
+  // the rows that survived. When the unused part of its allocation is large (the candidates
+  // of a step can be several times its rows, and tables stay alive along the depth-first
+  // path), the rows move into an allocation of their own size, so that memory held beyond the
+  // budget stays bounded.
+  int shrink(int j, DevTable &o, int32_t *&onext, int64_t cap) {
+    const int64_t rb = row_bytes(j), alloc = std::max<int64_t>(1, cap) * rb;
+    o.held = std::max<int64_t>(1, o.n) * rb;
+    const int64_t slack_limit = std::max<int64_t>((int64_t)64 << 20, (int64_t)(c->budget / 32));
+    if (alloc - o.held < slack_limit) return DM_OK;
+    DevTable t;
+    t.n = o.n;
+    t.w = o.w;
+    int32_t *tn = nullptr;
+    int r = dalloc_t(c, &t.rows, (size_t)std::max<int64_t>(1, o.n) * o.w);
+    if (r == DM_OK && o.score) r = dalloc_t(c, &t.score, std::max<int64_t>(1, o.n));
+    if (r == DM_OK && onext) r = dalloc_t(c, &tn, std::max<int64_t>(1, o.n));
+    if (r != DM_OK) {  // keep the original allocation
+      free_table(c, t);
+      dfree(c, tn);
+      return DM_OK;
+    }
+    if (o.n > 0) {
+      CK(cudaMemcpyAsync(t.rows, o.rows, sizeof(int32_t) * o.n * o.w, cudaMemcpyDeviceToDevice, c->stream));
+      if (o.score) CK(cudaMemcpyAsync(t.score, o.score, sizeof(float) * o.n, cudaMemcpyDeviceToDevice, c->stream));
+      if (onext) CK(cudaMemcpyAsync(tn, onext, sizeof(int32_t) * o.n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    free_table(c, o);
+    dfree(c, onext);
+    o = t;
+    o.held = std::max<int64_t>(1, o.n) * rb;
+    onext = tn;
+    return DM_OK;
   }
 
   int run_one(int j, const DevTable &in, int64_t lo, int64_t hi, int64_t cap) {
@@ -601,7 +655,8 @@ struct Exec {
     int64_t ntot = 0;
     RET(launch(j, in, lo, hi, cap, &o, &onext, &ntot));
     if (st[j].base.mode == 1) return DM_OK;
-    c->inflight += o.n * row_bytes(j);
+    RET(shrink(j, o, onext, cap));
+    c->inflight += o.held;
     return descend(j, o, onext, ntot);
   }
 
@@ -614,15 +669,23 @@ struct Exec {
     if (count_last || cand_total <= lim || in.n == 1) return run_one(j, in, 0, 0, std::max<int64_t>(1, cand_total));
     // chunked streaming: split the input so that each chunk's candidates fit the budget
     int64_t *pre = nullptr, *tmp = nullptr;
-    RET(dalloc_t(c, &pre, in.n + 1));
-    RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(in.n)));
-    CK(dmk::scan_i32(in_next, pre, in.n, tmp, c->stream));
     int64_t step = std::max<int64_t>(1, lim - st[j].max_group);
     int64_t nch = (cand_total + step - 1) / step;
     // boundaries (the last row index whose prefix is <= i * step) found on the device; only
     // the nch + 1 boundaries and their prefixes come back
     int64_t *dbound = nullptr;
-    RET(dalloc_t(c, &dbound, 2 * (nch + 2)));
+    {
+      int r = dalloc_t(c, &pre, in.n + 1);
+      if (r == DM_OK) r = dalloc_t(c, &tmp, dmk::scan_tmp_elems(in.n));
+      if (r == DM_OK) r = dalloc_t(c, &dbound, 2 * (nch + 2));
+      if (r != DM_OK) {
+        dfree(c, pre);
+        dfree(c, tmp);
+        dfree(c, dbound);
+        return r;
+      }
+    }
+    CK(dmk::scan_i32(in_next, pre, in.n, tmp, c->stream));
     CK(dmk::launch_chunk_bounds(pre, in.n, step, nch, dbound, dbound + nch + 1, c->stream));
     std::vector<int64_t> hb(2 * (nch + 1) + 1);
     CK(cudaMemcpyAsync(hb.data(), dbound, sizeof(int64_t) * 2 * (nch + 1), cudaMemcpyDeviceToHost, c->stream));
@@ -1629,15 +1692,15 @@ int dm_destroy(dm_ctx *c) {
   for (DevGraph *g : c->graphs) {
     if (!g) continue;
     for (auto &kv : g->motifs) {
-      cudaFreeAsync(kv.second.rows, c->stream);
-      if (kv.second.score) cudaFreeAsync(kv.second.score, c->stream);
+      dfree(c, kv.second.rows);
+      if (kv.second.score) dfree(c, kv.second.score);
     }
     for (auto &kv : g->indices) {
-      cudaFreeAsync(kv.second.rows, c->stream);
-      if (kv.second.score) cudaFreeAsync(kv.second.score, c->stream);
-      if (kv.second.offsets) cudaFreeAsync(kv.second.offsets, c->stream);
-      if (kv.second.slots) cudaFreeAsync(kv.second.slots, c->stream);
-      if (kv.second.keys) cudaFreeAsync(kv.second.keys, c->stream);
+      dfree(c, kv.second.rows);
+      if (kv.second.score) dfree(c, kv.second.score);
+      if (kv.second.offsets) dfree(c, kv.second.offsets);
+      if (kv.second.slots) dfree(c, kv.second.slots);
+      if (kv.second.keys) dfree(c, kv.second.keys);
     }
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
@@ -2061,9 +2124,9 @@ int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor, double heavy
       if (!g) continue;
       for (auto it = g->indices.begin(); it != g->indices.end();) {
         if (it->second.v.nkeys == 2 && !it->second.keys) {
-          cudaFreeAsync(it->second.rows, c->stream);
-          if (it->second.score) cudaFreeAsync(it->second.score, c->stream);
-          cudaFreeAsync(it->second.slots, c->stream);
+          dfree(c, it->second.rows);
+          if (it->second.score) dfree(c, it->second.score);
+          dfree(c, it->second.slots);
           it = g->indices.erase(it);
         } else {
           ++it;

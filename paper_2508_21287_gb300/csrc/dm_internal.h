@@ -8,7 +8,7 @@
 
 namespace dmi {
 
-constexpr int MAXW = 64;   // pattern vertices = maximum row width of an intermediate table
+constexpr int MAXW = 128;  // pattern vertices = maximum row width of an intermediate table
 constexpr int MAXM = 24;   // motif vertices
 constexpr int MAXBE = 64;  // back-edge checks in one step
 constexpr int MAXSTEPS = 128;
@@ -57,8 +57,9 @@ struct StepSpec {
   int32_t be_col[MAXBE][2] = {};
   int32_t be_vtx[MAXBE][2] = {};
   // induced matching: per new vertex i, the working columns (< w_in + i) whose pattern vertex
-  // is not adjacent to it in the pattern; their images must not be adjacent in the data graph
-  uint64_t nonadj[MAXM] = {};
+  // is not adjacent to it in the pattern (bit c of word c / 64); their images must not be
+  // adjacent in the data graph
+  uint64_t nonadj[MAXM][2] = {};
   double est_rows = 0.0;       // planner's estimate of the rows after the step
   float feat[32] = {};         // features seen by the cardinality model
 };
@@ -153,7 +154,7 @@ struct JoinArgs {
   int8_t be_a[MAXBE];
   int8_t be_b[MAXBE];
   int32_t induced;                   // 1: also require non-adjacency for the columns in nonadj
-  unsigned long long nonadj[MAXM];   // per new vertex: working columns it must not be adjacent to
+  unsigned long long nonadj[MAXM][2];  // per new vertex: working columns it must not be adjacent to
   int32_t wo;                // output width = w + n_new
   int8_t src_col[MAXW];      // position q of a written row holds working column src_col[q]
   // data graph

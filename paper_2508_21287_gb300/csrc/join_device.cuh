@@ -297,12 +297,14 @@ __device__ __forceinline__ bool induced_ok(const JoinArgs &a, const int32_t *rro
 #pragma unroll
   for (int i = 0; i < MAXNEW; i++) {
     if (i < a.n_new && ok) {
-      unsigned long long mk = a.nonadj[i];
-      while (mk && ok) {
-        const int c = __ffsll((long long)mk) - 1;
-        mk &= mk - 1;
-        const int32_t v = c < a.w ? rrow[c] : nv_pick<MAXNEW>(nv, c - a.w);
-        ok = !adjacent(a, nv[i], v);
+      for (int h = 0; h < 2 && ok; h++) {
+        unsigned long long mk = a.nonadj[i][h];
+        while (mk && ok) {
+          const int c = 64 * h + __ffsll((long long)mk) - 1;
+          mk &= mk - 1;
+          const int32_t v = c < a.w ? rrow[c] : nv_pick<MAXNEW>(nv, c - a.w);
+          ok = !adjacent(a, nv[i], v);
+        }
       }
     }
   }

@@ -328,7 +328,7 @@ static void set_wjoin_attrs() {
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load() & bit) return;
   WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>, k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
-  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   done.fetch_or(bit);
 }
 

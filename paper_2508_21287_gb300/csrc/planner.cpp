@@ -85,50 +85,82 @@ bool motif_def(int id, MotifDef *out) {
 }
 
 // ---------------------------------------------------------------- reduced pattern -----
+static inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+// A set of pattern vertices (ids < MAXW = 128).
+struct VSet {
+  uint64_t w[2] = {0, 0};
+  bool test(int v) const { return (w[v >> 6] >> (v & 63)) & 1ull; }
+  void set(int v) { w[v >> 6] |= 1ull << (v & 63); }
+  void clear(int v) { w[v >> 6] &= ~(1ull << (v & 63)); }
+  bool any() const { return (w[0] | w[1]) != 0; }
+  int count() const { return popc64(w[0]) + popc64(w[1]); }
+  VSet operator&(const VSet &o) const {
+    VSet r;
+    r.w[0] = w[0] & o.w[0];
+    r.w[1] = w[1] & o.w[1];
+    return r;
+  }
+  VSet without(const VSet &o) const {
+    VSet r;
+    r.w[0] = w[0] & ~o.w[0];
+    r.w[1] = w[1] & ~o.w[1];
+    return r;
+  }
+  VSet with(int v) const {
+    VSet r = *this;
+    r.set(v);
+    return r;
+  }
+  int pop_lowest() {  // smallest member, removed; the set must not be empty
+    const int h = w[0] ? 0 : 1;
+    const int b = __builtin_ctzll(w[h]);
+    w[h] &= w[h] - 1;
+    return 64 * h + b;
+  }
+};
+static_assert(MAXW <= 128, "VSet holds 128 vertices");
+
 struct PState {
   int n = 0;
-  uint64_t adj0[MAXW] = {}; // pattern adjacency bitmasks
-  uint64_t unc[MAXW] = {};  // uncovered pattern edges, adjacency bitmasks
-  uint64_t mapped = 0;
+  VSet adj0[MAXW];  // pattern adjacency
+  VSet unc[MAXW];   // uncovered pattern edges
+  VSet mapped;
   int ncols = 0;
   int col_of[MAXW];
   int col_vertex[MAXW];
   int uncovered_edges = 0;
 };
 
-static inline int popc64(uint64_t x) { return __builtin_popcountll(x); }
-
 // Visit matches of motif `m` in the uncovered graph in lexicographic order of the tuple
 // (image of position 0, 1, ...). `f(img)` returns false to stop. `budget` bounds the
 // number of search nodes.
 template <class F>
 static bool match_rec(const MotifDef &m, const PState &st, bool need_overlap, int p, int *img,
-                      uint64_t used, long long &budget, F &f) {
+                      const VSet &used, long long &budget, F &f) {
   if (--budget < 0) return false;
   if (p == m.k) {
-    if (need_overlap && !(used & st.mapped)) return true;
+    if (need_overlap && !(used & st.mapped).any()) return true;
     return f(img);
   }
-  uint64_t cand;
+  VSet cand;
   int deg_p = __builtin_popcount(m.adj[p]);
   if (p == 0) {
-    cand = 0;
     for (int v = 0; v < st.n; v++)
-      if (st.unc[v]) cand |= 1ull << v;
+      if (st.unc[v].any()) cand.set(v);
   } else {
     cand = st.unc[img[m.parent[p]]];
   }
-  cand &= ~used;
-  while (cand) {
-    int v = __builtin_ctzll(cand);
-    cand &= cand - 1;
-    if (popc64(st.unc[v]) < deg_p) continue;
+  cand = cand.without(used);
+  while (cand.any()) {
+    int v = cand.pop_lowest();
+    if (st.unc[v].count() < deg_p) continue;
     bool ok = true;
     for (int q = 0; q < p && ok; q++)
-      if (m.adj[p] >> q & 1u) ok = (st.unc[v] >> img[q]) & 1ull;
+      if (m.adj[p] >> q & 1u) ok = st.unc[v].test(img[q]);
     if (!ok) continue;
     img[p] = v;
-    if (!match_rec(m, st, need_overlap, p + 1, img, used | (1ull << v), budget, f)) return false;
+    if (!match_rec(m, st, need_overlap, p + 1, img, used.with(v), budget, f)) return false;
   }
   return true;
 }
@@ -140,7 +172,7 @@ static void make_step(const MotifDef &m, const int *img, const PState &st, StepS
   s->w_in = st.ncols;
   for (int p = 0; p < m.k; p++) {
     s->slice[p] = img[p];
-    if (st.mapped >> img[p] & 1ull) {
+    if (st.mapped.test(img[p])) {
       s->key_mpos[s->n_keys] = p;
       s->key_col[s->n_keys] = st.col_of[img[p]];
       s->n_keys++;
@@ -153,30 +185,29 @@ static void make_step(const MotifDef &m, const int *img, const PState &st, StepS
     const int p = img[s->new_mpos[i]];
     for (int c = 0; c < s->w_in + i; c++) {
       const int q = c < s->w_in ? st.col_vertex[c] : img[s->new_mpos[c - s->w_in]];
-      if (!(st.adj0[p] >> q & 1ull)) s->nonadj[i] |= 1ull << c;
+      if (!st.adj0[p].test(q)) s->nonadj[i][c >> 6] |= 1ull << (c & 63);
     }
   }
   // back-edges: uncovered pattern edges with both ends mapped after this step, that the
   // slice itself does not cover
-  uint64_t after = st.mapped;
-  for (int p = 0; p < m.k; p++) after |= 1ull << img[p];
-  uint64_t cov[MAXW] = {};
+  VSet after = st.mapped;
+  for (int p = 0; p < m.k; p++) after.set(img[p]);
+  VSet cov[MAXW];
   for (auto &e : m.edges) {
-    cov[img[e.first]] |= 1ull << img[e.second];
-    cov[img[e.second]] |= 1ull << img[e.first];
+    cov[img[e.first]].set(img[e.second]);
+    cov[img[e.second]].set(img[e.first]);
   }
   int colmap[MAXW];
-  for (int v = 0; v < st.n; v++) colmap[v] = (st.mapped >> v & 1ull) ? st.col_of[v] : -1;
+  for (int v = 0; v < st.n; v++) colmap[v] = st.mapped.test(v) ? st.col_of[v] : -1;
   for (int i = 0; i < s->n_new; i++) colmap[img[s->new_mpos[i]]] = s->w_in + i;
   for (int a = 0; a < st.n; a++) {
-    if (!(after >> a & 1ull)) continue;
-    uint64_t rest = st.unc[a] & ~cov[a] & after;
-    while (rest) {
-      int b = __builtin_ctzll(rest);
-      rest &= rest - 1;
+    if (!after.test(a)) continue;
+    VSet rest = st.unc[a].without(cov[a]) & after;
+    while (rest.any()) {
+      int b = rest.pop_lowest();
       if (b <= a) continue;
       // only edges that become checkable now: at least one endpoint is new in this step
-      bool a_new = !(st.mapped >> a & 1ull), b_new = !(st.mapped >> b & 1ull);
+      bool a_new = !st.mapped.test(a), b_new = !st.mapped.test(b);
       if (!a_new && !b_new) continue;
       if (s->n_be < MAXBE) {
         s->be_vtx[s->n_be][0] = a;
@@ -192,22 +223,22 @@ static void make_step(const MotifDef &m, const int *img, const PState &st, StepS
 static void apply_step(const MotifDef &m, const StepSpec &s, PState *st) {
   for (auto &e : m.edges) {
     int a = s.slice[e.first], b = s.slice[e.second];
-    if (st->unc[a] >> b & 1ull) st->uncovered_edges--;
-    st->unc[a] &= ~(1ull << b);
-    st->unc[b] &= ~(1ull << a);
+    if (st->unc[a].test(b)) st->uncovered_edges--;
+    st->unc[a].clear(b);
+    st->unc[b].clear(a);
   }
   for (int i = 0; i < s.n_new; i++) {
     int v = s.slice[s.new_mpos[i]];
     st->col_of[v] = st->ncols;
     st->col_vertex[st->ncols] = v;
     st->ncols++;
-    st->mapped |= 1ull << v;
+    st->mapped.set(v);
   }
   for (int i = 0; i < s.n_be && i < MAXBE; i++) {
     int a = s.be_vtx[i][0], b = s.be_vtx[i][1];
-    if (st->unc[a] >> b & 1ull) st->uncovered_edges--;
-    st->unc[a] &= ~(1ull << b);
-    st->unc[b] &= ~(1ull << a);
+    if (st->unc[a].test(b)) st->uncovered_edges--;
+    st->unc[a].clear(b);
+    st->unc[b].clear(a);
   }
 }
 
@@ -257,8 +288,8 @@ static int build_pstate(const Plan &pat, PState *st) {
   for (int u = 0; u < pat.n_p; u++)
     for (int k = pat.rp[u]; k < pat.rp[u + 1]; k++) {
       int v = pat.ci[k];
-      st->unc[u] |= 1ull << v;
-      st->adj0[u] |= 1ull << v;
+      st->unc[u].set(v);
+      st->adj0[u].set(v);
       if (u < v) st->uncovered_edges++;
     }
   for (int i = 0; i < MAXW; i++) st->col_of[i] = -1;
@@ -307,7 +338,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
   int guard = 0;
   while (st.uncovered_edges > 0) {
     if (++guard > MAXSTEPS) return DM_E_INVAL;
-    bool first = st.mapped == 0;
+    bool first = !st.mapped.any();
     StepSpec best;
     bool found = false;
     if (order == DM_ORDER_PAPER) {
@@ -319,7 +350,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
           make_step(m, im, st, &s);
           return false;  // first match is enough
         };
-        match_rec(m, st, !first, 0, img, 0, budget, f);
+        match_rec(m, st, !first, 0, img, VSet(), budget, f);
         if (budget >= 0 && s.k == m.k && s.motif == m.id) {
           best = s;
           found = true;
@@ -329,7 +360,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
       if (found) {
         MotifDef bd;
         motif_def(best.motif, &bd);
-        step_features(best, (int)bd.edges.size(), log_rows, pat.n_p, popc64(st.mapped), st.uncovered_edges, gs,
+        step_features(best, (int)bd.edges.size(), log_rows, pat.n_p, st.mapped.count(), st.uncovered_edges, gs,
                       best.feat);
         best.est_rows = exp(heuristic_log_rows(best.feat));
       }
@@ -337,7 +368,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
       // greedy: the match with the smallest estimated growth per new vertex (independence
       // estimate); ties: the larger motif, then enumeration order
       double bscore = 1e300;
-      const int mapped_before = popc64(st.mapped);
+      const int mapped_before = st.mapped.count();
       StepSpec s;
       float f[NFEAT];
       for (auto &m : defs) {
@@ -358,7 +389,7 @@ int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
           }
           return ++taken < 256;
         };
-        match_rec(m, st, !first, 0, img, 0, budget, visit);
+        match_rec(m, st, !first, 0, img, VSet(), budget, visit);
       }
       if (!found) return DM_E_INVAL;
       best.est_rows = exp(heuristic_log_rows(best.feat));

@@ -238,7 +238,7 @@ cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void
 __global__ void k_sort_within_rows(int32_t *rows, int64_t n, int32_t w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t *r = rows + i * w;
-    for (int a = 1; a < w; a++) {  // insertion sort: rows are at most 64 ids
+    for (int a = 1; a < w; a++) {  // insertion sort: rows are at most 128 ids
       int32_t x = r[a];
       int b = a - 1;
       while (b >= 0 && r[b] > x) {

@@ -329,6 +329,23 @@ def test_streaming_far_beyond_the_budget_is_consistent(ctx, B):
     assert got[0] == got[1] and got[0][0] > 10 ** 9
 
 
+def test_patterns_beyond_64_vertices(ctx, B):
+    # 91- and 106-vertex heavy-hex patches in larger heavy-hex graphs (rigid: few placements),
+    # and random connected 80- and 100-vertex sub-patches of the 4485-vertex heavy-hex
+    for (a, b), (c, d) in (((3, 7), (2, 6)), ((4, 6), (3, 5))):
+        g, p = I.heavy_hex(a, b), I.heavy_hex(c, d)
+        assert p.n > 64
+        check_all(ctx, ctx.load(g), g, p, scores=False)
+    g = I.heavy_hex(25, 34)
+    gid = ctx.load(g)
+    for n, seed in ((80, 1), (100, 1), (100, 2)):
+        p = I.sub_patch(g, n, seed)
+        ref = oracle.enumerate(g, p, rows=False, threads=16)
+        # the greedy order keeps the intermediate tables near the result size at this scale
+        # (the paper's order streams hundreds of millions of rows on some of them)
+        assert ctx.plan(gid, p, order=B.DM_ORDER_HEURISTIC).count() == (ref.count, ref.checksum)
+
+
 # ------------------------------------------------------------------ other graphs -----------
 def _er(n, p1000, seed):
     rng = I.SplitMix64(seed)
