@@ -1116,7 +1116,7 @@ int build_motif_by_joins(dm_ctx *c, DevGraph *g, const MotifDef &md) {
   RET(ensure_motif(c, g, 2));
   GraphStats gs;
   gs.V = g->V;
-  int r = decompose(mp, set, DM_ORDER_PAPER, gs, nullptr, nullptr, &mp.steps, mp.col_vertex);
+  int r = decompose(mp, set, DM_ORDER_PAPER, gs, &mp.steps, mp.col_vertex);
   if (r != DM_OK) return r;
   Exec ex;
   ex.c = c;
@@ -1459,17 +1459,6 @@ void normalise(const dm_ctx *c, const float *x, int32_t n, std::vector<float> &o
     for (int k = 0; k < NFEAT; k++) out[(size_t)i * NFEAT + k] = (x[(size_t)i * NFEAT + k] - c->m_mean[k]) / c->m_std[k];
 }
 
-// DM_ORDER_LEARNED: predicted log rows after each candidate step (planner feature vectors).
-int model_predict_plan(void *self, const float *feats, int n, float *out) {
-  dm_ctx *c = (dm_ctx *)self;
-  std::vector<float> x((size_t)n * NFEAT), xn, y(n);
-  for (int i = 0; i < n; i++) model_input(feats + (size_t)i * NFEAT, &x[(size_t)i * NFEAT]);
-  normalise(c, x.data(), n, xn);
-  RET(model_run(c, xn.data(), nullptr, n, y.data(), nullptr, nullptr));
-  for (int i = 0; i < n; i++) out[i] = feats[(size_t)i * NFEAT] + y[i];
-  return DM_OK;
-}
-
 // Predicted cost of a plan: bytes of every intermediate table it writes (rows from the chain
 // of predicted log growths, model or heuristic) plus 64 KiB per step for launch and barrier
 // overheads; and its largest predicted table.
@@ -1583,7 +1572,7 @@ int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, Gra
       CandidatePlan cp;
       cp.motifs = set;
       cp.order = ord;
-      if (decompose(p, set, ord, gs, nullptr, nullptr, &cp.steps, cp.col_vertex) != DM_OK) continue;
+      if (decompose(p, set, ord, gs, &cp.steps, cp.col_vertex) != DM_OK) continue;
       out->push_back(std::move(cp));
     }
   return DM_OK;
@@ -1884,8 +1873,8 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
   RET(plan_setup(c, gh, n_p, p_row_ptr, p_col_idx, opts, p, &g, gs));
   const bool learned = p.order == DM_ORDER_LEARNED && c->m_trained;
   if (!learned) {
-    RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, nullptr, nullptr,
-                  &p.steps, p.col_vertex));
+    RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, &p.steps,
+                  p.col_vertex));
     RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows));
   } else {
     // The trained model picks the plan among the candidate decompositions, costed with the
@@ -1987,7 +1976,7 @@ int32_t dm_decompose(int32_t n_p, const int32_t *p_row_ptr, const int32_t *p_col
   gs.avg_deg = 1;
   gs.max_deg = 1;
   for (int id : set) gs.motifs.push_back({id, 1});
-  RET(decompose(p, set, order, gs, nullptr, nullptr, &p.steps, p.col_vertex));
+  RET(decompose(p, set, order, gs, &p.steps, p.col_vertex));
   return describe_steps(p.steps, buf, buf_len);
 }
 

@@ -81,10 +81,8 @@ struct GraphStats {
   }
 };
 
-// Cardinality model: returns predicted log(rows after the step) for each candidate (one
-// feature vector of NFEAT floats each). Used by DM_ORDER_LEARNED.
+// Features per candidate step seen by the cardinality model (DM_ORDER_LEARNED).
 constexpr int NFEAT = 32;
-typedef int (*CardModelFn)(void *self, const float *feats, int n, float *out_log_rows);
 
 struct Plan {
   int32_t n_p = 0;
@@ -102,8 +100,7 @@ struct Plan {
 
 // Decompose a pattern (Sec. 3.2). Returns 0 or a DM_E_* code.
 int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
-              const GraphStats &gs, CardModelFn model, void *model_self, std::vector<StepSpec> *out,
-              int32_t *col_vertex);
+              const GraphStats &gs, std::vector<StepSpec> *out, int32_t *col_vertex);
 
 // Features of a candidate step (for the heuristic and the learned model).
 void step_features(const StepSpec &s, int n_edges, double log_rows_prev, int n_p, int mapped_before,

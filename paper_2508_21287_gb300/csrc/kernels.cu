@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(RS_BLK) k_radix_scatter(const uint32_t *keys, 
                                                           const int64_t *off, int nb, int32_t *perm_out) {
   __shared__ int wcnt[RS_BLK / 32][256];
   __shared__ int run[256];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   run[tid] = 0;
   for (int w = 0; w < RS_BLK / 32; w++) wcnt[w][tid] = 0;
   __syncthreads();

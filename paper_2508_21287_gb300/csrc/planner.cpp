@@ -16,9 +16,10 @@
 //    (a back-edge; the paper would join Res(M2) on both endpoints instead);
 //  * M2 always matches an uncovered edge that touches the mapped set (the pattern is
 //    connected), so the loop always ends.
-// DM_ORDER_HEURISTIC / DM_ORDER_LEARNED instead pick, among candidate slices of every
-// motif, the one with the smallest estimated growth of the intermediate table per newly
-// mapped vertex (estimate: independence heuristic, or the trained model).
+// DM_ORDER_HEURISTIC instead picks, among candidate slices of every motif, the one with the
+// smallest estimated growth of the intermediate table per newly mapped vertex (independence
+// estimate). DM_ORDER_LEARNED chooses among whole candidate plans (api.cu) by the trained
+// model's predicted cost.
 #include <math.h>
 #include <string.h>
 
@@ -297,8 +298,7 @@ static int build_pstate(const Plan &pat, PState *st) {
 }
 
 int decompose(const Plan &pat, const std::vector<int32_t> &motif_set, int order,
-              const GraphStats &gs, CardModelFn model, void *model_self, std::vector<StepSpec> *out,
-              int32_t *col_vertex) {
+              const GraphStats &gs, std::vector<StepSpec> *out, int32_t *col_vertex) {
   out->clear();
   PState st;
   build_pstate(pat, &st);
