@@ -919,6 +919,8 @@ int deliver(dm_ctx *c, const DevTable &t, int flags, dm_chunk_cb cb, void *user,
 
 struct TopkSink;
 int topk_take(dm_ctx *c, TopkSink *t, DevTable tab);
+bool topk_small_enough(const TopkSink *t);
+int topk_into_host(dm_ctx *c, TopkSink *t, const DevTable &sorted, int32_t *rows, float *scores, int64_t *n);
 
 struct AllSink : Sink {
   TopkSink *tap = nullptr;  // also feeds every final chunk to a top-k accumulator
@@ -930,16 +932,25 @@ struct AllSink : Sink {
   int64_t held_bytes = 0;
   bool streaming = false;
   uint64_t count = 0, checksum = 0;
+  // host buffers of the caller's top-k: when the whole result is one table, its top-k is
+  // copied out under the same synchronisation as the count and checksum
+  int32_t *final_rows = nullptr;
+  float *final_scores = nullptr;
+  bool final_done = false;
+  int64_t final_n = 0;
   // sort (checksum fused into the key packing), one synchronisation, delivery, then the top-k
-  // tap (which takes the table over)
-  int flush_one(dm_ctx *c, DevTable &t) {
+  // tap (which takes the table over). last: no table follows, nothing was flushed before.
+  int flush_one(dm_ctx *c, DevTable &t, bool last = false) {
     CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, c->stream));
     RET(sort_canonical(c, t, bits, c->d_ctr));
+    const bool fast_topk = last && tap && final_rows && topk_small_enough(tap);
+    if (fast_topk) RET(topk_into_host(c, tap, t, final_rows, final_scores, &final_n));
     RET(read_ctr(c));
+    final_done = fast_topk;
     count += (uint64_t)t.n;
     checksum += c->h_ctr[CTR_SUM];
     int r = deliver(c, t, flags, cb, user, true);
-    if (r == DM_OK && tap) return topk_take(c, tap, t);  // the tap takes ownership
+    if (r == DM_OK && tap && !fast_topk) return topk_take(c, tap, t);  // the tap takes ownership
     free_table(c, t);
     return r;
   }
@@ -961,14 +972,14 @@ struct AllSink : Sink {
     if (held.size() == 1) {  // sorting makes its own copy: no concatenation needed
       DevTable t = held[0];
       held.clear();
-      return flush_one(c, t);
+      return flush_one(c, t, !streaming);
     }
     CollectSink cs;
     cs.parts = held;
     held.clear();
     DevTable all;
     RET(cs.concat(c, w, scored, &all));
-    return flush_one(c, all);
+    return flush_one(c, all, !streaming);
   }
 };
 
@@ -1090,6 +1101,29 @@ struct TopkSink : Sink {
 };
 
 int topk_take(dm_ctx *c, TopkSink *t, DevTable tab) { return t->take(c, tab); }
+
+bool topk_small_enough(const TopkSink *t) { return !t->have && t->k <= 1024; }
+
+// Top-k of a canonically sorted table straight into the caller's host buffers (enqueued on
+// the stream; the caller synchronises); the table stays with the caller.
+int topk_into_host(dm_ctx *c, TopkSink *t, const DevTable &sorted, int32_t *rows, float *scores, int64_t *n) {
+  const int64_t m = std::min<int64_t>(t->k, sorted.n);
+  *n = m;
+  if (m <= 0) return DM_OK;
+  DevTable o;
+  o.w = sorted.w;
+  o.n = m;
+  RET(dalloc_t(c, &o.rows, (size_t)m * sorted.w));
+  RET(dalloc_t(c, &o.score, m));
+  void *tmp = nullptr;
+  RET(dalloc(c, &tmp, (size_t)dmk::topk_tmp_bytes(sorted.n)));
+  CK(dmk::topk_sorted(sorted.rows, sorted.score, sorted.n, sorted.w, (int32_t)t->k, tmp, o.rows, o.score, c->stream));
+  dfree(c, tmp);
+  CK(cudaMemcpyAsync(rows, o.rows, sizeof(int32_t) * m * o.w, cudaMemcpyDeviceToHost, c->stream));
+  if (scores) CK(cudaMemcpyAsync(scores, o.score, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream));
+  free_table(c, o);
+  return DM_OK;
+}
 
 int ensure_motif(dm_ctx *c, DevGraph *g, int id);
 
@@ -2193,11 +2227,17 @@ int dm_match_topk(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void
   sink.user = user;
   sink.bits = graph_bits(g);
   sink.tap = &tk;
+  sink.final_rows = out_rows;
+  sink.final_scores = out_scores;
   ex.sink = &sink;
   int r = ex.run();
   if (r == DM_OK) r = sink.finish(c, pl->p.n_p, true);
   for (auto &h : sink.held) free_table(c, h);
-  if (r == DM_OK) {
+  if (r == DM_OK && sink.final_done) {  // copied out with the last flush
+    *out_n = (int32_t)sink.final_n;
+    if (out_count) *out_count = sink.count;
+    if (out_checksum) *out_checksum = sink.checksum;
+  } else if (r == DM_OK) {
     int64_t m = tk.have ? tk.best.n : 0;
     if (m > 0) {
       CK(cudaMemcpyAsync(out_rows, tk.best.rows, sizeof(int32_t) * m * tk.best.w, cudaMemcpyDeviceToHost, c->stream));

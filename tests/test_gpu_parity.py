@@ -166,6 +166,25 @@ def test_match_topk_one_pass(ctx, hh, B, seed):
     assert st["kernel_launches"] > 0 and st["join_launches"] == st["chunks"]
 
 
+@pytest.mark.parametrize("chunk_rows", [0, 700])
+def test_match_topk_device_rows_and_streamed(ctx, hh, B, chunk_rows):
+    # the benchmark's call (device rows) and a streamed result (several flushes): the top-k and
+    # the checksum are the oracle's either way
+    g, gid = hh
+    for seed in (4, 5):
+        p = I.layout_query(g, seed)
+        plan = ctx.plan(gid, p, chunk_rows=chunk_rows)
+        seen = []
+        rows_k, sc_k, cnt, cs = B.dm_match_topk(ctx.h, plan.h, B.DM_ALL | B.DM_DEVICE_ROWS,
+                                                lambda r, s, m, n: seen.append(m) and 0, 100, p.n)
+        ref = oracle.enumerate(g, p)
+        assert cnt == ref.count == sum(seen) and cs == ref.checksum
+        s = oracle.scores(g, p, ref.rows)
+        order = oracle.topk(ref.rows, s, 100)
+        np.testing.assert_allclose(sc_k, s[order], rtol=RTOL, atol=0)
+        assert rows_k.shape == (min(100, ref.count), p.n)
+
+
 def test_topk_more_than_count_and_no_embeddings(ctx, hh, B):
     g, gid = hh
     check_topk(ctx, gid, g, I.cycle(12), 1000)      # 576 < k
