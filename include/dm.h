@@ -282,6 +282,11 @@ int dm_step_log(dm_ctx *ctx, float *feats, float *targets, int64_t cap, int64_t 
  * and from the independence heuristic otherwise. */
 int dm_plan_cost(const dm_plan_t *plan, double *cost, double *max_rows);
 
+/* Predicted rows after each step of a plan (the chain of predicted log growths it was costed
+ * with: the trained model's for DM_ORDER_LEARNED plans, the independence heuristic's
+ * otherwise). Writes up to cap values and returns the number of steps (or DM_E_INVAL). */
+int32_t dm_plan_predicted_rows(const dm_plan_t *plan, double *rows, int32_t cap);
+
 /* The model inputs of a plan's steps (cap rows of DM_MODEL_FEATURES) and the independence
  * heuristic's log growth of each; returns the number of steps. */
 int dm_plan_estimates(const dm_plan_t *plan, float *feats, float *heur_growth, int32_t cap);

@@ -90,6 +90,7 @@ _SIGS = {
     "dm_motif_table": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i64, ctypes.POINTER(_i64), _i32p]),
     "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_free": (None, [_vp]),
+    "dm_plan_predicted_rows": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
     "dm_plan_candidates": (_i32, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp), _i32]),
     "dm_plan_describe": (_i32, [_vp, _i32p, _i32]),
     "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
@@ -444,6 +445,14 @@ def dm_plan_cost(plan):
     c, m = ctypes.c_double(), ctypes.c_double()
     _check(_lib.dm_plan_cost(plan, ctypes.byref(c), ctypes.byref(m)), "dm_plan_cost")
     return c.value, m.value
+
+
+def dm_plan_predicted_rows(plan) -> np.ndarray:
+    n = _lib.dm_plan_predicted_rows(plan, None, 0)
+    _check(min(n, 0), "dm_plan_predicted_rows")
+    out = np.zeros(max(1, n), dtype=np.float64)
+    _lib.dm_plan_predicted_rows(plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+    return out[:n]
 
 
 def dm_plan_estimates(plan):

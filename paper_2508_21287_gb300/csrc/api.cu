@@ -1498,7 +1498,7 @@ void normalise(const dm_ctx *c, const float *x, int32_t n, std::vector<float> &o
 // overheads; and its largest predicted table.
 // Costs of several plans with one model evaluation over all their steps (see plan_cost).
 int plan_costs(dm_ctx *c, const std::vector<const std::vector<StepSpec> *> &plans, std::vector<double> *cost,
-               std::vector<double> *max_rows) {
+               std::vector<double> *max_rows, std::vector<std::vector<float>> *growths) {
   int total = 0;
   for (auto *st : plans) total += (int)st->size();
   std::vector<float> x((size_t)std::max(1, total) * NFEAT), growth(std::max(1, total));
@@ -1516,10 +1516,12 @@ int plan_costs(dm_ctx *c, const std::vector<const std::vector<StepSpec> *> &plan
   }
   cost->assign(plans.size(), 0.0);
   max_rows->assign(plans.size(), 0.0);
+  growths->assign(plans.size(), {});
   k = 0;
   for (size_t i = 0; i < plans.size(); i++) {
     double lr = 0, tot = 0, mx = 0;
     for (auto &s : *plans[i]) {
+      (*growths)[i].push_back(growth[k]);
       lr += growth[k++];
       double rows = exp(std::min(60.0, std::max(-60.0, lr)));
       mx = std::max(mx, rows);
@@ -1531,7 +1533,8 @@ int plan_costs(dm_ctx *c, const std::vector<const std::vector<StepSpec> *> &plan
   return DM_OK;
 }
 
-int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, double *cost, double *max_rows) {
+int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, double *cost, double *max_rows,
+              std::vector<float> *growth_out = nullptr) {
   const int n = (int)steps.size();
   std::vector<float> x((size_t)std::max(1, n) * NFEAT), growth(std::max(1, n));
   for (int j = 0; j < n; j++) {
@@ -1552,6 +1555,7 @@ int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, dou
   }
   *cost = total;
   *max_rows = mx;
+  if (growth_out) growth_out->assign(growth.begin(), growth.begin() + n);
   return DM_OK;
 }
 
@@ -1909,7 +1913,7 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
   if (!learned) {
     RET(decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs, &p.steps,
                   p.col_vertex));
-    RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows));
+    RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows, &p.pred_growth));
   } else {
     // The trained model picks the plan among the candidate decompositions, costed with the
     // model's per-step cardinalities.
@@ -1918,7 +1922,8 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
     std::vector<const std::vector<StepSpec> *> steps;
     for (auto &cp : cands) steps.push_back(&cp.steps);
     std::vector<double> cost, maxr;
-    RET(plan_costs(c, steps, &cost, &maxr));  // one model evaluation for every candidate
+    std::vector<std::vector<float>> growths;
+    RET(plan_costs(c, steps, &cost, &maxr, &growths));  // one model evaluation for every candidate
     double best = 1e308;
     for (size_t i = 0; i < cands.size(); i++) {
       if (cost[i] < best) {
@@ -1927,6 +1932,7 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
         memcpy(p.col_vertex, cands[i].col_vertex, sizeof(cands[i].col_vertex));
         p.pred_cost = cost[i];
         p.pred_max_rows = maxr[i];
+        p.pred_growth = growths[i];
         p.motifs = cands[i].motifs;
       }
     }
@@ -1954,7 +1960,7 @@ int32_t dm_plan_candidates(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p
     p.motifs = cands[i].motifs;
     p.steps = cands[i].steps;
     memcpy(p.col_vertex, cands[i].col_vertex, sizeof(p.col_vertex));
-    int r = plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows);
+    int r = plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows, &p.pred_growth);
     if (r == DM_OK) r = plan_finish(c, g, p);
     if (r != DM_OK) {
       for (int32_t j = 0; j < i; j++) {
@@ -2410,6 +2416,17 @@ int dm_plan_cost(const dm_plan_t *pl, double *cost, double *max_rows) {
   if (cost) *cost = pl->p.pred_cost;
   if (max_rows) *max_rows = pl->p.pred_max_rows;
   return DM_OK;
+}
+
+int32_t dm_plan_predicted_rows(const dm_plan_t *pl, double *rows, int32_t cap) {
+  if (!pl || cap < 0 || (cap > 0 && !rows)) return DM_E_INVAL;
+  const int32_t n = (int32_t)pl->p.pred_growth.size();
+  double lr = 0;
+  for (int32_t j = 0; j < n && j < cap; j++) {
+    lr += pl->p.pred_growth[j];
+    rows[j] = exp(std::min(60.0, std::max(-60.0, lr)));
+  }
+  return n;
 }
 
 int dm_plan_estimates(const dm_plan_t *pl, float *feats, float *heur_growth, int32_t cap) {

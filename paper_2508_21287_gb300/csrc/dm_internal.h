@@ -96,6 +96,7 @@ struct Plan {
   int64_t chunk_rows = 0, max_rows = 0;
   double pred_cost = 0;      // predicted bytes moved by the joins plus a per-step overhead
   double pred_max_rows = 0;  // predicted largest intermediate table
+  std::vector<float> pred_growth;  // predicted log growth of each step (model or heuristic)
 };
 
 // Decompose a pattern (Sec. 3.2). Returns 0 or a DM_E_* code.

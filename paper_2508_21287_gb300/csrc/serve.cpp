@@ -65,31 +65,24 @@ struct dm_server {
 namespace {
 
 // Projected device bytes of a plan: the largest pair of consecutive tables it materialises,
-// from the estimated log growth of each step (the trained model's when `c` has one and the
-// plan was made in the learned order, else the independence heuristic's).
-uint64_t projected_bytes(dm_ctx *c, bool learned, const dm_plan_t *pl, int64_t *max_rows_est) {
+// from the rows the plan predicts after each step (the trained model's for plans made in the
+// learned order, the independence heuristic's otherwise) and the tables' widths.
+uint64_t projected_bytes(const dm_plan_t *pl, int64_t *max_rows_est) {
   int32_t nwords = dm_plan_describe(pl, nullptr, 0);
   std::vector<int32_t> d(nwords > 0 ? nwords : 1);
   dm_plan_describe(pl, d.data(), nwords);
   int32_t n_steps = d[0];
-  std::vector<float> heur(n_steps > 0 ? n_steps : 1);
-  std::vector<float> feats((size_t)(n_steps > 0 ? n_steps : 1) * DM_MODEL_FEATURES);
-  dm_plan_estimates(pl, feats.data(), heur.data(), n_steps);
-  if (learned && n_steps > 0) {
-    std::vector<float> pred(n_steps);
-    if (dm_model_predict(c, feats.data(), n_steps, pred.data()) == DM_OK) heur = pred;
-  }
-  // walk the steps for the widths; estimated rows come from the planner's log growth chain
-  double lrows = 0.0, prev_bytes = 0.0, best = 0.0, maxr = 0.0;
+  std::vector<double> rows_after(n_steps > 0 ? n_steps : 1, 0.0);
+  dm_plan_predicted_rows(pl, rows_after.data(), n_steps);
+  double prev_bytes = 0.0, best = 0.0, maxr = 0.0;
   int32_t pos = 1, w = 0;
-  for (int32_t j = 0; j < n_steps; j++) {
+  for (int32_t j = 0; j < n_steps; j++) {  // walk the steps for the widths
     int32_t k = d[pos + 1];
     int32_t n_keys = d[pos + 2 + k];
     int32_t n_be = d[pos + 3 + k];
     w += k - n_keys;
     pos += 4 + k + 2 * n_be;
-    lrows += heur[j];
-    double rows = exp(std::min(60.0, lrows));
+    double rows = rows_after[j];
     maxr = std::max(maxr, rows);
     double bytes = rows * (4.0 * w + 4.0);
     best = std::max(best, bytes + prev_bytes);
@@ -123,7 +116,7 @@ void worker(dm_server *s, int slot) {
     bool reserved = false;
     if (rc == DM_OK) {
       int64_t est_rows = 0;
-      need = std::max<uint64_t>(projected_bytes(c, s->opts.order == DM_ORDER_LEARNED, pl, &est_rows), 1);
+      need = std::max<uint64_t>(projected_bytes(pl, &est_rows), 1);
       if (need > s->pool_total || (s->opts.max_rows > 0 && est_rows > s->opts.max_rows)) rc = DM_E_CAPACITY;
     }
     if (rc == DM_OK) {  // admission: wait until the projected memory fits the shared pool

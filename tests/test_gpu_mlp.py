@@ -88,6 +88,18 @@ def test_training_beats_the_heuristic(B):
             got = _log_steps(B, ctx, gid, [c], B.DM_ORDER_LEARNED)[0]
             ref = oracle.enumerate(g, c, rows=False, threads=8)
             assert got == (ref.count, ref.checksum)
+        # a learned plan keeps the model's per-step predictions it was chosen by; a paper plan
+        # keeps the independence heuristic's
+        p = held[3]
+        pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=B.DM_ORDER_LEARNED)
+        f, h = B.dm_plan_estimates(pl)
+        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(B.dm_model_predict(ctx.h, f))),
+                                   rtol=1e-5)
+        B.dm_plan_free(pl)
+        pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
+        f, h = B.dm_plan_estimates(pl)
+        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(h.astype(np.float64))), rtol=1e-5)
+        B.dm_plan_free(pl)
         # checkpoint: weights out and back in give the same predictions
         w = B.dm_model_weights(ctx.h)
         B.dm_model_init(ctx.h, 99)
