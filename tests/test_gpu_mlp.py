@@ -93,12 +93,12 @@ def test_training_beats_the_heuristic(B):
         p = held[3]
         pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=B.DM_ORDER_LEARNED)
         f, h = B.dm_plan_estimates(pl)
-        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(B.dm_model_predict(ctx.h, f))),
-                                   rtol=1e-5)
+        pred = B.dm_model_predict(ctx.h, f).astype(np.float64)
+        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(pred)), rtol=1e-9)
         B.dm_plan_free(pl)
         pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
         f, h = B.dm_plan_estimates(pl)
-        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(h.astype(np.float64))), rtol=1e-5)
+        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(h.astype(np.float64))), rtol=1e-9)
         B.dm_plan_free(pl)
         # checkpoint: weights out and back in give the same predictions
         w = B.dm_model_weights(ctx.h)
