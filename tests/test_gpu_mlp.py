@@ -93,8 +93,8 @@ def test_training_beats_the_heuristic(B):
         p = held[3]
         pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=B.DM_ORDER_LEARNED)
         f, h = B.dm_plan_estimates(pl)
-        pred = B.dm_model_predict(ctx.h, f).astype(np.float64)
-        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(pred)), rtol=1e-9)
+        pred_plan = B.dm_model_predict(ctx.h, f).astype(np.float64)
+        np.testing.assert_allclose(B.dm_plan_predicted_rows(pl), np.exp(np.cumsum(pred_plan)), rtol=1e-9)
         B.dm_plan_free(pl)
         pl = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
         f, h = B.dm_plan_estimates(pl)
