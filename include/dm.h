@@ -243,8 +243,9 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
  * accumulation) predicts, for a candidate join step, the log growth of the intermediate
  * table, log(1 + rows after) - log(1 + rows before). DM_ORDER_LEARNED plans are the cheapest,
  * under the model's predicted cardinalities, of several candidate decompositions (the
- * paper's rule and the greedy heuristic order, with the given motif set and with larger
- * motifs typical of the topology); without a trained model they use the heuristic order.
+ * paper's rule and the greedy heuristic order, with the given motif set, with motifs
+ * typical of the topology, and with two half-length paths for patterns of 16+ vertices; see
+ * dm_plan_candidates); without a trained model they use the heuristic order.
  * The output set never depends on the order. Feature vectors are DM_MODEL_FEATURES floats
  * (dm_plan_estimates / dm_step_log give them); parameters are FP32, flat, in the order
  * W1[128][32] b1[128] W2[128][128] b2[128] w3[128] b3, followed by the 32 input means and

@@ -1560,8 +1560,8 @@ int plan_cost(dm_ctx *c, const std::vector<StepSpec> &steps, bool use_model, dou
 }
 
 // The candidate decompositions DM_ORDER_LEARNED chooses from: the paper's rule and the greedy
-// heuristic order, each over the plan's motif set and over sets with a larger motif typical
-// of the topology (M8 or M12-O at degree <= 3, M6-2O or M6 at degree 4), and, for patterns of
+// heuristic order, each over the plan's motif set and over sets with a motif typical of the
+// topology (M8, M12-O or the claw M4-1 at degree <= 3, M6-2O or M6 at degree 4), and, for patterns of
 // 16+ vertices, over a set with two paths of about half the pattern: a long cycle then becomes
 // one path joined with a second path on both of its end vertices (a two-key join) instead of
 // a path grown to nearly the pattern's length and closed by a back-edge. Half-length paths are
@@ -1578,7 +1578,7 @@ int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, Gra
   std::vector<std::vector<int32_t>> sets{p.motifs};
   std::vector<int32_t> extra;
   if (!user_motifs) {
-    if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12)};
+    if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12), DM_MOTIF_M4_1};
     else if (g->max_deg == 4) extra = {DM_MOTIF_M6_2O, 6};
     else extra = {4};
   }
