@@ -6,7 +6,8 @@
  * data graph G_d and pattern graph G_p, enumerate every injective map f : V_p -> V_d such
  * that each pattern edge {u, v} maps onto a data edge {f(u), f(v)}. The library follows the
  * method's reading of that statement (Alg. 1 with the overlap filter of Sec. 3.2): edges
- * must be preserved, non-edges need not be (monomorphisms). Induced matching is future work.
+ * must be preserved, non-edges need not be (monomorphisms); dm_plan_opts.induced = 1 adds the
+ * non-edge condition of the literal statement.
  *
  * Method (Sec. 3.2-3.3, Alg. 1, Alg. 2): the pattern is decomposed into motif slices (paths,
  * cycles, stars, ...); the embeddings Res(M) of each motif in G_d are tables of vertex-id
