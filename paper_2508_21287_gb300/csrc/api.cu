@@ -1290,14 +1290,17 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
       if (j > 0) cap[j] = std::max<int64_t>(cap[j], (int64_t)TR * ex.st[j].max_group);
       cost += ex.p->steps[j].est_rows;
     }
-    cap[0] = std::max<int64_t>(cap[0], root_chunk);
+    // root chunks: the tuned size, larger for plans whose first table is so long that the
+    // tuned size would cut it into many more items than the GPU has CTAs (per-item overhead)
     int64_t n0 = ex.st[0].seed_table->n;
-    for (int64_t lo = 0; lo < n0; lo += root_chunk) {
+    const int64_t chunk = std::max<int64_t>(root_chunk, (n0 + 4ll * c->num_sms - 1) / (4ll * c->num_sms));
+    cap[0] = std::max<int64_t>(cap[0], chunk);
+    for (int64_t lo = 0; lo < n0; lo += chunk) {
       dmk::BatchItem it{};
       it.plan = i;
       it.lo = lo;
-      it.hi = std::min(n0, lo + root_chunk);
-      items.push_back({cost / std::max<double>(1.0, (double)(n0 + root_chunk - 1) / root_chunk), it});
+      it.hi = std::min(n0, lo + chunk);
+      items.push_back({cost / std::max<double>(1.0, (double)(n0 + chunk - 1) / chunk), it});
       items_per[i]++;
     }
   }
