@@ -316,8 +316,35 @@ __device__ __forceinline__ int32_t join_value(const JoinArgs &a, const int32_t *
   return col < a.w ? rrow[col] : __ldg(trow + a.new_mpos[col - a.w]);
 }
 
-// Join, filter and score one candidate (R row r of the tile, motif row m) whose new vertices
-// nv were loaded beforehand.
+// New vertex i of a candidate: preloaded in registers for steps with few new vertices; read
+// from the motif row when needed (and only while the candidate survives) for the wide variant,
+// whose candidates mostly fail after a few of their many new vertices.
+template <int MAXNEW>
+__device__ __forceinline__ int32_t new_vertex(const JoinArgs &a, const int32_t *trow, const int32_t (&nv)[MAXNEW],
+                                              int i) {
+  return MAXNEW > 4 ? __ldg(trow + a.new_mpos[i]) : nv[i];
+}
+
+template <int MAXNEW>
+__device__ __forceinline__ bool induced_ok_lazy(const JoinArgs &a, const int32_t *rrow, const int32_t *trow) {
+  bool ok = true;
+  for (int i = 0; i < a.n_new && ok; i++) {
+    const int32_t vi = __ldg(trow + a.new_mpos[i]);
+    for (int h = 0; h < 2 && ok; h++) {
+      unsigned long long mk = a.nonadj[i][h];
+      while (mk && ok) {
+        const int c = 64 * h + __ffsll((long long)mk) - 1;
+        mk &= mk - 1;
+        const int32_t v = c < a.w ? rrow[c] : __ldg(trow + a.new_mpos[c - a.w]);
+        ok = !adjacent(a, vi, v);
+      }
+    }
+  }
+  return ok;
+}
+
+// Join, filter and score one candidate (R row r of the tile, motif row m); for MAXNEW <= 4 its
+// new vertices nv were loaded beforehand.
 template <int MAXNEW>
 __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S, const int32_t *tile, const float *ts,
                                            int ws, bool seed, int r, int m, const int32_t (&nv)[MAXNEW], float &sc) {
@@ -328,9 +355,12 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
   if (ok && !seed) {  // FilterOverlappingNodes: new vertices must not repeat a mapped one
     if (MAXNEW > 4 && S.bm) {  // many new vertices: one bit test each in the row's id bitmap
       const unsigned long long *b = S.bm + (size_t)r * S.bmw;
-#pragma unroll
-      for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new && ok) ok = !((b[nv[i] >> 6] >> (nv[i] & 63)) & 1ull);
+      for (int i = 0; i < a.n_new && ok; i++) {
+        const int32_t v = new_vertex<MAXNEW>(a, trow, nv, i);
+        ok = !((b[v >> 6] >> (v & 63)) & 1ull);
+      }
+    } else if (MAXNEW > 4) {
+      for (int i = 0; i < a.n_new && ok; i++) ok = !row_has(rrow, a.w, new_vertex<MAXNEW>(a, trow, nv, i));
     } else {
 #pragma unroll
       for (int i = 0; i < MAXNEW; i++)
@@ -338,13 +368,17 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
     }
   }
   sc = 0.f;
-  if (a.scored) {
+  if (a.scored && ok) {
     sc = (!seed && a.Rs) ? ts[r] : 0.f;
     if (a.ix.score) sc += __ldg(a.ix.score + m);
     if (a.qerr) {
+      if (MAXNEW > 4) {
+        for (int i = 0; i < a.n_new; i++) sc += __ldg(a.qerr + new_vertex<MAXNEW>(a, trow, nv, i));
+      } else {
 #pragma unroll
-      for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new) sc += __ldg(a.qerr + nv[i]);
+        for (int i = 0; i < MAXNEW; i++)
+          if (i < a.n_new) sc += __ldg(a.qerr + nv[i]);
+      }
     }
   }
   for (int e = 0; e < a.n_be && ok; e++) {
@@ -353,7 +387,7 @@ __device__ __forceinline__ bool join_check(const JoinArgs &a, const JoinSmem &S,
     ok = adjacent(a, va, vb);
     if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
   }
-  if (ok && a.induced) ok = induced_ok<MAXNEW>(a, rrow, nv);
+  if (ok && a.induced) ok = MAXNEW > 4 ? induced_ok_lazy<MAXNEW>(a, rrow, trow) : induced_ok<MAXNEW>(a, rrow, nv);
   if (sc > a.prune) ok = false;
   return ok;
 }
@@ -468,9 +502,11 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
       myr[k] = r;
       mym[k] = m;
       const int32_t *trow = mrows + (int64_t)m * mw;  // row 0 for idle lanes: a valid address
+      if (MAXNEW <= 4) {  // the wide variant reads its new vertices lazily (join_check)
 #pragma unroll
-      for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new) nv[k][i] = __ldg(trow + a.new_mpos[i]);
+        for (int i = 0; i < MAXNEW; i++)
+          if (i < a.n_new) nv[k][i] = __ldg(trow + a.new_mpos[i]);
+      }
     }
     unsigned pass = 0;
 #pragma unroll
@@ -484,9 +520,14 @@ __device__ __forceinline__ void join_tile(const JoinArgs &a, const JoinSmem &S, 
           mys[k] = sc;
           if (MODE == 1) {
             unsigned long long p = seed ? 0ull : S.part[myr[k]];
+            const int32_t *trow = mrows + (int64_t)mym[k] * mw;
+            if (MAXNEW > 4) {
+              for (int i = 0; i < a.n_new; i++) p += col_term(S.npos[i], __ldg(trow + a.new_mpos[i]));
+            } else {
 #pragma unroll
-            for (int i = 0; i < MAXNEW; i++)
-              if (i < a.n_new) p += col_term(S.npos[i], nv[k][i]);
+              for (int i = 0; i < MAXNEW; i++)
+                if (i < a.n_new) p += col_term(S.npos[i], nv[k][i]);
+            }
             acc_sum += dmix64(p + (unsigned long long)(uint32_t)wo);
             acc_rows++;
           }
