@@ -490,10 +490,17 @@ def run_c4(args):
     bh, _, _ = batched(heur_plans)
     bh["plan_ms_total"] = heur_plan_ms
     model = train_model(B, ctx, gid, g)
-    learned_plans, learned_plan_ms = make(B.DM_ORDER_LEARNED)
+    single_plans, learned_plan_ms = make(B.DM_ORDER_LEARNED)
+    for p in single_plans:
+        B.dm_plan_free(p)
+    t0 = time.perf_counter()  # the same plans, planned together (host threads, one model evaluation)
+    learned_plans = B.dm_plan_batch(ctx.h, gid, [(p.n, p.row_ptr, p.col_idx) for p in pats],
+                                    order=B.DM_ORDER_LEARNED)
+    learned_batch_plan_ms = 1e3 * (time.perf_counter() - t0)
     with ClockSampler(local) as clk:
         bl, launches, ms = batched(learned_plans)
     bl["plan_ms_total"] = learned_plan_ms
+    bl["plan_batch_ms_total"] = learned_batch_plan_ms
     assert bl["embeddings_per_step"] == bat["embeddings_per_step"] == bh["embeddings_per_step"] == plain_emb
     line = {"metric": METRIC, "value": bl["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": bl["ms_per_step"], "higher_is_better": True, "scaling": "weak",

@@ -91,6 +91,8 @@ _SIGS = {
     "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_free": (None, [_vp]),
     "dm_plan_predicted_rows": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
+    "dm_plan_batch": (ctypes.c_int, [_vp, _i32, _i32, _i32p, ctypes.POINTER(_i32p), ctypes.POINTER(_i32p),
+                                     ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_candidates": (_i32, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp), _i32]),
     "dm_plan_describe": (_i32, [_vp, _i32p, _i32]),
     "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
@@ -232,6 +234,30 @@ def dm_plan(ctx, graph: int, n_p: int, row_ptr, col_idx, motifs=None, order: int
     _check(_lib.dm_plan(ctx, int(graph), int(n_p), _p32(rp), _p32(ci), ctypes.byref(opts), ctypes.byref(h)),
            "dm_plan", ctx)
     return h
+
+
+def dm_plan_batch(ctx, graph: int, patterns, motifs=None, order: int = DM_ORDER_PAPER,
+                  join_algo: int = DM_JOIN_AUTO, chunk_rows: int = 0, max_rows: int = 0,
+                  induced: bool = False) -> list:
+    """dm_plan for a list of (n_p, row_ptr, col_idx) patterns with shared options."""
+    n = len(patterns)
+    arrs = [(_arr_i32(rp), _arr_i32(ci)) for _, rp, ci in patterns]
+    n_p = _arr_i32([int(p[0]) for p in patterns] or [0])
+    rps = (_i32p * max(1, n))(*[_p32(a[0]) for a in arrs])
+    cis = (_i32p * max(1, n))(*[_p32(a[1]) for a in arrs])
+    opts = dm_plan_opts()
+    keep = None
+    if motifs:
+        keep = _arr_i32(list(motifs))
+        opts.motifs = _p32(keep)
+        opts.n_motifs = len(keep)
+    opts.order, opts.join_algo = int(order), int(join_algo)
+    opts.chunk_rows, opts.max_rows = int(chunk_rows), int(max_rows)
+    opts.induced = int(bool(induced))
+    out = (_vp * max(1, n))()
+    _check(_lib.dm_plan_batch(ctx, int(graph), n, _p32(n_p), rps, cis, ctypes.byref(opts), out),
+           "dm_plan_batch", ctx)
+    return [_vp(out[i]) for i in range(n)]
 
 
 def dm_plan_free(plan) -> None:

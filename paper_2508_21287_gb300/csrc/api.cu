@@ -12,6 +12,8 @@
 #include <memory>
 #include <string>
 #include <tuple>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "../../include/dm.h"
@@ -1576,9 +1578,12 @@ struct CandidatePlan {
   int32_t col_vertex[MAXW] = {};
 };
 
-int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, GraphStats &gs,
-                    std::vector<CandidatePlan> *out) {
-  std::vector<std::vector<int32_t>> sets{p.motifs};
+// The candidate motif sets of a pattern; builds their motif tables (device work, calling
+// thread) and adds them to the graph statistics.
+int candidate_sets(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, GraphStats &gs,
+                   std::vector<std::vector<int32_t>> *out) {
+  std::vector<std::vector<int32_t>> &sets = *out;
+  sets.assign(1, p.motifs);
   std::vector<int32_t> extra;
   if (!user_motifs) {
     if (g->max_deg <= 3) extra = {8, DM_MOTIF_CYCLE(12), DM_MOTIF_M4_1};
@@ -1607,6 +1612,12 @@ int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, Gra
       sets.push_back(set);
     }
   }
+  return DM_OK;
+}
+
+// Every (motif set, order) decomposition of a pattern; host work only.
+void decompose_candidates(const Plan &p, const std::vector<std::vector<int32_t>> &sets, const GraphStats &gs,
+                          std::vector<CandidatePlan> *out) {
   out->clear();
   for (auto &set : sets)
     for (int ord : {DM_ORDER_PAPER, DM_ORDER_HEURISTIC}) {
@@ -1616,6 +1627,13 @@ int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, Gra
       if (decompose(p, set, ord, gs, &cp.steps, cp.col_vertex) != DM_OK) continue;
       out->push_back(std::move(cp));
     }
+}
+
+int candidate_plans(dm_ctx *c, DevGraph *g, const Plan &p, bool user_motifs, GraphStats &gs,
+                    std::vector<CandidatePlan> *out) {
+  std::vector<std::vector<int32_t>> sets;
+  RET(candidate_sets(c, g, p, user_motifs, gs, &sets));
+  decompose_candidates(p, sets, gs, out);
   return DM_OK;
 }
 
@@ -1942,6 +1960,81 @@ int dm_plan(dm_ctx *c, dm_graph gh, int32_t n_p, const int32_t *p_row_ptr, const
   }
   RET(plan_finish(c, g, p));
   *out = pl.release();
+  return DM_OK;
+}
+
+int dm_plan_batch(dm_ctx *c, dm_graph gh, int32_t n_patterns, const int32_t *n_p, const int32_t *const *p_row_ptr,
+                  const int32_t *const *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out) {
+  if (!c || !out || n_patterns < 0 || (n_patterns > 0 && (!n_p || !p_row_ptr || !p_col_idx))) return DM_E_INVAL;
+  for (int32_t i = 0; i < n_patterns; i++) out[i] = nullptr;
+  const int order = opts ? opts->order : DM_ORDER_PAPER;
+  const bool learned = order == DM_ORDER_LEARNED && c->m_trained;
+  const bool user_motifs = opts && opts->motifs && opts->n_motifs > 0;
+  std::vector<std::unique_ptr<dm_plan_t>> pl(n_patterns);
+  std::vector<GraphStats> gs(n_patterns);
+  std::vector<std::vector<std::vector<int32_t>>> sets(n_patterns);
+  DevGraph *g = nullptr;
+  // the calling thread: checks, motif tables (device work)
+  for (int32_t i = 0; i < n_patterns; i++) {
+    pl[i].reset(new dm_plan_t());
+    RET(plan_setup(c, gh, n_p[i], p_row_ptr[i], p_col_idx[i], opts, pl[i]->p, &g, gs[i]));
+    if (learned) RET(candidate_sets(c, g, pl[i]->p, user_motifs, gs[i], &sets[i]));
+  }
+  // host threads: the decompositions
+  std::vector<std::vector<CandidatePlan>> cands(n_patterns);
+  std::vector<int> rc(n_patterns, DM_OK);
+  std::atomic<int32_t> next{0};
+  auto work = [&]() {
+    for (int32_t i; (i = next.fetch_add(1)) < n_patterns;) {
+      Plan &p = pl[i]->p;
+      if (learned) {
+        decompose_candidates(p, sets[i], gs[i], &cands[i]);
+        if (cands[i].empty()) rc[i] = DM_E_INVAL;
+      } else {
+        rc[i] = decompose(p, p.motifs, p.order == DM_ORDER_LEARNED ? DM_ORDER_HEURISTIC : p.order, gs[i], &p.steps,
+                          p.col_vertex);
+      }
+    }
+  };
+  const int nt = (int)std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt && t < n_patterns; t++) th.emplace_back(work);
+  work();
+  for (auto &t : th) t.join();
+  for (int32_t i = 0; i < n_patterns; i++) RET(rc[i]);
+  // costs: one model evaluation for every candidate of every pattern, or the heuristic chain
+  if (learned) {
+    std::vector<const std::vector<StepSpec> *> steps;
+    for (auto &cv : cands)
+      for (auto &cp : cv) steps.push_back(&cp.steps);
+    std::vector<double> cost, maxr;
+    std::vector<std::vector<float>> growths;
+    RET(plan_costs(c, steps, &cost, &maxr, &growths));
+    size_t k = 0;
+    for (int32_t i = 0; i < n_patterns; i++) {
+      Plan &p = pl[i]->p;
+      double best = 1e308;
+      for (auto &cp : cands[i]) {
+        if (cost[k] < best) {
+          best = cost[k];
+          p.steps = cp.steps;
+          memcpy(p.col_vertex, cp.col_vertex, sizeof(cp.col_vertex));
+          p.pred_cost = cost[k];
+          p.pred_max_rows = maxr[k];
+          p.pred_growth = growths[k];
+          p.motifs = cp.motifs;
+        }
+        k++;
+      }
+    }
+  } else {
+    for (int32_t i = 0; i < n_patterns; i++) {
+      Plan &p = pl[i]->p;
+      RET(plan_cost(c, p.steps, false, &p.pred_cost, &p.pred_max_rows, &p.pred_growth));
+    }
+  }
+  for (int32_t i = 0; i < n_patterns; i++) RET(plan_finish(c, g, pl[i]->p));
+  for (int32_t i = 0; i < n_patterns; i++) out[i] = pl[i].release();
   return DM_OK;
 }
 

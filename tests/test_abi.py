@@ -117,3 +117,11 @@ def test_decompose_rejects_bad_input(B):
         p = I.path(3)
         B.dm_decompose(3, p.row_ptr, p.col_idx, [999])
     assert e.value.code == B.DM_E_NOTFOUND
+
+
+def test_plan_batch_checks_arguments_without_a_device(B):
+    from paper_2508_21287_gb300 import inputs as I
+    p = I.path(3)
+    with pytest.raises(B.DMError) as e:
+        B.dm_plan_batch(None, 0, [(p.n, p.row_ptr, p.col_idx)])
+    assert e.value.code == B.DM_E_INVAL

@@ -88,6 +88,22 @@ def test_training_beats_the_heuristic(B):
             got = _log_steps(B, ctx, gid, [c], B.DM_ORDER_LEARNED)[0]
             ref = oracle.enumerate(g, c, rows=False, threads=8)
             assert got == (ref.count, ref.checksum)
+        # batched planning (host threads, one model evaluation) gives dm_plan's plans, pattern
+        # by pattern, for the learned and the fixed orders
+        pats = held[:60] + [I.cycle(36)]
+        for order in (B.DM_ORDER_LEARNED, B.DM_ORDER_HEURISTIC, B.DM_ORDER_PAPER):
+            batch = B.dm_plan_batch(ctx.h, gid, [(q.n, q.row_ptr, q.col_idx) for q in pats], order=order)
+            for q, pb in zip(pats, batch):
+                ps = B.dm_plan(ctx.h, gid, q.n, q.row_ptr, q.col_idx, order=order)
+                assert B.dm_plan_describe(pb) == B.dm_plan_describe(ps)
+                assert np.array_equal(B.dm_plan_predicted_rows(pb), B.dm_plan_predicted_rows(ps))
+                B.dm_plan_free(ps)
+            for q, pb in list(zip(pats, batch))[:5]:
+                ref = oracle.enumerate(g, q, rows=False, threads=8)
+                assert B.dm_match(ctx.h, pb, B.DM_COUNT) == (ref.count, ref.checksum)
+            for pb in batch:
+                B.dm_plan_free(pb)
+        assert B.dm_plan_batch(ctx.h, gid, []) == []
         # a learned plan keeps the model's per-step predictions it was chosen by; a paper plan
         # keeps the independence heuristic's
         p = held[3]
