@@ -59,6 +59,9 @@ def parse_args():
                     help="c3: data graph family (heavy-hex m x n, square grid 60x60, random 3-regular V=4096)")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
     ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
+    ap.add_argument("--contexts", type=int, default=0,
+                    help="c2/c3: library contexts (each its own stream and host thread) the queries of a step "
+                         "are spread over; 0 = 8 for c2, 1 for c3")
     return ap.parse_args()
 
 
@@ -239,19 +242,55 @@ def run_ours(args):
     hh = tuple(int(x) for x in args.hh.split(","))
     g, pats = workload(rank, args.batch, args.workload, hh, args.only_path, args.graph)
     count_mode = args.workload == "c3"
-    ctx = B.Context(local)
+    n_ctx = args.contexts or (1 if count_mode else 8)
+    # independent queries: each context (own CUDA stream, arena and graph copy) is driven by its
+    # own host thread, so one query's dependent launches overlap with the others'
+    ctxs = [B.Context(local) for _ in range(n_ctx)]
+    streams = [torch.cuda.Stream() for _ in range(n_ctx)]
+    gids = []
+    for c, st_ in zip(ctxs, streams):
+        B.dm_set_stream(c.h, st_)
+        gids.append(c.load(g))
+        B.dm_enable_timing(c.h, True)
     stream = torch.cuda.Stream()
-    B.dm_set_stream(ctx.h, stream)
-    gid = ctx.load(g)
-    B.dm_enable_timing(ctx.h, True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    import concurrent.futures as cf
+    pool = cf.ThreadPoolExecutor(n_ctx)
+    lock = threading.Lock()
 
     acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0, "chunks": 0,
            "max_rows": 0}
 
-    def step(host_rows: bool, record: bool):
+    qpats = [(p.n, p.row_ptr, p.col_idx) for p in pats]
+
+    def step(host_rows: bool, rec, use=None):
+        use = list(range(n_ctx)) if use is None else use
+        if count_mode:
+            if len(use) == 1:
+                return step_ctx(use[0], pats, host_rows, rec)
+            return sum(pool.map(lambda t: step_ctx(t, pats[t::n_ctx], host_rows, rec), use))
+        # layout queries: the library's multi-context runner (one native thread per context)
+        hb = [0]
+
+        def host_cb(i, r, s_):
+            with lock:
+                hb[0] += r.nbytes + (0 if s_ is None else s_.nbytes)
+            return 0
+        res, st = B.dm_match_topk_queries([ctxs[t].h for t in use], [gids[t] for t in use], qpats, K_TOP,
+                                          mode=B.DM_ALL if host_rows else B.DM_ALL | B.DM_DEVICE_ROWS,
+                                          cb=host_cb if host_rows else None)
+        if rec is not None:
+            rec["d2h"] += hb[0]
+            for key in ("join_ms", "join_bytes", "join_launches", "chunks"):
+                rec[key] += st[key]
+            rec["launches"] += st["kernel_launches"]
+            rec["max_rows"] = max(rec["max_rows"], st["max_rows"])
+        return sum(x[2] for x in res)
+
+    def step_ctx(t: int, queries, host_rows: bool, rec):
+        ctx, gid = ctxs[t], gids[t]
         emb = 0
-        for p in pats:
+        for p in queries:
             plan = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
             if count_mode:
                 cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
@@ -259,21 +298,35 @@ def run_ours(args):
                 sink = []
                 _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL, lambda r, s: sink.append((r, s)) and 0,
                                                K_TOP, p.n)
-                if record:
-                    acc["d2h"] += sum(r.nbytes + (0 if s is None else s.nbytes) for r, s in sink)
+                if rec is not None:
+                    with lock:
+                        rec["d2h"] += sum(r.nbytes + (0 if s is None else s.nbytes) for r, s in sink)
             else:
                 _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL | B.DM_DEVICE_ROWS, lambda *a: 0, K_TOP, p.n)
             st = B.dm_get_stats(ctx.h)
             B.dm_plan_free(plan)
-            if record:
-                acc["join_ms"] += st["join_ms"]
-                acc["join_bytes"] += st["join_bytes"]
-                acc["join_launches"] += st["join_launches"]
-                acc["launches"] += st["kernel_launches"]
-                acc["chunks"] += st["chunks"]
-                acc["max_rows"] = max(acc["max_rows"], st["max_rows"])
+            if rec is not None:
+                with lock:
+                    rec["join_ms"] += st["join_ms"]
+                    rec["join_bytes"] += st["join_bytes"]
+                    rec["join_launches"] += st["join_launches"]
+                    rec["launches"] += st["kernel_launches"]
+                    rec["chunks"] += st["chunks"]
+                    rec["max_rows"] = max(rec["max_rows"], st["max_rows"])
             emb += cnt
         return emb
+
+    def fork():  # the contexts' streams start after everything queued on the timing stream
+        e = torch.cuda.Event()
+        e.record(stream)
+        for st_ in streams:
+            st_.wait_event(e)
+
+    def join():  # and the timing stream waits for all of them
+        for st_ in streams:
+            e = torch.cuda.Event()
+            e.record(st_)
+            stream.wait_event(e)
 
     def barrier():
         if world > 1:
@@ -282,7 +335,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step(False, False)
+        step(False, None)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     with ClockSampler(local) as clk:
@@ -290,7 +343,9 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
             ev[i][0].record(stream)
-            acc["emb"] += step(False, True)
+            fork()
+            acc["emb"] += step(False, acc)
+            join()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -309,15 +364,15 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e and not count_mode:
         h2d = sum(p.row_ptr.nbytes + p.col_idx.nbytes for p in pats)
-        acc2 = acc["d2h"]
+        eacc = {k: 0 for k in acc}
         barrier()
         t0 = time.perf_counter()
         emb2 = 0
         for _ in range(args.steps):
-            emb2 += step(True, True)
+            emb2 += step(True, eacc)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        d2h = (acc["d2h"] - acc2) // max(1, args.steps)
+        d2h = eacc["d2h"] // max(1, args.steps)
         e2e = {"value": emb2 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     peaks = {}
@@ -327,13 +382,23 @@ def run_ours(args):
     except OSError:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = acc["join_bytes"] / (acc["join_ms"] / 1e3) / 1e9 if acc["join_ms"] > 0 else 0.0
+    racc = acc
+    if n_ctx > 1:  # a launch's own duration is defined with one query on the device at a time:
+        racc = {k: 0 for k in acc}  # time the kernels in a separate pass, one context, queries in order
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            step(False, racc, use=[0])
+        torch.cuda.synchronize()
+    achieved = racc["join_bytes"] / (racc["join_ms"] / 1e3) / 1e9 if racc["join_ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "k_joinw", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "traffic": JOIN_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload) if not args.only_path else None,
-                "algorithmic_bytes_per_launch": acc["join_bytes"] / max(1, acc["join_launches"]),
-                "avg_launch_us": 1e3 * acc["join_ms"] / max(1, acc["join_launches"]),
-                "launches": acc["join_launches"]}
+                "algorithmic_bytes_per_launch": racc["join_bytes"] / max(1, racc["join_launches"]),
+                "avg_launch_us": 1e3 * racc["join_ms"] / max(1, racc["join_launches"]),
+                "launches": racc["join_launches"],
+                "timed": "in the timed steps" if n_ctx == 1 else "separate pass, one context, queries in sequence"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -344,12 +409,14 @@ def run_ours(args):
                                           args.graph, "heavy-hex " + args.hh.replace(",", "x"))),
                        "motifs": "M4-O,M6-O,M2" if count_mode and args.graph == "grid" else "M4,M2",
                        "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}",
+                       "parallelism": f"replicas x{world}", "contexts": n_ctx,
                        "join_chunks_per_step": acc["chunks"] / args.steps, "largest_table_rows": acc["max_rows"]},
             "e2e": e2e, "gpu_launches": acc["launches"], "clocks": clocks, "roofline": roofline}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(g, pats, count_only=count_mode)
-    ctx.close()
+    pool.shutdown()
+    for c in ctxs:
+        c.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -394,6 +394,30 @@ typedef struct dm_stats {
 int dm_get_stats(dm_ctx *ctx, dm_stats *out);
 int dm_enable_timing(dm_ctx *ctx, int on);
 
+/* Many independent layout queries at once (no counterpart in the paper: a host-side runner
+ * for callers with a batch of queries, each too small to fill the GPU alone). Query i
+ * (0 <= i < n_q) is the pattern (n_p[i], p_row_ptr[i], p_col_idx[i]); it is planned with opts
+ * (nullable) and answered exactly as dm_plan + dm_match_topk(mode, k) would answer it alone.
+ * Context ctxs[t] (0 <= t < n_ctx, distinct contexts on one device, each with the same data
+ * graph loaded as gids[t]) is driven by its own host thread; the threads take queries in
+ * index order, so queries on different contexts overlap on the GPU. Outputs per query:
+ * out_rows[i] (k x n_p[i] int32 host buffer, required), out_scores[i] (k floats; out_scores
+ * or an entry may be NULL), out_n[i], and, where the arrays are not NULL, out_counts[i],
+ * out_checksums[i] and out_status[i] (DM_OK or the query's error). cb, if not NULL, receives
+ * every query's rows as dm_match_topk's callback would, plus the query index; it is called
+ * from the worker threads and must be thread-safe. out_stats (nullable): the dm_stats fields
+ * chunks, join_ms, join_launches, join_bytes and kernel_launches summed over the queries,
+ * max_rows their maximum, total_ms the wall time of the call (n_steps 0). Returns DM_OK, or
+ * the status of the lowest-numbered failing query (the others still run). */
+typedef int (*dm_query_cb)(void *user, int32_t query, const int32_t *rows, const float *scores,
+                           int64_t nrows, int32_t n_cols);
+int dm_match_topk_queries(dm_ctx *const *ctxs, const dm_graph *gids, int32_t n_ctx, int32_t n_q,
+                          const int32_t *n_p, const int32_t *const *p_row_ptr,
+                          const int32_t *const *p_col_idx, const dm_plan_opts *opts, int mode,
+                          dm_query_cb cb, void *user, int32_t k, int32_t *const *out_rows,
+                          float *const *out_scores, int32_t *out_n, uint64_t *out_counts,
+                          uint64_t *out_checksums, int32_t *out_status, dm_stats *out_stats);
+
 const char *dm_strerror(int code);
 
 /* Text of the last CUDA failure seen by the context (empty if none); owned by the context. */

@@ -69,6 +69,8 @@ class dm_server_stats(ctypes.Structure):
 
 DM_CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int32)
+DM_QUERY_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int32)
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -91,6 +93,10 @@ _SIGS = {
     "dm_plan": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_free": (None, [_vp]),
     "dm_plan_predicted_rows": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
+    "dm_match_topk_queries": (ctypes.c_int, [ctypes.POINTER(_vp), _i32p, _i32, _i32, _i32p, ctypes.POINTER(_i32p),
+                                             ctypes.POINTER(_i32p), ctypes.POINTER(dm_plan_opts), ctypes.c_int,
+                                             DM_QUERY_CB, _vp, _i32, ctypes.POINTER(_i32p), ctypes.POINTER(_fp),
+                                             _i32p, _u64p, _u64p, _i32p, ctypes.POINTER(dm_stats)]),
     "dm_plan_batch": (ctypes.c_int, [_vp, _i32, _i32, _i32p, ctypes.POINTER(_i32p), ctypes.POINTER(_i32p),
                                      ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp)]),
     "dm_plan_candidates": (_i32, [_vp, _i32, _i32, _i32p, _i32p, ctypes.POINTER(dm_plan_opts), ctypes.POINTER(_vp), _i32]),
@@ -347,6 +353,63 @@ def dm_match_topk(ctx, plan, mode: int, cb, k: int, n_p: int):
         raise err[0]
     _check(rc, "dm_match_topk", ctx)
     return rows[:n.value], scores[:n.value], cnt.value, cs.value
+
+
+def dm_match_topk_queries(ctxs, gids, patterns, k: int, mode: int = DM_ALL, cb=None, motifs=None,
+                          order: int = DM_ORDER_PAPER):
+    """Many (n_p, row_ptr, col_idx) queries over several contexts at once, one host thread per
+    context. cb(query, rows, scores) receives host copies, or cb(query, rows_ptr, scores_ptr, m,
+    n) device pointers with DM_DEVICE_ROWS, from the worker threads. Returns a list of
+    (rows, scores, count, checksum, status) per query and the summed statistics."""
+    n = len(patterns)
+    ctx_arr = (_vp * len(ctxs))(*[c.value if isinstance(c, _vp) else c for c in ctxs])
+    gid_arr = _arr_i32(list(gids))
+    arrs = [(_arr_i32(rp), _arr_i32(ci)) for _, rp, ci in patterns]
+    n_p = _arr_i32([int(p[0]) for p in patterns] or [0])
+    rps = (_i32p * max(1, n))(*[_p32(a[0]) for a in arrs])
+    cis = (_i32p * max(1, n))(*[_p32(a[1]) for a in arrs])
+    rows = [np.zeros((k, int(p[0])), dtype=np.int32) for p in patterns]
+    scores = [np.zeros(k, dtype=np.float32) for _ in patterns]
+    rows_p = (_i32p * max(1, n))(*[_p32(r) for r in rows])
+    scores_p = (_fp * max(1, n))(*[x.ctypes.data_as(_fp) for x in scores])
+    out_n = np.zeros(max(1, n), dtype=np.int32)
+    counts = np.zeros(max(1, n), dtype=np.uint64)
+    sums = np.zeros(max(1, n), dtype=np.uint64)
+    status = np.zeros(max(1, n), dtype=np.int32)
+    opts = dm_plan_opts()
+    keep = None
+    if motifs:
+        keep = _arr_i32(list(motifs))
+        opts.motifs = _p32(keep)
+        opts.n_motifs = len(keep)
+    opts.order = int(order)
+    err = []
+
+    def _tramp(user, q, r, sc, nrows, ncols):
+        try:
+            if mode & DM_DEVICE_ROWS:
+                res = cb(q, ctypes.cast(r, ctypes.c_void_p).value, ctypes.cast(sc, ctypes.c_void_p).value, nrows, ncols)
+            else:
+                a = np.ctypeslib.as_array(r, shape=(nrows * ncols,)).reshape(nrows, ncols).copy()
+                s_ = np.ctypeslib.as_array(sc, shape=(nrows,)).copy() if sc else None
+                res = cb(q, a, s_)
+            return int(bool(res))
+        except BaseException as e:  # noqa: BLE001 - re-raised after the C call returns
+            err.append(e)
+            return 1
+    c_cb = DM_QUERY_CB(_tramp) if cb is not None else DM_QUERY_CB()
+    st = dm_stats()
+    rc = _lib.dm_match_topk_queries(ctx_arr, _p32(gid_arr), len(ctxs), n, _p32(n_p), rps, cis, ctypes.byref(opts),
+                                    int(mode), c_cb, None, int(k), rows_p, scores_p, _p32(out_n),
+                                    counts.ctypes.data_as(_u64p), sums.ctypes.data_as(_u64p), _p32(status),
+                                    ctypes.byref(st))
+    if err:
+        raise err[0]
+    _check(rc, "dm_match_topk_queries")
+    res = [(rows[i][:out_n[i]], scores[i][:out_n[i]], int(counts[i]), int(sums[i]), int(status[i])) for i in range(n)]
+    stats = {"chunks": st.chunks, "max_rows": st.max_rows, "join_ms": st.join_ms, "join_launches": st.join_launches,
+             "join_bytes": st.join_bytes, "total_ms": st.total_ms, "kernel_launches": st.kernel_launches}
+    return res, stats
 
 
 def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):

@@ -332,10 +332,10 @@ static void set_wjoin_attrs() {
   done.fetch_or(bit);
 }
 
-int wjoin_grid(const JoinArgs &a, int num_sms) {
+int wjoin_grid(const JoinArgs &a, int num_sms, int64_t row_hint) {
   set_wjoin_attrs();
   WJoinKernel k = pick_wjoin(a);
-  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? INT64_MAX / 2 : a.N);
+  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? (row_hint > 0 ? row_hint : INT64_MAX / 2) : a.N);
   int64_t blocks_needed = (rows + (int64_t)WT * WJ_WARPS - 1) / ((int64_t)WT * WJ_WARPS);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WJ_BLK, wjoin_smem(a));

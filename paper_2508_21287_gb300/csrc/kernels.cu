@@ -16,8 +16,8 @@ using namespace dmi;
 
 namespace dmk {
 
-std::atomic<int64_t> g_launches{0};
-int64_t launch_count() { return g_launches.load(); }
+thread_local int64_t g_launches = 0;
+int64_t launch_count() { return g_launches; }
 
 // ------------------------------------------------------------------ graph prep ---------
 __device__ __forceinline__ int32_t slot_source(const int32_t *row_ptr, int32_t V, int64_t e) {

@@ -30,9 +30,11 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-// Number of kernels launched by this library in the process so far.
+// Number of kernels this library has launched from the calling thread so far (a context's
+// calls run on the calling thread, so per-call differences stay exact when several threads
+// drive their own contexts at once).
 int64_t launch_count();
-extern std::atomic<int64_t> g_launches;
+extern thread_local int64_t g_launches;
 
 // Fused join step of Alg. 1 (InnerJoin + FilterOverlappingNodes + back-edge filter + score
 // + compaction, or count + checksum in the last step), warp-centric (join_warp.cu). The grid
@@ -40,7 +42,10 @@ extern std::atomic<int64_t> g_launches;
 // pdl: launched with programmatic dependent launch (the previous stream operation must be a
 // kernel of the same chain).
 cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s, bool pdl = false);
-int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
+// row_hint: for a launch that reads its input row count on the device (n_dev), an estimate of
+// that count to size the grid by (0 = one full wave). The kernel loops over its tiles, so any
+// hint gives the same result; a low one only runs slower.
+int wjoin_grid(const dmi::JoinArgs &a, int num_sms, int64_t row_hint = 0);
 
 // Data-graph preparation.
 cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, const float *eerr,

@@ -125,3 +125,16 @@ def test_plan_batch_checks_arguments_without_a_device(B):
     with pytest.raises(B.DMError) as e:
         B.dm_plan_batch(None, 0, [(p.n, p.row_ptr, p.col_idx)])
     assert e.value.code == B.DM_E_INVAL
+
+
+def test_query_runner_checks_arguments_without_a_device(B):
+    import ctypes
+    from paper_2508_21287_gb300 import inputs as I
+    p = I.path(3)
+    fake = ctypes.c_void_p(0x1000)
+    with pytest.raises(B.DMError) as e:  # one context given twice: refused before any use
+        B.dm_match_topk_queries([fake, fake], [0, 0], [(p.n, p.row_ptr, p.col_idx)], 5)
+    assert e.value.code == B.DM_E_INVAL
+    with pytest.raises(B.DMError) as e:
+        B.dm_match_topk_queries([], [], [(p.n, p.row_ptr, p.col_idx)], 5)
+    assert e.value.code == B.DM_E_INVAL

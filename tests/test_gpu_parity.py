@@ -185,6 +185,51 @@ def test_match_topk_device_rows_and_streamed(ctx, hh, B, chunk_rows):
         assert rows_k.shape == (min(100, ref.count), p.n)
 
 
+def test_many_queries_over_several_contexts(ctx, hh, B):
+    # the multi-context runner answers each query exactly as one dm_match_topk call alone;
+    # host rows (with the query index) and device rows both reach the callback
+    g, gid = hh
+    qs = [I.layout_query(g, s) for s in range(12)]
+    pats = [(q.n, q.row_ptr, q.col_idx) for q in qs]
+    ctxs = [B.Context(0) for _ in range(3)]
+    try:
+        gids = [c.load(g) for c in ctxs]
+        got = {}
+        res, st = B.dm_match_topk_queries([c.h for c in ctxs], gids, pats, 100,
+                                          cb=lambda i, r, s: got.setdefault(i, []).append((r, s)) and 0)
+        launches = 0
+        for i, (q, (rows_k, sc_k, cnt, cs, status)) in enumerate(zip(qs, res)):
+            assert status == B.DM_OK
+            plan = ctx.plan(gid, q)
+            one = []
+            r1, s1, c1, cs1 = B.dm_match_topk(ctx.h, plan.h, B.DM_ALL, lambda r, s: one.append((r, s)) and 0, 100, q.n)
+            launches += B.dm_get_stats(ctx.h)["kernel_launches"]
+            assert (cnt, cs) == (c1, cs1)
+            assert np.array_equal(rows_k, r1) and np.array_equal(sc_k, s1)
+            rows = np.concatenate([r for r, _ in got[i]])
+            assert np.array_equal(rows, np.concatenate([r for r, _ in one]))
+            assert np.array_equal(np.concatenate([s for _, s in got[i]]), np.concatenate([s for _, s in one]))
+            if i < 4:
+                ref = oracle.enumerate(g, q, rows=False)
+                assert (cnt, cs) == (ref.count, ref.checksum)
+        assert st["kernel_launches"] >= launches > 0 and st["join_launches"] > 0
+        seen = {}
+        res2, _ = B.dm_match_topk_queries([c.h for c in ctxs], gids, pats, 7, mode=B.DM_ALL | B.DM_DEVICE_ROWS,
+                                          cb=lambda i, r, s, m, n: seen.__setitem__(i, seen.get(i, 0) + m) and 0)
+        for i, (rows_k, sc_k, cnt, cs, status) in enumerate(res2):
+            assert status == B.DM_OK and cnt == res[i][2] == seen.get(i, 0) and cs == res[i][3]
+            assert np.array_equal(rows_k, res[i][0][:7])
+        res3, _ = B.dm_match_topk_queries([ctxs[0].h], gids[:1], pats[:3], 5)  # one context, no callback
+        assert [x[2:4] for x in res3] == [x[2:4] for x in res[:3]]
+        res0, st0 = B.dm_match_topk_queries([c.h for c in ctxs], gids, [], 5)
+        assert res0 == [] and st0["kernel_launches"] == 0
+        with pytest.raises(B.DMError):
+            B.dm_match_topk_queries([ctxs[0].h, ctxs[0].h], gids[:2], pats[:2], 5)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 def test_topk_more_than_count_and_no_embeddings(ctx, hh, B):
     g, gid = hh
     check_topk(ctx, gid, g, I.cycle(12), 1000)      # 576 < k
