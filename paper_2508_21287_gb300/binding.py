@@ -355,27 +355,40 @@ def dm_match_topk(ctx, plan, mode: int, cb, k: int, n_p: int):
     return rows[:n.value], scores[:n.value], cnt.value, cs.value
 
 
+class QueryBatch:
+    """Queries marshalled once for dm_match_topk_queries, with their output buffers: a caller
+    that answers the same queries repeatedly passes this instead of the pattern list."""
+
+    def __init__(self, patterns, k: int):
+        self.k = int(k)
+        self.n = n = len(patterns)
+        self._arrs = [(_arr_i32(rp), _arr_i32(ci)) for _, rp, ci in patterns]
+        self.n_p = _arr_i32([int(p[0]) for p in patterns] or [0])
+        self.rps = (_i32p * max(1, n))(*[_p32(a[0]) for a in self._arrs])
+        self.cis = (_i32p * max(1, n))(*[_p32(a[1]) for a in self._arrs])
+        self.rows = [np.zeros((self.k, int(p[0])), dtype=np.int32) for p in patterns]
+        self.scores = [np.zeros(self.k, dtype=np.float32) for _ in patterns]
+        self.rows_p = (_i32p * max(1, n))(*[_p32(r) for r in self.rows])
+        self.scores_p = (_fp * max(1, n))(*[x.ctypes.data_as(_fp) for x in self.scores])
+        self.out_n = np.zeros(max(1, n), dtype=np.int32)
+        self.counts = np.zeros(max(1, n), dtype=np.uint64)
+        self.sums = np.zeros(max(1, n), dtype=np.uint64)
+        self.status = np.zeros(max(1, n), dtype=np.int32)
+
+
 def dm_match_topk_queries(ctxs, gids, patterns, k: int, mode: int = DM_ALL, cb=None, motifs=None,
                           order: int = DM_ORDER_PAPER):
-    """Many (n_p, row_ptr, col_idx) queries over several contexts at once, one host thread per
-    context. cb(query, rows, scores) receives host copies, or cb(query, rows_ptr, scores_ptr, m,
-    n) device pointers with DM_DEVICE_ROWS, from the worker threads. Returns a list of
-    (rows, scores, count, checksum, status) per query and the summed statistics."""
-    n = len(patterns)
+    """Many (n_p, row_ptr, col_idx) queries (or a QueryBatch) over several contexts at once,
+    one host thread per context. cb(query, rows, scores) receives host copies, or cb(query,
+    rows_ptr, scores_ptr, m, n) device pointers with DM_DEVICE_ROWS, from the worker threads.
+    Returns a list of (rows, scores, count, checksum, status) per query (rows and scores are
+    views of the batch's buffers) and the summed statistics."""
+    qb = patterns if isinstance(patterns, QueryBatch) else QueryBatch(patterns, k)
+    if qb.k != int(k):
+        raise ValueError("QueryBatch was made for another k")
+    n = qb.n
     ctx_arr = (_vp * len(ctxs))(*[c.value if isinstance(c, _vp) else c for c in ctxs])
     gid_arr = _arr_i32(list(gids))
-    arrs = [(_arr_i32(rp), _arr_i32(ci)) for _, rp, ci in patterns]
-    n_p = _arr_i32([int(p[0]) for p in patterns] or [0])
-    rps = (_i32p * max(1, n))(*[_p32(a[0]) for a in arrs])
-    cis = (_i32p * max(1, n))(*[_p32(a[1]) for a in arrs])
-    rows = [np.zeros((k, int(p[0])), dtype=np.int32) for p in patterns]
-    scores = [np.zeros(k, dtype=np.float32) for _ in patterns]
-    rows_p = (_i32p * max(1, n))(*[_p32(r) for r in rows])
-    scores_p = (_fp * max(1, n))(*[x.ctypes.data_as(_fp) for x in scores])
-    out_n = np.zeros(max(1, n), dtype=np.int32)
-    counts = np.zeros(max(1, n), dtype=np.uint64)
-    sums = np.zeros(max(1, n), dtype=np.uint64)
-    status = np.zeros(max(1, n), dtype=np.int32)
     opts = dm_plan_opts()
     keep = None
     if motifs:
@@ -399,14 +412,15 @@ def dm_match_topk_queries(ctxs, gids, patterns, k: int, mode: int = DM_ALL, cb=N
             return 1
     c_cb = DM_QUERY_CB(_tramp) if cb is not None else DM_QUERY_CB()
     st = dm_stats()
-    rc = _lib.dm_match_topk_queries(ctx_arr, _p32(gid_arr), len(ctxs), n, _p32(n_p), rps, cis, ctypes.byref(opts),
-                                    int(mode), c_cb, None, int(k), rows_p, scores_p, _p32(out_n),
-                                    counts.ctypes.data_as(_u64p), sums.ctypes.data_as(_u64p), _p32(status),
-                                    ctypes.byref(st))
+    rc = _lib.dm_match_topk_queries(ctx_arr, _p32(gid_arr), len(ctxs), n, _p32(qb.n_p), qb.rps, qb.cis,
+                                    ctypes.byref(opts), int(mode), c_cb, None, int(k), qb.rows_p, qb.scores_p,
+                                    _p32(qb.out_n), qb.counts.ctypes.data_as(_u64p), qb.sums.ctypes.data_as(_u64p),
+                                    _p32(qb.status), ctypes.byref(st))
     if err:
         raise err[0]
     _check(rc, "dm_match_topk_queries")
-    res = [(rows[i][:out_n[i]], scores[i][:out_n[i]], int(counts[i]), int(sums[i]), int(status[i])) for i in range(n)]
+    on, cn, sm, stt = qb.out_n.tolist(), qb.counts.tolist(), qb.sums.tolist(), qb.status.tolist()
+    res = [(qb.rows[i][:on[i]], qb.scores[i][:on[i]], cn[i], sm[i], stt[i]) for i in range(n)]
     stats = {"chunks": st.chunks, "max_rows": st.max_rows, "join_ms": st.join_ms, "join_launches": st.join_launches,
              "join_bytes": st.join_bytes, "total_ms": st.total_ms, "kernel_launches": st.kernel_launches}
     return res, stats

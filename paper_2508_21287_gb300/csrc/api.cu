@@ -302,10 +302,24 @@ int sort_canonical(dm_ctx *c, DevTable &t, int bits, unsigned long long *ctr = n
   }
   void *tmp = nullptr;
   RET(dalloc(c, &tmp, (size_t)dmk::msort_tmp_bytes(t.n)));
-  int32_t *perm = nullptr;
-  CK(dmk::msort_rows(t.rows, t.n, t.w, bits, tmp, &perm, ctr ? ctr + CTR_SUM : nullptr, c->stream));
   DevTable o;
-  RET(gather_table(c, t, perm, t.n, &o));
+  if (t.n <= dmk::msort_into_max_rows()) {  // small tables: rows go straight to their positions
+    o.n = t.n;
+    o.w = t.w;
+    int r = dalloc_t(c, &o.rows, (size_t)t.n * t.w);
+    if (r == DM_OK && t.score) r = dalloc_t(c, &o.score, t.n);
+    if (r != DM_OK) {
+      free_table(c, o);
+      dfree(c, tmp);
+      return r;
+    }
+    CK(dmk::msort_rows_into(t.rows, t.score, t.n, t.w, bits, tmp, o.rows, o.score, ctr ? ctr + CTR_SUM : nullptr,
+                            c->num_sms, c->stream));
+  } else {
+    int32_t *perm = nullptr;
+    CK(dmk::msort_rows(t.rows, t.n, t.w, bits, tmp, &perm, ctr ? ctr + CTR_SUM : nullptr, c->stream));
+    RET(gather_table(c, t, perm, t.n, &o));
+  }
   dfree(c, tmp);
   free_table(c, t);
   t = o;
@@ -763,14 +777,14 @@ struct Exec {
         a.in_cap = prev_cap;
       }
       // The input count of step j > 0 is read on the device. A step the planner expects to be
-      // small gets a grid for 4x its predicted rows (at least a quarter block per SM) instead
+      // small gets a grid for twice its predicted rows (at least a block per eight SMs) instead
       // of a full wave, so that small queries on other streams find free SMs.
       int64_t hint = 0;
       if (j > 0 && (int)p->pred_growth.size() >= j) {
         double lr = 0;
         for (int i = 0; i < j; i++) lr += p->pred_growth[i];
         const double pred = exp(std::min(40.0, std::max(-40.0, lr)));
-        if (pred * 4 < (double)c->num_sms * 1024) hint = (int64_t)(pred * 4) + (int64_t)c->num_sms * 64;
+        if (pred * 2 < (double)c->num_sms * 1024) hint = (int64_t)(pred * 2) + (int64_t)c->num_sms * 32;
       }
       int grid = dmk::wjoin_grid(a, c->num_sms, hint);
       CK(dmk::launch_wjoin(a, grid, c->stream, j > 0));  // steps chain kernel to kernel

@@ -305,15 +305,12 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
 
 typedef void (*WJoinKernel)(JoinArgs);
 
+static int wjoin_variant(const JoinArgs &a) { return (a.mode == 1 ? 0 : 3) + (a.n_new <= 1 ? 0 : a.n_new <= 4 ? 1 : 2); }
+
 static WJoinKernel pick_wjoin(const JoinArgs &a) {
-  if (a.mode == 1) {
-    if (a.n_new <= 1) return k_joinw<1, 1>;
-    if (a.n_new <= 4) return k_joinw<4, 1>;
-    return k_joinw<MAXM, 1>;
-  }
-  if (a.n_new <= 1) return k_joinw<1, 0>;
-  if (a.n_new <= 4) return k_joinw<4, 0>;
-  return k_joinw<MAXM, 0>;
+  static const WJoinKernel ks[6] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>,
+                                    k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
+  return ks[wjoin_variant(a)];
 }
 
 static size_t wjoin_smem(const JoinArgs &a) { return (size_t)WJ_WARPS * warp_smem_bytes(join_row_stride(a.w)); }
@@ -337,9 +334,17 @@ int wjoin_grid(const JoinArgs &a, int num_sms, int64_t row_hint) {
   WJoinKernel k = pick_wjoin(a);
   int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? (row_hint > 0 ? row_hint : INT64_MAX / 2) : a.N);
   int64_t blocks_needed = (rows + (int64_t)WT * WJ_WARPS - 1) / ((int64_t)WT * WJ_WARPS);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WJ_BLK, wjoin_smem(a));
-  if (per_sm < 1) per_sm = 1;
+  // resident blocks per SM for this variant and row stride, asked of the runtime once (the
+  // query costs host time on every launch otherwise); every device of the process is taken to
+  // be of one architecture
+  static std::atomic<int> occ[6][MAXW / 4 + 2];
+  const int slot = join_row_stride(a.w) / 4;
+  int per_sm = occ[wjoin_variant(a)][slot].load(std::memory_order_relaxed);
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WJ_BLK, wjoin_smem(a));
+    if (per_sm < 1) per_sm = 1;
+    occ[wjoin_variant(a)][slot].store(per_sm, std::memory_order_relaxed);
+  }
   int64_t g = (int64_t)num_sms * per_sm;
   if (blocks_needed < g) g = blocks_needed;
   return (int)(g < 1 ? 1 : g);

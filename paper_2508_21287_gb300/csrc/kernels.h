@@ -102,6 +102,13 @@ cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned
 // row indices in ascending lexicographic order; ids are below 2^bits. tmp holds
 // msort_tmp_bytes(n) bytes.
 int64_t msort_tmp_bytes(int64_t n);
+// Tables of at most msort_into_max_rows() rows: the canonical order written straight into
+// out_rows / out_scores (nullable) in three launches (key packing with the optional checksum,
+// tile sort, rank scatter, the last on at most max_blocks blocks); tmp as for msort_rows.
+int64_t msort_into_max_rows();
+cudaError_t msort_rows_into(const int32_t *rows, const float *scores, int64_t n, int32_t w, int bits, void *tmp,
+                            int32_t *out_rows, float *out_scores, unsigned long long *sum, int max_blocks,
+                            cudaStream_t s);
 // When sum is set, the row checksums (sum of H(row), as the count-mode join) are added to it.
 cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
                        unsigned long long *sum, cudaStream_t s);

@@ -179,7 +179,103 @@ __global__ void k_merge_pass(const SortKeys S, int64_t n, int64_t L, const unsig
   }
 }
 
+// Up to RS_LANES tiles: instead of merge passes and a gather, one launch gives every element
+// of the tile-sorted (key, idx) arrays its final position, its rank in its own tile plus, for
+// each other tile, the number of that tile's elements before it (a lower bound by binary
+// search, one lane of a 16-lane group per tile), and copies its row (and score) there. The
+// order is the same strict order as the tile sort's (key, remaining columns, index), so the
+// positions are a permutation.
+constexpr int RS_LANES = 16;
+
+template <int KW>
+__device__ __forceinline__ void rank_scatter_one(const SortKeys &S, int64_t n, const unsigned long long *key,
+                                                 const int32_t *idx, const float *ins, int32_t *out, float *outs,
+                                                 int64_t e) {
+  const int l = threadIdx.x % RS_LANES;
+  const unsigned seg = 0xFFFFu << (threadIdx.x & 16);
+  const int t = (int)(e / MS_TILE);
+  const int ntiles = (int)((n + MS_TILE - 1) / MS_TILE);
+  unsigned long long kx[KW];
+#pragma unroll
+  for (int j = 0; j < KW; j++) kx[j] = key[(int64_t)j * n + e];
+  const int32_t ix = idx[e];
+  int64_t cnt = 0;
+  if (l < ntiles && l != t) {
+    const int64_t b = (int64_t)l * MS_TILE;
+    int64_t lo = b, hi = b + MS_TILE < n ? b + MS_TILE : n;
+    while (lo < hi) {  // first element of tile l not before x
+      const int64_t mid = (lo + hi) >> 1;
+      unsigned long long km[KW];
+#pragma unroll
+      for (int j = 0; j < KW; j++) km[j] = key[(int64_t)j * n + mid];
+      if (row_less<KW>(S, km, idx[mid], kx, ix)) lo = mid + 1;
+      else hi = mid;
+    }
+    cnt = lo - b;
+  }
+#pragma unroll
+  for (int o = RS_LANES / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(seg, cnt, o, RS_LANES);
+  const int64_t pos = (e - (int64_t)t * MS_TILE) + cnt;
+  if (pos >= n) return;  // cannot happen for sorted tiles; no write outside the table regardless
+  const int32_t *src = S.rows + (int64_t)ix * S.w;
+  for (int c = l; c < S.w; c += RS_LANES) out[pos * S.w + c] = __ldg(src + c);
+  if (l == 0 && outs) outs[pos] = __ldg(ins + ix);
+}
+
+template <int KW>
+__global__ void k_rank_scatter(const SortKeys S, int64_t n, const unsigned long long *key, const int32_t *idx,
+                               const float *ins, int32_t *out, float *outs) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const int64_t groups = (int64_t)gridDim.x * blockDim.x / RS_LANES;
+  for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / RS_LANES; e < n; e += groups)
+    rank_scatter_one<KW>(S, n, key, idx, ins, out, outs, e);  // a 16-lane group shares e: it loops together
+}
+
+
 int64_t msort_tmp_bytes(int64_t n) { return n * (8 * MS_KW + 4) * 2 + 256; }
+int64_t msort_into_max_rows() { return (int64_t)RS_LANES * MS_TILE; }
+
+template <int KW>
+static void msort_into_launch(const SortKeys &S, int64_t n, int bits, int cpw, unsigned long long *k0, int32_t *i0,
+                              const float *ins, int32_t *out, float *outs, unsigned long long *sum, int max_blocks,
+                              cudaStream_t s) {
+  int grid = (int)((n + 255) / 256);
+  k_pack_keys<KW><<<grid, 256, 0, s>>>(S.rows, n, S.w, bits, cpw, k0, i0, sum);
+  launch_pdl(k_sort_tiles<KW>, dim3((unsigned)((n + MS_TILE - 1) / MS_TILE)), dim3(MS_BLK), 0, s, S, n, k0, i0);
+  int64_t rs_grid = (n * RS_LANES + 255) / 256;
+  if (rs_grid > max_blocks) rs_grid = max_blocks;
+  launch_pdl(k_rank_scatter<KW>, dim3((unsigned)rs_grid), dim3(256), 0, s, S, n, (const unsigned long long *)k0,
+             (const int32_t *)i0, ins, out, outs);
+}
+
+cudaError_t msort_rows_into(const int32_t *rows, const float *scores, int64_t n, int32_t w, int bits, void *tmp,
+                            int32_t *out_rows, float *out_scores, unsigned long long *sum, int max_blocks,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (max_blocks < 1) max_blocks = 1;
+  if (n > msort_into_max_rows()) return cudaErrorInvalidValue;
+  if (bits < 1) bits = 1;
+  if (bits > 32) bits = 32;
+  const int cpw = 64 / bits;
+  int kw = (w + cpw - 1) / cpw;
+  if (kw < 1) kw = 1;
+  if (kw > MS_KW) kw = MS_KW;
+  SortKeys S;
+  S.rows = rows;
+  S.w = w;
+  S.packed = kw * cpw < w ? kw * cpw : w;
+  unsigned long long *k0 = (unsigned long long *)tmp;
+  int32_t *i0 = (int32_t *)(k0 + (int64_t)kw * n);
+  switch (kw) {
+    case 1: msort_into_launch<1>(S, n, bits, cpw, k0, i0, scores, out_rows, out_scores, sum, max_blocks, s); break;
+    case 2: msort_into_launch<2>(S, n, bits, cpw, k0, i0, scores, out_rows, out_scores, sum, max_blocks, s); break;
+    case 3: msort_into_launch<3>(S, n, bits, cpw, k0, i0, scores, out_rows, out_scores, sum, max_blocks, s); break;
+    default: msort_into_launch<4>(S, n, bits, cpw, k0, i0, scores, out_rows, out_scores, sum, max_blocks, s); break;
+  }
+  g_launches += 3;
+  return cudaGetLastError();
+}
 
 template <int KW>
 static int msort_launch(const SortKeys &S, int64_t n, int bits, int cpw, unsigned long long *k0,
