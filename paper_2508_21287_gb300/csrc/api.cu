@@ -776,17 +776,7 @@ struct Exec {
         a.n_dev = c->d_ctr_steps + (size_t)(j - 1) * CTR_N + CTR_ROWS;
         a.in_cap = prev_cap;
       }
-      // The input count of step j > 0 is read on the device. A step the planner expects to be
-      // small gets a grid for twice its predicted rows (at least a block per eight SMs) instead
-      // of a full wave, so that small queries on other streams find free SMs.
-      int64_t hint = 0;
-      if (j > 0 && (int)p->pred_growth.size() >= j) {
-        double lr = 0;
-        for (int i = 0; i < j; i++) lr += p->pred_growth[i];
-        const double pred = exp(std::min(40.0, std::max(-40.0, lr)));
-        if (pred * 2 < (double)c->num_sms * 1024) hint = (int64_t)(pred * 2) + (int64_t)c->num_sms * 32;
-      }
-      int grid = dmk::wjoin_grid(a, c->num_sms, hint);
+      int grid = dmk::wjoin_grid(a, c->num_sms);
       CK(dmk::launch_wjoin(a, grid, c->stream, j > 0));  // steps chain kernel to kernel
       prev_rows = orows;
       prev_score = a.outs;

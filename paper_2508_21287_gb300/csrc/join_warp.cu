@@ -104,9 +104,19 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
   return ok;
 }
 
-// Write the warp's staged survivors: one reservation, then coalesced element-parallel stores.
-// code[q] < 0x100: working column of the R row; else 0x100 | index of the new vertex (read
-// from the staging area when STG, else from the motif row).
+// Word q of staged survivor s's output row. code[q] < 0x100: working column of the R row; else
+// 0x100 | index of the new vertex (read from the staging area when STG, else from the motif row).
+template <bool STG>
+__device__ __forceinline__ int32_t out_word(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int wsv, int s,
+                                            int q) {
+  const int cd = code[q];
+  if (cd < 0x100) return W.rows[W.st_r[s] * wsv + cd];
+  if (STG) return W.st_nv[s * STAGE_NV + (cd & 0xff)];
+  return __ldg(a.ix.rows + (int64_t)W.st_m[s] * a.ix.mw + a.new_mpos[cd & 0xff]);
+}
+
+// Write the warp's staged survivors: one reservation, then coalesced stores, 16 bytes per lane
+// from the first 16-byte boundary of the reserved range (scalar head and tail).
 template <bool STG>
 __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int wsv, int n,
                                        unsigned long long &nsum) {
@@ -136,15 +146,23 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
   }
   int32_t *dst = a.out + base * wo;
   const int ne = Kc * wo;
-  int s = lane / wo, q = lane % wo;
-  const int ds = 32 / wo, dq = 32 % wo;
-  for (int e = lane; e < ne; e += 32) {
-    const int cd = code[q];
-    int32_t v;
-    if (cd < 0x100) v = W.rows[W.st_r[s] * wsv + cd];
-    else if (STG) v = W.st_nv[s * STAGE_NV + (cd & 0xff)];
-    else v = __ldg(mrows + (int64_t)W.st_m[s] * mw + a.new_mpos[cd & 0xff]);
-    dst[e] = v;
+  const int h = min((int)((4 - (((uintptr_t)dst >> 2) & 3)) & 3), ne);  // words before a 16-byte boundary
+  if (lane < h) dst[lane] = out_word<STG>(a, W, code, wsv, lane / wo, lane % wo);
+  const int n4 = (ne - h) >> 2;
+  int4 *d4 = (int4 *)(dst + h);
+  int s = (h + 4 * lane) / wo, q = h + 4 * lane - s * wo;  // word h + 4 * k of the lane, with carry
+  const int ds = 128 / wo, dq = 128 % wo;
+  for (int k = lane; k < n4; k += 32) {
+    int4 v;
+    int ss = s, qq = q;
+    v.x = out_word<STG>(a, W, code, wsv, ss, qq);
+    if (++qq == wo) qq = 0, ss++;
+    v.y = out_word<STG>(a, W, code, wsv, ss, qq);
+    if (++qq == wo) qq = 0, ss++;
+    v.z = out_word<STG>(a, W, code, wsv, ss, qq);
+    if (++qq == wo) qq = 0, ss++;
+    v.w = out_word<STG>(a, W, code, wsv, ss, qq);
+    d4[k] = v;
     s += ds;
     q += dq;
     if (q >= wo) {
@@ -152,6 +170,7 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
       s++;
     }
   }
+  for (int e = h + 4 * n4 + lane; e < ne; e += 32) dst[e] = out_word<STG>(a, W, code, wsv, e / wo, e % wo);
   __syncwarp();
 }
 
@@ -195,15 +214,39 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     if (!seed) {
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
-      int r = lane / w, c = lane % w;  // element e = r * w + c, advanced with carry
-      const int dr = 32 / w, dc = 32 % w;
-      for (int e = lane; e < ne; e += 32) {
-        W.rows[r * wsv + c] = __ldg(src + e);
-        r += dr;
-        c += dc;
-        if (c >= w) {
-          c -= w;
-          r++;
+      if ((((uintptr_t)src) & 15) == 0) {  // 16-byte loads; their words go to the padded rows
+        const int n4 = ne >> 2;
+        int r = (lane * 4) / w, c = lane * 4 - r * w;  // first word 4 * k of the lane, with carry
+        const int dr = 128 / w, dc = 128 % w;
+        for (int k = lane; k < n4; k += 32) {
+          const int4 x = __ldg((const int4 *)src + k);
+          int rr = r, cc = c;
+          W.rows[rr * wsv + cc] = x.x;
+          if (++cc == w) cc = 0, rr++;
+          W.rows[rr * wsv + cc] = x.y;
+          if (++cc == w) cc = 0, rr++;
+          W.rows[rr * wsv + cc] = x.z;
+          if (++cc == w) cc = 0, rr++;
+          W.rows[rr * wsv + cc] = x.w;
+          r += dr;
+          c += dc;
+          if (c >= w) {
+            c -= w;
+            r++;
+          }
+        }
+        for (int e = n4 * 4 + lane; e < ne; e += 32) W.rows[(e / w) * wsv + e % w] = __ldg(src + e);
+      } else {
+        int r = lane / w, c = lane % w;  // element e = r * w + c, advanced with carry
+        const int dr = 32 / w, dc = 32 % w;
+        for (int e = lane; e < ne; e += 32) {
+          W.rows[r * wsv + c] = __ldg(src + e);
+          r += dr;
+          c += dc;
+          if (c >= w) {
+            c -= w;
+            r++;
+          }
         }
       }
       if (a.Rs && lane < nr) W.rs[lane] = __ldg(a.Rs + r0 + lane);
@@ -329,10 +372,10 @@ static void set_wjoin_attrs() {
   done.fetch_or(bit);
 }
 
-int wjoin_grid(const JoinArgs &a, int num_sms, int64_t row_hint) {
+int wjoin_grid(const JoinArgs &a, int num_sms) {
   set_wjoin_attrs();
   WJoinKernel k = pick_wjoin(a);
-  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? (row_hint > 0 ? row_hint : INT64_MAX / 2) : a.N);
+  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? INT64_MAX / 2 : a.N);
   int64_t blocks_needed = (rows + (int64_t)WT * WJ_WARPS - 1) / ((int64_t)WT * WJ_WARPS);
   // resident blocks per SM for this variant and row stride, asked of the runtime once (the
   // query costs host time on every launch otherwise); every device of the process is taken to

@@ -42,10 +42,9 @@ extern thread_local int64_t g_launches;
 // pdl: launched with programmatic dependent launch (the previous stream operation must be a
 // kernel of the same chain).
 cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s, bool pdl = false);
-// row_hint: for a launch that reads its input row count on the device (n_dev), an estimate of
-// that count to size the grid by (0 = one full wave). The kernel loops over its tiles, so any
-// hint gives the same result; a low one only runs slower.
-int wjoin_grid(const dmi::JoinArgs &a, int num_sms, int64_t row_hint = 0);
+// One full wave for a launch that reads its input row count on the device (n_dev), else the
+// blocks its rows need, at most one wave.
+int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
 
 // Data-graph preparation.
 cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, const float *eerr,
