@@ -40,7 +40,7 @@ WORKLOAD = "C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 
 # Per-launch DRAM traffic (read + write bytes) of k_joinw from the ncu capture of the same
 # workload summarised in profiles/ (k_joinw_c2_dram_traffic.md); None where no capture of that
 # workload with the current kernel exists.
-JOIN_TRAFFIC_BYTES_PER_LAUNCH = {"c2": 492611}
+JOIN_TRAFFIC_BYTES_PER_LAUNCH = {"c2": 490853}
 
 
 def parse_args():
