@@ -7,9 +7,10 @@
 // back to the remaining columns of the rows themselves. Tiles of 1024 rows are sorted by a
 // bitonic network in shared memory; runs are then merged pairwise, each element finding its
 // output position by a binary search in the other run (stable: ties keep run order). A sort
-// of N rows takes 2 + ceil(log2(N / 1024)) launches. The key-packing kernel can also add the
-// rows' checksum hashes (the same H as the join's count mode) into a counter, so that
-// delivering a table needs no separate hashing pass.
+// of N rows takes 2 + ceil(log2(N / 1024)) launches; tables of up to 16 tiles instead place
+// every row at its final position in one rank-scatter launch (msort_rows_into). The
+// key-packing kernel can also add the rows' checksum hashes (the same H as the join's count
+// mode) into a counter, so that delivering a table needs no separate hashing pass.
 //
 // Top-k runs on a canonically sorted table: the key of row i is (FP32 score bits, i); scores
 // are non-negative, so the bit pattern orders like the value, and i orders like the row.
