@@ -106,6 +106,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def combine_ranks(ms: float, units: float, device: str = "cuda") -> tuple[float, float]:
+    """The whole job's time and work: the slowest rank's milliseconds and the sum of the units
+    (embeddings, bytes) all ranks processed. Each rank works on its own queries (weak scaling),
+    so this is the only exchange; a single process gets its own numbers back."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -349,15 +364,7 @@ def run_ours(args):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    emb_total = acc["emb"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([emb_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        ms, emb_total = float(t.item()), float(e.item())
+    ms, emb_total = combine_ranks(sum(a.elapsed_time(b) for a, b in ev), acc["emb"])
     value = emb_total / (ms / 1e3)
     clocks = clk.summary()
 
@@ -371,9 +378,12 @@ def run_ours(args):
         for _ in range(args.steps):
             emb2 += step(True, eacc)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        d2h = eacc["d2h"] // max(1, args.steps)
-        e2e = {"value": emb2 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        el_ms, emb2 = combine_ranks(1e3 * (time.perf_counter() - t0), emb2)
+        barrier()
+        _, h2d = combine_ranks(0.0, h2d)
+        _, d2h = combine_ranks(0.0, eacc["d2h"] // max(1, args.steps))
+        e2e = {"value": emb2 / (el_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
     peaks = {}
     try:
@@ -509,6 +519,9 @@ def run_c4(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         launches = 0
         torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -517,6 +530,8 @@ def run_c4(args):
             ev[i][1].record(stream)
             launches += B.dm_get_stats(ctx.h)["kernel_launches"]
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
         emb = int(counts.sum())
         done = list(B.dm_batch_latency(ctx.h, len(plans)))  # completion of each pattern, last step
@@ -570,8 +585,9 @@ def run_c4(args):
     bl["plan_ms_total"] = learned_plan_ms
     bl["plan_batch_ms_total"] = learned_batch_plan_ms
     assert bl["embeddings_per_step"] == bat["embeddings_per_step"] == bh["embeddings_per_step"] == plain_emb
-    line = {"metric": METRIC, "value": bl["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": bl["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+    ms_job, emb_job = combine_ranks(sum(ms), bl["embeddings_per_step"] * len(ms))  # all ranks' patterns
+    line = {"metric": METRIC, "value": emb_job / (ms_job / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_job / len(ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": wl_name(args), "patterns_per_step": len(pats),
                        "embeddings_per_step": bl["embeddings_per_step"], "l2": "flushed between steps (256 MiB write)",
@@ -595,7 +611,7 @@ def run_c5(args):
     import numpy as np
     import threading as th
     import torch
-    rank, world, local = dist_env()
+    rank, _, local = dist_env()
     torch.cuda.set_device(local)
     from paper_2508_21287_gb300 import build
     build.build()
@@ -662,7 +678,7 @@ def run_c5(args):
         sweep = serve(B.DM_ORDER_LEARNED)
         sweep_paper = serve(B.DM_ORDER_PAPER)
     top = sweep[-1]
-    line = {"metric": "requests/sec", "value": top["completed_per_s"], "unit": "requests/s", "n_gpus": world,
+    line = {"metric": "requests/sec", "value": top["completed_per_s"], "unit": "requests/s", "n_gpus": 1,
             "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD_C5, "requests_per_rate": n_req, "slots": 8, "max_rows": 4_000_000,
@@ -682,7 +698,7 @@ def run_motifs(args):
     20-vertex patterns, greedy order (the paper's largest-motif-first order streams hundreds of
     millions of rows on some 60-vertex patterns), count + checksum, per motif set."""
     import torch
-    rank, world, local = dist_env()
+    rank, _, local = dist_env()
     torch.cuda.set_device(local)
     from paper_2508_21287_gb300 import build
     build.build()
@@ -723,7 +739,7 @@ def run_motifs(args):
                         "embeddings": emb, "embeddings_per_s": emb / (sum(times) / 1e3)})
     ctx.close()
     best = max(out, key=lambda r: r["embeddings_per_s"])
-    line = {"metric": METRIC, "value": best["embeddings_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
+    line = {"metric": METRIC, "value": best["embeddings_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": sum(r["ms_total"] for r in out), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "motif-set study: random connected patterns, counts identical across sets",
@@ -736,6 +752,8 @@ def run_motifs(args):
 
 def main():
     args = parse_args()
+    if args.workload in ("c5", "motifs") and args.impl != "reference" and dist_env()[1] > 1 and dist_env()[0] != 0:
+        return 0  # one-GPU studies: under torchrun rank 0 alone runs and reports them (n_gpus 1)
     if args.workload == "c5" and args.impl != "reference":
         return run_c5(args)
     if args.impl == "reference":

@@ -1,0 +1,57 @@
+"""The N > 1 path of the benchmark on CPU: two gloo ranks launched by torchrun. Each rank
+takes its own queries (disjoint seeds, weak scaling) and the only exchange is the job's
+time (slowest rank) and work (sum over ranks)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+import textwrap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = textwrap.dedent("""
+    import json, sys
+    sys.path.insert(0, {root!r})
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo")
+    r = dist.get_rank()
+    ms, units = bench.combine_ranks(10.0 * (r + 1), 100 * (r + 1), device="cpu")
+    g, pats = bench.workload(r, 6, "c2")
+    edges = [sorted(p.edges()) for p in pats]
+    got = [None, None]
+    dist.all_gather_object(got, edges)
+    rank, world, local = bench.dist_env()
+    print(json.dumps({{"rank": r, "env": [rank, world, local], "ms": ms, "units": units, "n": len(pats),
+                      "disjoint": all(e not in got[1 - r] for e in edges)}}))
+    dist.destroy_process_group()
+""")
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_shard_queries_and_combine_time_and_work(tmp_path):
+    script = tmp_path / "child.py"
+    script.write_text(CHILD.format(root=ROOT))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script)]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    assert sorted(x["rank"] for x in lines) == [0, 1]
+    for x in lines:
+        assert x["ms"] == 20.0 and x["units"] == 300.0  # max of 10, 20 and sum of 100, 200
+        assert x["env"][:2] == [x["rank"], 2] and x["n"] == 6
+        assert x["disjoint"]  # no query of one rank is a query of the other
+
+
+def test_single_process_keeps_its_own_numbers():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.combine_ranks(12.5, 7, device="cpu") == (12.5, 7.0)
