@@ -23,8 +23,9 @@ CHILD = textwrap.dedent("""
     got = [None, None]
     dist.all_gather_object(got, edges)
     rank, world, local = bench.dist_env()
-    print(json.dumps({{"rank": r, "env": [rank, world, local], "ms": ms, "units": units, "n": len(pats),
-                      "disjoint": all(e not in got[1 - r] for e in edges)}}))
+    with open(sys.argv[1] + "/rank%d.json" % r, "w") as f:  # one file per rank: no interleaved output
+        json.dump({{"rank": r, "env": [rank, world, local], "ms": ms, "units": units, "n": len(pats),
+                   "disjoint": all(e not in got[1 - r] for e in edges)}}, f)
     dist.destroy_process_group()
 """)
 
@@ -39,11 +40,11 @@ def test_two_gloo_ranks_shard_queries_and_combine_time_and_work(tmp_path):
     script = tmp_path / "child.py"
     script.write_text(CHILD.format(root=ROOT))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
-           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script)]
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script), str(tmp_path)]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
-    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    lines = [json.loads((tmp_path / f"rank{r}.json").read_text()) for r in range(2)]
     assert sorted(x["rank"] for x in lines) == [0, 1]
     for x in lines:
         assert x["ms"] == 20.0 and x["units"] == 300.0  # max of 10, 20 and sum of 100, 200
