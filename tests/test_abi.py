@@ -138,3 +138,41 @@ def test_query_runner_checks_arguments_without_a_device(B):
     with pytest.raises(B.DMError) as e:
         B.dm_match_topk_queries([], [], [(p.n, p.row_ptr, p.col_idx)], 5)
     assert e.value.code == B.DM_E_INVAL
+
+
+def _motif_edges(motif: int):
+    # position pairs of the path and cycle motifs (M_k: k positions in a row; M_{k-O}: closed)
+    if motif < 100:
+        return [(i, i + 1) for i in range(motif - 1)]
+    k = motif - 100
+    return [(i, (i + 1) % k) for i in range(k)]
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("motifs", [[2], [3], [4], [4, 2], [104, 2], [104, 106, 2], [112, 4, 2], [8, 4, 2]])
+def test_slices_and_back_edges_enforce_exactly_the_pattern_edges(B, motifs, order):
+    # Every slice places its motif on pattern edges (so a join never asks for an edge the
+    # pattern lacks), and the slices' motif edges together with the back-edges are exactly the
+    # pattern's edges (so no pattern edge goes unchecked): the conditions under which Alg. 1
+    # returns exactly Emb(G_p, G_d).
+    from paper_2508_21287_gb300 import inputs as I
+    g = I.heavy_hex(3, 4)
+    grid = I.grid(6, 6)
+    pats = [I.random_tree(12 + s, s) for s in range(3)] + [I.cycle_with_chords(10 + s, s) for s in range(3)]
+    pats += [I.sub_patch(g, 14 + 4 * s, s) for s in range(3)] + [I.sub_patch(grid, 9 + 3 * s, s) for s in range(3)]
+    pats += [I.cycle(12), I.cycle(18), I.path(9)]
+    for p in pats:
+        try:
+            d = B.dm_decompose(p.n, p.row_ptr, p.col_idx, motifs, order=order)
+        except B.DMError:
+            continue  # a motif set that cannot start this pattern (no slice fits) is refused
+        edges = set(p.edges())
+        enforced = []
+        for s in d:
+            sl = s["slice"]
+            for a, b in _motif_edges(s["motif"]):
+                e = tuple(sorted((sl[a], sl[b])))
+                assert e in edges, (p.n, motifs, s)
+                enforced.append(e)
+            enforced += [tuple(sorted(e)) for e in s["backedges"]]
+        assert set(enforced) == edges, (p.n, motifs, order)
