@@ -176,3 +176,46 @@ def test_slices_and_back_edges_enforce_exactly_the_pattern_edges(B, motifs, orde
                 enforced.append(e)
             enforced += [tuple(sorted(e)) for e in s["backedges"]]
         assert set(enforced) == edges, (p.n, motifs, order)
+
+
+def _motif_pattern(motif: int):
+    from paper_2508_21287_gb300 import inputs as I
+    return I.path(motif) if motif < 100 else I.cycle(motif - 100)
+
+
+@pytest.mark.parametrize("motifs", [[2], [4, 2], [104, 2], [104, 106, 2], [8, 4, 2]])
+def test_plan_executed_on_the_host_gives_the_oracle_set(B, motifs):
+    # The plan's slices run through Alg. 1 in plain Python (motif tables from the oracle, joins on
+    # the shared pattern vertices, distinct images, back-edge tests) give exactly the oracle's
+    # embedding set: the decomposition is sound and complete, independent of the kernels.
+    import numpy as np
+    import oracle
+    from paper_2508_21287_gb300 import inputs as I
+    cases = [(I.grid(5, 5), I.grid(2, 3)), (I.grid(5, 5), I.cycle(6)), (I.grid(5, 5), I.sub_patch(I.grid(6, 6), 8, 2)),
+             (I.heavy_hex(2, 3), I.path(7)), (I.heavy_hex(2, 3), I.cycle(12)), (I.grid(4, 5), I.random_tree(8, 3))]
+    for data, p in cases:
+        d = B.dm_decompose(p.n, p.row_ptr, p.col_idx, motifs)
+        adj = set(data.edges()) | {(b, a) for a, b in data.edges()}
+        tables = {}
+        R = None  # list of dicts pattern vertex -> data vertex
+        for s in d:
+            m = s["motif"]
+            if m not in tables:
+                tables[m] = oracle.enumerate(data, _motif_pattern(m)).rows
+            sl = s["slice"]
+            out = []
+            for t in tables[m]:
+                cand = dict(zip(sl, (int(x) for x in t)))
+                for row in (R if R is not None else [{}]):
+                    if any(row[v] != cand[v] for v in cand if v in row):
+                        continue  # join keys disagree
+                    new = [cand[v] for v in cand if v not in row]
+                    if len(set(new)) != len(new) or set(new) & set(row.values()):
+                        continue  # images must stay distinct
+                    merged = {**row, **cand}
+                    if all((merged[a], merged[b]) in adj for a, b in s["backedges"]):
+                        out.append(merged)
+            R = out
+        got = sorted(tuple(r[v] for v in range(p.n)) for r in R)
+        ref = oracle.enumerate(data, p)
+        assert got == [tuple(x) for x in np.asarray(ref.rows).tolist()], (p.n, motifs)
