@@ -2,7 +2,7 @@
  * CPU oracle for subgraph-isomorphism enumeration (Delta-Motif, arXiv 2508.21287).
  *
  * TEST INFRASTRUCTURE ONLY. Nothing on the product path may link, load or call this
- * file; the tests, the smoke check and the benchmark's CPU-baseline leg use it to judge
+ * file; the tests, the smoke check and the benchmark's CPU-baseline leg use it to check
  * the CUDA path. It shares no code, header, table or helper with the CUDA library.
  *
  * What it computes is the plain definition of the result, not the paper's method:
