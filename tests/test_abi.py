@@ -183,8 +183,9 @@ def _motif_pattern(motif: int):
     return I.path(motif) if motif < 100 else I.cycle(motif - 100)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("motifs", [[2], [4, 2], [104, 2], [104, 106, 2], [8, 4, 2]])
-def test_plan_executed_on_the_host_gives_the_oracle_set(B, motifs):
+def test_plan_executed_on_the_host_gives_the_oracle_set(B, motifs, order):
     # The plan's slices run through Alg. 1 in plain Python (motif tables from the oracle, joins on
     # the shared pattern vertices, distinct images, back-edge tests) give exactly the oracle's
     # embedding set: the decomposition is sound and complete, independent of the kernels.
@@ -194,7 +195,7 @@ def test_plan_executed_on_the_host_gives_the_oracle_set(B, motifs):
     cases = [(I.grid(5, 5), I.grid(2, 3)), (I.grid(5, 5), I.cycle(6)), (I.grid(5, 5), I.sub_patch(I.grid(6, 6), 8, 2)),
              (I.heavy_hex(2, 3), I.path(7)), (I.heavy_hex(2, 3), I.cycle(12)), (I.grid(4, 5), I.random_tree(8, 3))]
     for data, p in cases:
-        d = B.dm_decompose(p.n, p.row_ptr, p.col_idx, motifs)
+        d = B.dm_decompose(p.n, p.row_ptr, p.col_idx, motifs, order=order)
         adj = set(data.edges()) | {(b, a) for a, b in data.edges()}
         tables = {}
         R = None  # list of dicts pattern vertex -> data vertex
