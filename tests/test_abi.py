@@ -220,3 +220,32 @@ def test_plan_executed_on_the_host_gives_the_oracle_set(B, motifs, order):
         got = sorted(tuple(r[v] for v in range(p.n)) for r in R)
         ref = oracle.enumerate(data, p)
         assert got == [tuple(x) for x in np.asarray(ref.rows).tolist()], (p.n, motifs)
+
+
+@pytest.mark.parametrize("n", [63, 64, 65, 100, 128])
+def test_wide_patterns_enforce_exactly_their_edges(B, n):
+    # patterns across the 64-vertex word boundary of the planner's vertex sets, up to the
+    # 128-vertex limit: the slice and back-edge conditions hold, the plan is deterministic,
+    # and one vertex more is refused
+    from paper_2508_21287_gb300 import inputs as I
+    g = I.heavy_hex(6, 6)
+    for p in (I.sub_patch(g, n, 5), I.random_tree(n, n)):
+        for order in (0, 1):
+            d = B.dm_decompose(p.n, p.row_ptr, p.col_idx, [4, 2], order=order)
+            assert d == B.dm_decompose(p.n, p.row_ptr, p.col_idx, [4, 2], order=order)
+            edges = set(p.edges())
+            enforced, mapped = [], set()
+            for s in d:
+                sl = s["slice"]
+                assert len(set(sl)) == len(sl)
+                for a, b in _motif_edges(s["motif"]):
+                    e = tuple(sorted((sl[a], sl[b])))
+                    assert e in edges
+                    enforced.append(e)
+                enforced += [tuple(sorted(e)) for e in s["backedges"]]
+                mapped |= set(sl)
+            assert set(enforced) == edges and mapped == set(range(p.n))
+    t = I.random_tree(129, 1)
+    with pytest.raises(B.DMError) as e:
+        B.dm_decompose(t.n, t.row_ptr, t.col_idx, [4, 2])
+    assert e.value.code == B.DM_E_INVAL
