@@ -146,12 +146,14 @@ int dm_plan(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
 
 void dm_plan_free(dm_plan_t *plan);
 
-/* dm_plan for n_patterns patterns at once (pattern i: n_p[i] vertices, CSR p_row_ptr[i] /
+/* dm_plan (the decomposition and join order of Sec. 3.2) for n_patterns patterns at once,
+ * no counterpart in the paper as a batch (pattern i: n_p[i] vertices, CSR p_row_ptr[i] /
  * p_col_idx[i]), the same options for all: motif tables are prepared on the calling thread,
  * the decompositions run on host threads, and with DM_ORDER_LEARNED every candidate of every
- * pattern is costed in one model evaluation. Plans equal those of dm_plan pattern by pattern.
- * On error nothing is returned (out[i] = NULL for all i) and the status is that of the first
- * failing pattern. */
+ * pattern is costed in one model evaluation. Plans equal those of dm_plan pattern by pattern;
+ * out (n_patterns entries, caller-owned array) receives them, each to be released with
+ * dm_plan_free. On error nothing is returned (out[i] = NULL for all i) and the status is that
+ * of the first failing pattern. */
 int dm_plan_batch(dm_ctx *ctx, dm_graph g, int32_t n_patterns, const int32_t *n_p,
                   const int32_t *const *p_row_ptr, const int32_t *const *p_col_idx,
                   const dm_plan_opts *opts, dm_plan_t **out);
