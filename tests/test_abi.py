@@ -249,3 +249,16 @@ def test_wide_patterns_enforce_exactly_their_edges(B, n):
     with pytest.raises(B.DMError) as e:
         B.dm_decompose(t.n, t.row_ptr, t.col_idx, [4, 2])
     assert e.value.code == B.DM_E_INVAL
+
+
+def test_query_batch_marshals_once(B):
+    import ctypes
+    from paper_2508_21287_gb300 import inputs as I
+    qs = [I.path(4), I.cycle(6), I.star(3)]
+    qb = B.QueryBatch([(q.n, q.row_ptr, q.col_idx) for q in qs], 7)
+    assert qb.n == 3 and qb.k == 7 and list(qb.n_p) == [4, 6, 4]
+    assert [r.shape for r in qb.rows] == [(7, 4), (7, 6), (7, 4)] and all(x.shape == (7,) for x in qb.scores)
+    for i, q in enumerate(qs):  # the pointer arrays point at the marshalled CSR of each query
+        assert qb.rps[i][q.n] == q.row_ptr[-1] and qb.cis[i][0] == q.col_idx[0]
+    with pytest.raises(ValueError):  # a batch is made for one k
+        B.dm_match_topk_queries([ctypes.c_void_p(0x1000)], [0], qb, 5)
