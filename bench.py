@@ -1,25 +1,34 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the Delta-Motif GB300 library (one JSON line on rank 0).
 
-Workload (layout selection on a ~160-qubit heavy-hex device): data graph = heavy-hex 4 x 6
-(159 vertices, 182 edges) with log-normal(-5, 0.5) FP32 edge errors; one step = a batch of
-layout queries (10-30 vertices, max degree 3; even seeds a random spanning tree of a random
-device patch, odd seeds the induced patch with its cell cycles), each planned (motif
-decomposition) and matched: every embedding in canonical order with its FP32 layout score,
-plus the top-100 layouts. Embeddings stay on the device for `value`; `e2e` repeats the step
-through the same C ABI with every embedding copied to host memory.
+Headline workload (the largest single-GPU configuration of the scaling study): data graph =
+heavy-hex 53 x 59 (V = 16 082 qubits, the paper's lattice family at ~3.5x its largest size);
+one step = 32 seeded queries, paths of 8-24 vertices and random connected sub-patches of 12-40
+vertices, each planned (motif decomposition, Sec. 3.2) and matched (Alg. 1) to its count and
+64-bit checksum of the canonical embeddings. Intermediate tables reach ~3e7 rows (GBs, far
+beyond the 129 MB L2). `value` = embeddings per second with the data graph resident and the
+patterns already planned; `e2e` = the same queries through the C ABI as a caller makes them
+(dm_plan from host pattern arrays, then dm_match to the host count and checksum), wall clock.
+`roofline` = the join kernel's algorithmic bytes over its CUDA-event time in the timed steps.
+
+The same JSON line nests the other configurations, each measured in this run (N = 1 only):
+`c2` (32 layout queries on heavy-hex 4x6, every embedding with its FP32 score plus the
+top-100, over 8 contexts), `c4` (512 uneven patterns: one call per pattern vs one persistent
+launch, paper vs learned plans, all on CUDA events) and `c5` (serving: Poisson arrivals over
+three graphs, p50/p99 and requests/s).
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the library's
 stream, with a 256 MiB write between steps to flush L2 (outside the events). Under torchrun
-each rank runs its own batch (replicas, weak scaling; no collective on the data path) and the
-maximum time over ranks is reported.
+each rank runs its own queries (replicas, weak scaling; no collective on the data path) and
+the job time is the maximum over ranks.
 
---impl reference times the CPU oracle (plain backtracking, FP64 scores, top-100) on the same
-workload on the host cores, a bounded number of passes over the batch.
+--impl reference times the CPU oracle (plain backtracking; count + checksum for the headline)
+on the same queries on the host cores, a bounded number of passes over the batch.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -35,12 +44,23 @@ METRIC = "embeddings/sec"
 UNIT = "embeddings/s"
 K_TOP = 100
 BATCH = 32
-WORKLOAD = "C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 10-30 vertices, all embeddings + FP32 scores + top-100"
+WORKLOAD_C2 = ("C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 10-30 vertices, all "
+               "embeddings + FP32 scores + top-100")
 
-# Per-launch DRAM traffic (read + write bytes) of k_joinw from the ncu capture of the same
-# workload summarised in profiles/ (k_joinw_c2_dram_traffic.md); None where no capture of that
-# workload with the current kernel exists.
-JOIN_TRAFFIC_BYTES_PER_LAUNCH = {"c2": 490853}
+# Mean DRAM bytes (read + write) per k_joinw launch, from the ncu capture of one step of the
+# workload (the profiles/ summary of that workload gives the command), keyed by workload and by
+# the digest of the join kernel's sources at capture time: after any change to those sources
+# the number no longer describes the kernel and the line reports null.
+JOIN_SOURCES = ("join_warp.cu", "join_device.cuh", "dm_internal.h")
+JOIN_TRAFFIC_BYTES_PER_LAUNCH: dict[tuple[str, str], float] = {}
+
+
+def join_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in JOIN_SOURCES:
+        with open(os.path.join(ROOT, "paper_2508_21287_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse_args():
@@ -52,13 +72,13 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "motifs"])
+    ap.add_argument("--no-extras", action="store_true", help="headline only: skip the nested c2/c4/c5 runs")
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5", "motifs"])
     ap.add_argument("--rates", default="500,2000,8000,16000,32000", help="c5: Poisson arrival rates (requests/s)")
     ap.add_argument("--hh", default="53,59", help="heavy-hex m,n of the c3 workload")
     ap.add_argument("--graph", default="heavyhex", choices=["heavyhex", "grid", "rr3"],
                     help="c3: data graph family (heavy-hex m x n, square grid 60x60, random 3-regular V=4096)")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
-    ap.add_argument("--learned", action="store_true", help="c4: plans ordered by the trained cardinality model")
     ap.add_argument("--contexts", type=int, default=0,
                     help="c2/c3: library contexts (each its own stream and host thread) the queries of a step "
                          "are spread over; 0 = 8 for c2, 1 for c3")
@@ -73,7 +93,7 @@ WORKLOAD_C3 = ("C3 scaling: heavy-hex {m}x{n} (V={V}), seeded paths of 8-24 vert
                "vertices, count + 64-bit checksum")
 
 
-def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: int = 0, graph: str = "heavyhex"):
+def workload(rank: int, batch: int, kind: str = "c3", hh=(53, 59), only_path: int = 0, graph: str = "heavyhex"):
     from paper_2508_21287_gb300 import inputs as I
     if kind == "c2":
         g = I.lognormal_weights(I.heavy_hex(4, 6), seed=7)
@@ -100,6 +120,12 @@ def workload(rank: int, batch: int, kind: str = "c2", hh=(53, 59), only_path: in
         else:
             pats.append(I.sub_patch(g, psz[0] + rng.below(psz[1] - psz[0] + 1), rank * batch + i))
     return g, pats
+
+
+def workload_key(args, kind: str) -> str:
+    if kind != "c3":
+        return kind
+    return f"c3:{args.graph}:{args.hh if args.graph == 'heavyhex' else ''}:{args.only_path}:{args.batch}"
 
 
 def dist_env():
@@ -203,12 +229,13 @@ WORKLOAD_C5 = ("C5 serving: Poisson arrivals of top-10 layout requests (patterns
                "cycles / subdivided grids) over heavy-hex 4x6, grid 32x32 and random 3-regular V=2048, 8 slots")
 
 
-def wl_name(args):
-    if args.workload == "c2":
-        return WORKLOAD
-    if args.workload == "c5":
+def wl_name(args, kind=None):
+    kind = kind or args.workload
+    if kind == "c2":
+        return WORKLOAD_C2
+    if kind == "c5":
         return WORKLOAD_C5
-    if args.workload == "c4":
+    if kind == "c4":
         return WORKLOAD_C4
     if args.graph == "grid":
         return WORKLOAD_C3_GRID
@@ -242,21 +269,37 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import numpy as np
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def init_run():
+    """Rank environment, device and the built library (raises if it cannot be built)."""
     import torch
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2508_21287_gb300 import build
     build.build()
     from paper_2508_21287_gb300 import binding as B
+    return B, rank, world, local
 
+
+def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
+    """One workload of independent queries (c3: count + checksum; c2: every embedding with its
+    score plus the top-100), timed over args.steps steps; returns the JSON line (dict)."""
+    import torch
+    B, rank, world, local = init_run()
     hh = tuple(int(x) for x in args.hh.split(","))
-    g, pats = workload(rank, args.batch, args.workload, hh, args.only_path, args.graph)
-    count_mode = args.workload == "c3"
+    g, pats = workload(rank, args.batch, kind, hh, args.only_path, args.graph)
+    count_mode = kind == "c3"
     n_ctx = args.contexts or (1 if count_mode else 8)
     # independent queries: each context (own CUDA stream, arena and graph copy) is driven by its
     # own host thread, so one query's dependent launches overlap with the others'
@@ -275,15 +318,24 @@ def run_ours(args):
 
     acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0, "chunks": 0,
            "max_rows": 0}
-
     qpats = B.QueryBatch([(p.n, p.row_ptr, p.col_idx) for p in pats], K_TOP)  # marshalled once, reused
+    # count mode: plans are made once, outside the timed steps (the e2e leg plans inside)
+    plans = [[B.dm_plan(ctxs[t].h, gids[t], p.n, p.row_ptr, p.col_idx) if i % n_ctx == t else None
+              for i, p in enumerate(pats)] for t in range(n_ctx)] if count_mode else None
 
-    def step(host_rows: bool, rec, use=None):
+    def record(rec, st):
+        with lock:
+            for key in ("join_ms", "join_bytes", "join_launches", "chunks"):
+                rec[key] += st[key]
+            rec["launches"] += st["kernel_launches"]
+            rec["max_rows"] = max(rec["max_rows"], st["max_rows"])
+
+    def step(host: bool, rec, use=None):
         use = list(range(n_ctx)) if use is None else use
         if count_mode:
             if len(use) == 1:
-                return step_ctx(use[0], pats, host_rows, rec)
-            return sum(pool.map(lambda t: step_ctx(t, pats[t::n_ctx], host_rows, rec), use))
+                return count_ctx(use[0], host, rec)
+            return sum(pool.map(lambda t: count_ctx(t, host, rec), use))
         # layout queries: the library's multi-context runner (one native thread per context)
         hb = [0]
 
@@ -292,42 +344,30 @@ def run_ours(args):
                 hb[0] += r.nbytes + (0 if s_ is None else s_.nbytes)
             return 0
         res, st = B.dm_match_topk_queries([ctxs[t].h for t in use], [gids[t] for t in use], qpats, K_TOP,
-                                          mode=B.DM_ALL if host_rows else B.DM_ALL | B.DM_DEVICE_ROWS,
-                                          cb=host_cb if host_rows else None)
+                                          mode=B.DM_ALL if host else B.DM_ALL | B.DM_DEVICE_ROWS,
+                                          cb=host_cb if host else None)
         if rec is not None:
-            rec["d2h"] += hb[0]
-            for key in ("join_ms", "join_bytes", "join_launches", "chunks"):
-                rec[key] += st[key]
-            rec["launches"] += st["kernel_launches"]
-            rec["max_rows"] = max(rec["max_rows"], st["max_rows"])
+            rec["d2h"] += hb[0] + sum(K_TOP * (4 * q.n + 4) for q in pats)
+            record(rec, st)
         return sum(x[2] for x in res)
 
-    def step_ctx(t: int, queries, host_rows: bool, rec):
+    def count_ctx(t: int, host: bool, rec):
+        """Count + checksum of this context's queries: the pre-made plans (device-resident
+        measurement), or, for the e2e leg, dm_plan from the host pattern arrays each time."""
         ctx, gid = ctxs[t], gids[t]
         emb = 0
-        for p in queries:
-            plan = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
-            if count_mode:
-                cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
-            elif host_rows:
-                sink = []
-                _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL, lambda r, s: sink.append((r, s)) and 0,
-                                               K_TOP, p.n)
-                if rec is not None:
-                    with lock:
-                        rec["d2h"] += sum(r.nbytes + (0 if s is None else s.nbytes) for r, s in sink)
-            else:
-                _, _, cnt, _ = B.dm_match_topk(ctx.h, plan, B.DM_ALL | B.DM_DEVICE_ROWS, lambda *a: 0, K_TOP, p.n)
-            st = B.dm_get_stats(ctx.h)
-            B.dm_plan_free(plan)
+        for i, p in enumerate(pats):
+            if i % n_ctx != t:
+                continue
+            plan = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx) if host else plans[t][i]
+            cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
+            if host:
+                B.dm_plan_free(plan)
             if rec is not None:
-                with lock:
-                    rec["join_ms"] += st["join_ms"]
-                    rec["join_bytes"] += st["join_bytes"]
-                    rec["join_launches"] += st["join_launches"]
-                    rec["launches"] += st["kernel_launches"]
-                    rec["chunks"] += st["chunks"]
-                    rec["max_rows"] = max(rec["max_rows"], st["max_rows"])
+                st = B.dm_get_stats(ctx.h)
+                record(rec, st)
+                with lock:  # counters of every join launch come back to the host: 8 x u64 each
+                    rec["d2h"] += 64 * st["join_launches"]
             emb += cnt
         return emb
 
@@ -369,7 +409,7 @@ def run_ours(args):
     clocks = clk.summary()
 
     e2e = None
-    if not args.no_e2e and not count_mode:
+    if with_e2e:
         h2d = sum(p.row_ptr.nbytes + p.col_idx.nbytes for p in pats)
         eacc = {k: 0 for k in acc}
         barrier()
@@ -383,14 +423,12 @@ def run_ours(args):
         _, h2d = combine_ranks(0.0, h2d)
         _, d2h = combine_ranks(0.0, eacc["d2h"] // max(1, args.steps))
         e2e = {"value": emb2 / (el_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h),
+               "path": ("dm_plan from host pattern CSR + dm_match(DM_COUNT) to host count and checksum, per query"
+                        if count_mode else
+                        "dm_match_topk_queries: every embedding and score copied to host, top-100 to host")}
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = read_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     racc = acc
     if n_ctx > 1:  # a launch's own duration is defined with one query on the device at a time:
@@ -403,37 +441,95 @@ def run_ours(args):
             step(False, racc, use=[0])
         torch.cuda.synchronize()
     achieved = racc["join_bytes"] / (racc["join_ms"] / 1e3) / 1e9 if racc["join_ms"] > 0 else 0.0
+    digest = join_kernel_digest()
+    traffic = JOIN_TRAFFIC_BYTES_PER_LAUNCH.get((workload_key(args, kind), digest))
     roofline = {"bound": "hbm", "kernel": "k_joinw", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "traffic": JOIN_TRAFFIC_BYTES_PER_LAUNCH.get(args.workload) if not args.only_path else None,
+                "frac": achieved / peak, "peak_source": "measured (burst copy)" if "hbm_gbs" in peaks else "fallback",
+                "traffic": traffic, "kernel_digest": digest,
                 "algorithmic_bytes_per_launch": racc["join_bytes"] / max(1, racc["join_launches"]),
                 "avg_launch_us": 1e3 * racc["join_ms"] / max(1, racc["join_launches"]),
                 "launches": racc["join_launches"],
-                "timed": "in the timed steps" if n_ctx == 1 else "separate pass, one context, queries in sequence"}
+                "timed": ("in the timed steps (CUDA events on the library's stream)" if n_ctx == 1 else
+                          "separate pass, one context, queries in sequence")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl_name(args), "queries_per_step": len(pats), "embeddings_per_step": emb_total / args.steps / world,
+            "config": {"workload": wl_name(args, kind), "queries_per_step": len(pats),
+                       "embeddings_per_step": emb_total / args.steps / world,
                        "data_graph": ("heavy-hex 4x6" if not count_mode else
                                       {"grid": "grid 60x60", "rr3": "random 3-regular V=4096"}.get(
                                           args.graph, "heavy-hex " + args.hh.replace(",", "x"))),
                        "motifs": "M4-O,M6-O,M2" if count_mode and args.graph == "grid" else "M4,M2",
-                       "l2": "flushed between steps (256 MiB write)",
+                       "output": "count + 64-bit checksum" if count_mode else "all embeddings + FP32 scores + top-100",
+                       "l2": "flushed between steps (256 MiB write); intermediate tables far larger than L2"
+                             if count_mode else "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}", "contexts": n_ctx,
                        "join_chunks_per_step": acc["chunks"] / args.steps, "largest_table_rows": acc["max_rows"]},
             "e2e": e2e, "gpu_launches": acc["launches"], "clocks": clocks, "roofline": roofline}
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if with_cpu and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(g, pats, count_only=count_mode)
     pool.shutdown()
+    if plans:
+        for row in plans:
+            for pl in row:
+                if pl is not None:
+                    B.dm_plan_free(pl)
     for c in ctxs:
         c.close()
+    return line
+
+
+def run_ours(args):
+    rank, world, _ = dist_env()
+    kind = args.workload
+    line = measure_queries(args, kind, with_e2e=not args.no_e2e, with_cpu=not args.no_cpu)
+    if kind == "c3" and world == 1 and not args.no_extras and not args.only_path:
+        line["extras_note"] = ("c2, c4 and c5 below are the other configurations, each measured in this run "
+                               "after the headline")
+        line["c2"] = summary_c2(measure_queries(args_for(args, "c2"), "c2", with_e2e=True, with_cpu=False))
+        line["c4"] = summary_c4(run_c4(args_for(args, "c4"), emit=False))
+        line["c5"] = summary_c5(run_c5(args_for(args, "c5"), emit=False))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def args_for(args, kind: str):
+    a = argparse.Namespace(**vars(args))
+    a.workload = kind
+    a.contexts = 0
+    a.batch = BATCH
+    return a
+
+
+def summary_c2(line):
+    return {"workload": line["config"]["workload"], "value": line["value"], "unit": UNIT,
+            "ms_per_step": line["ms_per_step"], "contexts": line["config"]["contexts"],
+            "e2e": line["e2e"], "gpu_launches": line["gpu_launches"],
+            "roofline": {k: line["roofline"][k] for k in ("achieved", "frac", "avg_launch_us", "launches", "timed")}}
+
+
+def summary_c4(line):
+    keep = ("value", "ms_per_step", "p50_ms_per_pattern", "p99_ms_per_pattern")
+    out = {"workload": line["config"]["workload"], "unit": UNIT}
+    for arm in ("plain_paper", "plain_learned", "batched_paper", "batched_heuristic_choice", "batched_learned"):
+        out[arm] = {k: line[arm][k] for k in keep}
+    out["batched_learned_over_plain_learned"] = line["batched_learned_over_plain_learned"]
+    out["batched_learned_over_plain_paper"] = line["batched_learned_over_plain_paper"]
+    out["model"] = line["model"]
+    return out
+
+
+def summary_c5(line):
+    return {"workload": line["config"]["workload"], "unit": "requests/s", "value": line["value"],
+            "p50_ms": line["p50_ms"], "p99_ms": line["p99_ms"], "rejected_fraction": line["rejected_fraction"],
+            "sweep": [{k: r[k] for k in ("rate", "completed_per_s", "p50_ms", "p99_ms", "rejected")}
+                      for r in line["sweep"]],
+            "overlap": line["overlap"]}
 
 
 def train_model(B, ctx, gid, g, n_train: int = 300):
@@ -486,19 +582,15 @@ def train_model_graphs(B, ctx, gids, n_train: int = 120, max_rows: int = 4_000_0
     return B.dm_model_weights(ctx.h), int(len(t))
 
 
-def run_c4(args):
-    """C4: 512 uneven patterns on one graph. Plain form: one dm_match per pattern, each timed
-    alone. Batched: every pattern in one persistent launch (dm_match_batch). Batched+learned:
-    the same with plans ordered by the trained cardinality model. Plans are made up front."""
+def run_c4(args, emit: bool = True):
+    """C4: 512 uneven patterns on one graph, every arm on CUDA events over the same warm-up and
+    steps. Plain form: one dm_match per pattern (the paper's single-pattern form), with the
+    paper's plans and with the learned plans. Batched: every pattern in one persistent launch
+    (dm_match_batch), with paper plans, with the candidate plans chosen by the independence
+    heuristic, and with the learned plans. Per-pattern latency = completion time of each pattern
+    when all arrive together at the start of the step. Plans are made up front."""
     import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2508_21287_gb300 import build
-    build.build()
-    from paper_2508_21287_gb300 import binding as B
+    B, rank, world, local = init_run()
     nb = args.batch if args.batch != BATCH else 512
     g, pats = workload(rank, nb, "c4")
     ctx = B.Context(local)
@@ -513,15 +605,48 @@ def run_c4(args):
         pl = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, order=order) for p in pats]
         return pl, 1e3 * (time.perf_counter() - t0)
 
-    def batched(plans, clk=None):
-        for _ in range(args.warmup):
-            counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        launches = 0
+    def sync_ranks():
         torch.cuda.synchronize()
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    def plain(plans):
+        """One dm_match per pattern, in order; an event after each pattern on the library's
+        stream gives its completion time from the start of the step."""
+        for _ in range(args.warmup):
+            for p in plans:
+                B.dm_match(ctx.h, p, B.DM_COUNT)
+        ms, launches, emb, done = [], 0, 0, []
+        sync_ranks()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in plans]
+            e0.record(stream)
+            emb = 0
+            for p, e in zip(plans, evs):
+                c, _ = B.dm_match(ctx.h, p, B.DM_COUNT)
+                e.record(stream)
+                emb += c
+                launches += B.dm_get_stats(ctx.h)["kernel_launches"]
+            torch.cuda.synchronize()
+            done = [e0.elapsed_time(e) for e in evs]
+            ms.append(done[-1])
+        sync_ranks()
+        return {"value": emb * len(ms) / (sum(ms) / 1e3), "ms_per_step": sum(ms) / len(ms),
+                "p50_ms_per_pattern": pct(done, 0.5), "p99_ms_per_pattern": pct(done, 0.99),
+                "latency": "completion time of each pattern from the start of the step, all arriving together "
+                           "and served one by one (last step, CUDA events)",
+                "embeddings_per_step": emb}, launches, ms
+
+    def batched(plans):
+        for _ in range(args.warmup):
+            counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches = 0
+        sync_ranks()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -529,9 +654,7 @@ def run_c4(args):
             counts, _ = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
             ev[i][1].record(stream)
             launches += B.dm_get_stats(ctx.h)["kernel_launches"]
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        sync_ranks()
         ms = [a.elapsed_time(b) for a, b in ev]
         emb = int(counts.sum())
         done = list(B.dm_batch_latency(ctx.h, len(plans)))  # completion of each pattern, last step
@@ -541,21 +664,8 @@ def run_c4(args):
                 "launch": B.dm_batch_config(ctx.h), "embeddings_per_step": emb}, launches, ms
 
     paper_plans, paper_plan_ms = make(B.DM_ORDER_PAPER)
-    lat, plain_emb = [], 0
-    for p in paper_plans:  # plain form
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        c, _ = B.dm_match(ctx.h, p, B.DM_COUNT)
-        lat.append(1e3 * (time.perf_counter() - s0))
-        plain_emb += c
-    done, acc = [], 0.0
-    for x in lat:  # the same arrival model as the batch: all patterns at once, served in order
-        acc += x
-        done.append(acc)
-    plain = {"value": plain_emb / (sum(lat) / 1e3), "ms_total": sum(lat), "p50_ms_per_pattern": pct(done, 0.5),
-             "p99_ms_per_pattern": pct(done, 0.99),
-             "latency": "completion time of each pattern when all arrive together and are served one by one",
-             "p50_service_ms": pct(lat, 0.5), "p99_service_ms": pct(lat, 0.99), "plan_ms_total": paper_plan_ms}
+    plain_paper, _, _ = plain(paper_plans)
+    plain_paper["plan_ms_total"] = paper_plan_ms
     bat, _, _ = batched(paper_plans)
     # the same candidate plans the learned planner weighs, chosen by the independence heuristic's
     # cost instead of the model's: what the model adds over the plain cardinality heuristic
@@ -580,42 +690,49 @@ def run_c4(args):
     learned_plans = B.dm_plan_batch(ctx.h, gid, [(p.n, p.row_ptr, p.col_idx) for p in pats],
                                     order=B.DM_ORDER_LEARNED)
     learned_batch_plan_ms = 1e3 * (time.perf_counter() - t0)
+    plain_learned, _, _ = plain(learned_plans)
+    plain_learned["plan_ms_total"] = learned_plan_ms
     with ClockSampler(local) as clk:
         bl, launches, ms = batched(learned_plans)
     bl["plan_ms_total"] = learned_plan_ms
     bl["plan_batch_ms_total"] = learned_batch_plan_ms
-    assert bl["embeddings_per_step"] == bat["embeddings_per_step"] == bh["embeddings_per_step"] == plain_emb
+    assert (bl["embeddings_per_step"] == bat["embeddings_per_step"] == bh["embeddings_per_step"]
+            == plain_paper["embeddings_per_step"] == plain_learned["embeddings_per_step"])
     ms_job, emb_job = combine_ranks(sum(ms), bl["embeddings_per_step"] * len(ms))  # all ranks' patterns
+
+    def ratio(a, b):
+        return {"embeddings_per_s": a["value"] / b["value"],
+                "p99_latency": b["p99_ms_per_pattern"] / a["p99_ms_per_pattern"]}
     line = {"metric": METRIC, "value": emb_job / (ms_job / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_job / len(ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl_name(args), "patterns_per_step": len(pats),
+            "config": {"workload": wl_name(args, "c4"), "patterns_per_step": len(pats),
                        "embeddings_per_step": bl["embeddings_per_step"], "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "plain": plain, "batched": bat, "batched_heuristic_choice": bh, "batched_learned": bl, "model": model,
-            "gpu_launches": launches, "clocks": clk.summary(), "e2e": None}
-    if rank == 0 and world == 1 and not args.no_cpu:
+            "plain_paper": plain_paper, "plain_learned": plain_learned, "batched_paper": bat,
+            "batched_heuristic_choice": bh, "batched_learned": bl,
+            # the persistent launch's own gain (same learned plans) and the whole form's gain
+            "batched_learned_over_plain_learned": ratio(bl, plain_learned),
+            "batched_learned_over_plain_paper": ratio(bl, plain_paper),
+            "model": model, "gpu_launches": launches, "clocks": clk.summary(), "e2e": None}
+    if emit and rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(g, pats, count_only=True)
     for p in paper_plans + heur_plans + learned_plans:
         B.dm_plan_free(p)
     ctx.close()
-    if rank == 0:
+    if emit and rank == 0:
         print(json.dumps(line))
-    return 0
+    return line
 
 
-def run_c5(args):
+def run_c5(args, emit: bool = True):
     """Serving: requests arrive as a Poisson process and are answered by the library's server
     (continuous admission onto 8 slots by projected join memory); per rate, completed
-    requests/s, p50/p99 latency (arrival to answer) and the fraction rejected by the caps."""
+    requests/s, p50/p99 latency (arrival to answer), the fraction rejected by the caps, and how
+    many requests overlapped another on the GPU timeline."""
     import numpy as np
     import threading as th
-    import torch
-    rank, _, local = dist_env()
-    torch.cuda.set_device(local)
-    from paper_2508_21287_gb300 import build
-    build.build()
-    from paper_2508_21287_gb300 import binding as B
+    B, rank, _, local = init_run()
     from paper_2508_21287_gb300 import inputs as I
     graphs = [I.lognormal_weights(I.heavy_hex(4, 6), seed=11), I.lognormal_weights(I.grid(32, 32), seed=12),
               I.lognormal_weights(I.random_regular3(2048, 13), seed=13)]
@@ -640,9 +757,13 @@ def run_c5(args):
             B.dm_server_set_model(srv, weights)
         for gi, p in make(900000)[:60]:  # warm-up: motif tables and indices in every slot
             B.dm_server_wait(srv, B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10), 10, p.n)
+        st0 = B.dm_server_stats_get(srv)
         sweep = sweep_rates(srv, gids)
+        st1 = B.dm_server_stats_get(srv)
         B.dm_server_destroy(srv)
-        return sweep
+        done = st1["completed"] - st0["completed"]
+        return sweep, {"max_running": st1["max_running"], "overlapped": st1["overlapped"] - st0["overlapped"],
+                       "completed": done}
 
     def sweep_rates(srv, gids):
         sweep = []
@@ -675,8 +796,8 @@ def run_c5(args):
         return sweep
 
     with ClockSampler(local) as clk:
-        sweep = serve(B.DM_ORDER_LEARNED)
-        sweep_paper = serve(B.DM_ORDER_PAPER)
+        sweep, ov = serve(B.DM_ORDER_LEARNED)
+        sweep_paper, _ = serve(B.DM_ORDER_PAPER)
     top = sweep[-1]
     line = {"metric": "requests/sec", "value": top["completed_per_s"], "unit": "requests/s", "n_gpus": 1,
             "steps": len(rates), "warmup": 1, "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True,
@@ -685,10 +806,12 @@ def run_c5(args):
                        "pool_bytes": 32 << 30, "parallelism": "replicas"},
             "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "rejected_fraction": top["rejected"],
             "order": "learned", "sweep": sweep, "sweep_paper_order": sweep_paper,
+            "overlap": {**ov, "note": "over the rate sweep, learned order: requests whose device interval "
+                                      "(CUDA events on their slot's stream) intersected another's"},
             "model": {"samples": n_samples, "train_s": train_s}, "clocks": clk.summary(), "e2e": None}
-    if rank == 0:
+    if emit and rank == 0:
         print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_motifs(args):
@@ -698,11 +821,7 @@ def run_motifs(args):
     20-vertex patterns, greedy order (the paper's largest-motif-first order streams hundreds of
     millions of rows on some 60-vertex patterns), count + checksum, per motif set."""
     import torch
-    rank, _, local = dist_env()
-    torch.cuda.set_device(local)
-    from paper_2508_21287_gb300 import build
-    build.build()
-    from paper_2508_21287_gb300 import binding as B
+    B, rank, _, local = init_run()
     from paper_2508_21287_gb300 import inputs as I
     studies = [("heavy-hex 25x34", I.heavy_hex(25, 34), 60,
                 [("M2,M4 (preset)", [4, 2]), ("M2,M4-1", [201, 2]), ("M2,M12-O", [112, 2]),
@@ -755,11 +874,13 @@ def main():
     if args.workload in ("c5", "motifs") and args.impl != "reference" and dist_env()[1] > 1 and dist_env()[0] != 0:
         return 0  # one-GPU studies: under torchrun rank 0 alone runs and reports them (n_gpus 1)
     if args.workload == "c5" and args.impl != "reference":
-        return run_c5(args)
+        run_c5(args)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
-        return run_c4(args)
+        run_c4(args)
+        return 0
     if args.workload == "motifs":
         return run_motifs(args)
     return run_ours(args)

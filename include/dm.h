@@ -89,12 +89,17 @@ typedef struct dm_plan_opts {
 
 /* ------------------------------------------------------------------ context --------- */
 
-/* Create a context on CUDA device `device`. mem_budget_bytes bounds the device memory the
- * intermediate tables of one dm_match may hold (0 = half of the free memory at creation);
- * larger results are streamed in chunks (depth-first over the join steps). */
+/* Create a context on CUDA device `device`. No counterpart in the paper (its tables live in a
+ * dataframe library's memory pool): a context owns a stream, counters and the device memory
+ * of its graphs and tables. mem_budget_bytes bounds the device memory the intermediate tables
+ * of one dm_match may hold (0 = half of the free memory at creation); larger results are
+ * streamed in chunks (depth-first over the join steps). Errors: DM_E_INVAL (out NULL),
+ * DM_E_CUDA (no such device, or stream/event creation failed), DM_E_NOMEM. */
 int dm_create(dm_ctx **out, int device, uint64_t mem_budget_bytes);
 
-/* Release every graph, motif table and buffer of the context. */
+/* Release every graph, motif table and buffer of the context (no counterpart in the paper).
+ * Waits for the context's stream first. The handle is invalid afterwards. DM_E_INVAL for
+ * NULL. */
 int dm_destroy(dm_ctx *ctx);
 
 /* Run subsequent device work on `stream` (a cudaStream_t; NULL = the context's own stream). */
@@ -107,9 +112,13 @@ int dm_set_budget(dm_ctx *ctx, uint64_t mem_budget_bytes);
 
 /* Load a data graph (Sec. 3.1). edge_err (nullable) is aligned with col_idx: the error of
  * the directed slot, equal on both directions of an edge. qubit_err (nullable) has n
- * entries. The graph, its adjacency bitmap and its Res(M2) table (Sec. 3.3) stay resident
- * on the device until dm_destroy. Errors: DM_E_INVAL for malformed CSR,
- * DM_E_DISCONNECTED if G_d is not connected. */
+ * entries. Weights must be finite (NaN or infinity: DM_E_INVAL). Error rates are >= 0 in the
+ * paper's use (Sec. 5.4); negative weights are accepted, but then dm_score_topk cannot prune
+ * rows by their partial score and keeps every row until the end (slower, same answer).
+ * The graph, its adjacency bitmap and its Res(M2) table (Sec. 3.3) stay resident
+ * on the device until dm_destroy. Errors: DM_E_INVAL for malformed CSR or weights,
+ * DM_E_DISCONNECTED if G_d is not connected; on any error no graph is registered and nothing
+ * stays allocated. */
 int dm_load_data_graph(dm_ctx *ctx, int32_t n_vertices, const int32_t *row_ptr,
                        const int32_t *col_idx, const float *edge_err, const float *qubit_err,
                        dm_graph *out);
@@ -144,6 +153,8 @@ int dm_motif_table(dm_ctx *ctx, dm_graph g, int32_t motif_id, int32_t *out_rows,
 int dm_plan(dm_ctx *ctx, dm_graph g, int32_t n_p, const int32_t *p_row_ptr,
             const int32_t *p_col_idx, const dm_plan_opts *opts, dm_plan_t **out);
 
+/* Release a plan made by dm_plan, dm_plan_batch or dm_plan_candidates (no counterpart in
+ * the paper; host memory only, no device work). NULL is accepted. */
 void dm_plan_free(dm_plan_t *plan);
 
 /* dm_plan (the decomposition and join order of Sec. 3.2) for n_patterns patterns at once,
@@ -211,8 +222,11 @@ int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void 
              uint64_t *out_count, uint64_t *out_checksum);
 
 /* Count + checksum for n_plans plans on the same data graph in one persistent launch
- * (captured in a CUDA graph). out_counts / out_checksums have n_plans entries. Results are
- * identical to dm_match(DM_COUNT) on each plan alone. */
+ * (captured in a CUDA graph). Each plan is Alg. 1 (Sec. 3.2) as in dm_match; running many
+ * plans in one launch has no counterpart in the paper (it answers one pattern at a time).
+ * mode must be DM_COUNT (else DM_E_INVAL). out_counts / out_checksums have n_plans entries
+ * (caller-owned host arrays). Results are identical to dm_match(DM_COUNT) on each plan alone.
+ * Errors: DM_E_INVAL (plans on different graphs, NULL arguments), DM_E_NOMEM, DM_E_CUDA. */
 int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, int mode,
                    uint64_t *out_counts, uint64_t *out_checksums);
 
@@ -239,7 +253,10 @@ int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor, double hea
 
 /* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,
  * row) key, in that order. out_rows: k x n_p int32 host buffer; out_scores: k floats
- * (nullable); out_n receives the number written. Needs edge weights (DM_E_INVAL if none). */
+ * (nullable); out_n receives the number written. Needs edge weights (DM_E_INVAL if none).
+ * When every weight of the graph is >= 0, rows whose partial score already exceeds the
+ * current k-th best are dropped inside the joins (a partial score is then a lower bound of
+ * the full one); with a negative weight nothing is pruned. The answer is the same either way. */
 int dm_score_topk(dm_ctx *ctx, const dm_plan_t *plan, int32_t k, int32_t *out_rows,
                   float *out_scores, int32_t *out_n);
 
@@ -326,6 +343,9 @@ typedef struct dm_server_opts {
 typedef struct dm_server_stats {
     int64_t submitted, completed, rejected, failed, queued, in_flight;
     uint64_t pool_used, pool_total;
+    int64_t max_running;  /* most requests inside their device work at one time (host view) */
+    int64_t overlapped;   /* requests whose device interval (CUDA events on the slot's stream,
+                             timed against one reference event) intersected another request's */
 } dm_server_stats;
 
 int dm_server_create(dm_server **out, int device, const dm_server_opts *opts);
@@ -362,8 +382,9 @@ int dm_server_destroy(dm_server *s);
  * every GPU that loads the library until exit); nothing is allocated or freed.
  * Limits: n <= DM_SORT_STATIC_MAX_ROWS (else DM_E_CAPACITY), 1 <= w <= 64 (else DM_E_INVAL).
  * Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream) and the call
- * returns without waiting. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * returns without waiting. Every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, host-side); the first lookup on a device may load the
+ * library's device code there, so make the first call on each device before any stream
  * capture. All calls share the one array: calls whose work overlaps on the GPU (other streams,
  * other host threads) race and corrupt each other's results; serialise them. */
 #define DM_SORT_STATIC_MAX_ROWS (1 << 20)
@@ -420,6 +441,7 @@ int dm_match_topk_queries(dm_ctx *const *ctxs, const dm_graph *gids, int32_t n_c
                           float *const *out_scores, int32_t *out_n, uint64_t *out_counts,
                           uint64_t *out_checksums, int32_t *out_status, dm_stats *out_stats);
 
+/* Name of a DM_* status code, a static string (no counterpart in the paper). */
 const char *dm_strerror(int code);
 
 /* Text of the last CUDA failure seen by the context (empty if none); owned by the context. */

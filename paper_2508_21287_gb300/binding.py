@@ -64,7 +64,8 @@ class dm_server_opts(ctypes.Structure):
 class dm_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
-                ("pool_used", ctypes.c_uint64), ("pool_total", ctypes.c_uint64)]
+                ("pool_used", ctypes.c_uint64), ("pool_total", ctypes.c_uint64),
+                ("max_running", ctypes.c_int64), ("overlapped", ctypes.c_int64)]
 
 
 DM_CHUNK_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),

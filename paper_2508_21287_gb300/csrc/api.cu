@@ -2,6 +2,8 @@
 // plans (Sec. 3.2), the chunked join executor (Alg. 1), canonical output, top-k scoring.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -54,6 +56,9 @@ struct DevGraph {
   int32_t adj_words = 0;
   double avg_deg = 0;
   int32_t max_deg = 0;
+  // every edge and vertex weight is >= 0, so a partial score never exceeds a full one and
+  // top-k may drop rows whose partial score is above the current k-th best
+  bool nonneg_weights = true;
   std::map<int, DevTable> motifs;
   std::map<std::tuple<int, int, int, int>, Index> indices;  // (motif, key position 0, 1, sort-merge)
 };
@@ -1662,6 +1667,28 @@ void finish_stats(dm_ctx *c, std::chrono::steady_clock::time_point t0) {
 
 }  // namespace
 
+// Everything a data graph holds on the device: CSR, weights, bitmap, motif tables, indices.
+void free_graph(dm_ctx *c, DevGraph *g) {
+  if (!g) return;
+  for (auto &kv : g->motifs) {
+    dfree(c, kv.second.rows);
+    if (kv.second.score) dfree(c, kv.second.score);
+  }
+  for (auto &kv : g->indices) {
+    dfree(c, kv.second.rows);
+    if (kv.second.score) dfree(c, kv.second.score);
+    if (kv.second.offsets) dfree(c, kv.second.offsets);
+    if (kv.second.slots) dfree(c, kv.second.slots);
+    if (kv.second.keys) dfree(c, kv.second.keys);
+  }
+  cudaFree(g->row_ptr);
+  cudaFree(g->col_idx);
+  cudaFree(g->eerr);
+  cudaFree(g->qerr);
+  cudaFree(g->adj);
+  delete g;
+}
+
 // =================================================================== C ABI ==============
 extern "C" {
 
@@ -1751,26 +1778,7 @@ int dm_destroy(dm_ctx *c) {
   cudaStreamSynchronize(c->stream);
   batch_release(c, c->batch);
   c->batch = nullptr;
-  for (DevGraph *g : c->graphs) {
-    if (!g) continue;
-    for (auto &kv : g->motifs) {
-      dfree(c, kv.second.rows);
-      if (kv.second.score) dfree(c, kv.second.score);
-    }
-    for (auto &kv : g->indices) {
-      dfree(c, kv.second.rows);
-      if (kv.second.score) dfree(c, kv.second.score);
-      if (kv.second.offsets) dfree(c, kv.second.offsets);
-      if (kv.second.slots) dfree(c, kv.second.slots);
-      if (kv.second.keys) dfree(c, kv.second.keys);
-    }
-    cudaFree(g->row_ptr);
-    cudaFree(g->col_idx);
-    cudaFree(g->eerr);
-    cudaFree(g->qerr);
-    cudaFree(g->adj);
-    delete g;
-  }
+  for (DevGraph *g : c->graphs) free_graph(c, g);
   cudaStreamSynchronize(c->stream);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->d_ctr_steps) cudaFree(c->d_ctr_steps);
@@ -1801,6 +1809,16 @@ int dm_load_data_graph_ex(dm_ctx *c, int32_t n, const int32_t *row_ptr, const in
   cudaSetDevice(c->device);
   HostCSR h;
   RET(validate_csr(n, row_ptr, col_idx, edge_err, &h));
+  bool nonneg = true;  // weights must be finite; negative ones are kept but switch off pruning
+  for (float e : h.ee) {
+    if (!std::isfinite(e)) return DM_E_INVAL;
+    nonneg &= e >= 0.f;
+  }
+  if (qubit_err)
+    for (int32_t v = 0; v < n; v++) {
+      if (!std::isfinite(qubit_err[v])) return DM_E_INVAL;
+      nonneg &= qubit_err[v] >= 0.f;
+    }
   if (score_form == DM_SCORE_LOG_FIDELITY) {  // error rates must leave a positive fidelity
     for (float e : h.ee)
       if (!(e >= 0.f && e < 1.f)) return DM_E_INVAL;
@@ -1816,6 +1834,7 @@ int dm_load_data_graph_ex(dm_ctx *c, int32_t n, const int32_t *row_ptr, const in
   for (int32_t u = 0; u < n; u++) md = std::max(md, h.rp[u + 1] - h.rp[u]);
   g->max_deg = md;
   g->avg_deg = (double)g->nnz / n;
+  g->nonneg_weights = nonneg;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) return DM_E_NOMEM;
     if (bytes && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return DM_E_CUDA;
@@ -1838,10 +1857,15 @@ int dm_load_data_graph_ex(dm_ctx *c, int32_t n, const int32_t *row_ptr, const in
       r = DM_E_CUDA;
   }
   if (r == DM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) r = DM_E_CUDA;
+  if (r == DM_OK) r = ensure_motif(c, g, 2);
+  if (r != DM_OK) {  // a graph that failed to load is neither registered nor kept
+    cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+    free_graph(c, g);
+    return r;
+  }
   c->graphs.push_back(g);
   *out = (dm_graph)(c->graphs.size() - 1);
-  if (r == DM_OK) r = ensure_motif(c, g, 2);
-  if (r != DM_OK) return r;
   return DM_OK;
 }
 
@@ -2296,7 +2320,9 @@ int dm_score_topk(dm_ctx *c, const dm_plan_t *pl, int32_t k, int32_t *out_rows, 
   TopkSink sink;
   sink.g = g;
   sink.k = k;
-  sink.prune_ptr = &ex.prune;
+  // bound pruning is exact only when no weight is negative (a partial score is then a lower
+  // bound of every completion's score)
+  sink.prune_ptr = g->nonneg_weights ? &ex.prune : nullptr;
   ex.sink = &sink;
   int r = ex.run();
   if (r == DM_OK) {

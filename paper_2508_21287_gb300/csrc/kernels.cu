@@ -80,7 +80,7 @@ cudaError_t launch_bitmap(const int32_t *row_ptr, const int32_t *col_idx, int32_
 }
 
 // ------------------------------------------------------------------ scan ---------------
-constexpr int SCAN_BLK = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_BLK * SCAN_ITEMS;
+static_assert(SCAN_TILE == SCAN_BLK * SCAN_ITEMS, "scan tile");
 
 template <class T>
 __global__ void __launch_bounds__(SCAN_BLK) k_scan_tile(const T *in, int64_t *out, int64_t n, int64_t *sums) {
@@ -137,12 +137,6 @@ __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *sums_scan, in
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums_scan[nb];
 }
 
-int64_t scan_tmp_elems(int64_t n) {
-  int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-  if (nb <= 1) return 1;
-  return 2 * nb + 1 + scan_tmp_elems(nb);
-}
-
 template <class T>
 static cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
@@ -170,9 +164,7 @@ cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, c
 }
 
 // ------------------------------------------------------------------ radix sort ---------
-constexpr int RS_BLK = 256, RS_ITEMS = 8, RS_TILE = RS_BLK * RS_ITEMS;
-
-int64_t radix_hist_elems(int64_t n) { return 256 * ((n + RS_TILE - 1) / RS_TILE); }
+static_assert(RS_TILE == RS_BLK * RS_ITEMS, "radix tile");
 
 __global__ void __launch_bounds__(RS_BLK) k_radix_hist(const uint32_t *keys, int64_t stride, const int32_t *perm,
                                                        int64_t n, int shift, int64_t *hist, int nb) {

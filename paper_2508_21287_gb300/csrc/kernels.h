@@ -54,15 +54,21 @@ cudaError_t launch_bitmap(const int32_t *row_ptr, const int32_t *col_idx, int32_
                           int32_t words, unsigned long long *adj, cudaStream_t s);
 
 // Exclusive scan of n values into out[0..n], out[n] = total. tmp must hold
-// scan_tmp_elems(n) int64 values.
-int64_t scan_tmp_elems(int64_t n);
+// scan_tmp_elems(n) int64 values: per level of the scan over tile sums, the sums and their scan.
+constexpr int SCAN_BLK = 256, SCAN_ITEMS = 8, SCAN_TILE = 2048;
+constexpr int64_t scan_tmp_elems(int64_t n) {
+  return (n + SCAN_TILE - 1) / SCAN_TILE <= 1
+             ? 1
+             : 2 * ((n + SCAN_TILE - 1) / SCAN_TILE) + 1 + scan_tmp_elems((n + SCAN_TILE - 1) / SCAN_TILE);
+}
 cudaError_t scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 
 // One stable LSD pass: perm_out = perm_in stably sorted by the 8-bit digit
 // (key >> shift) & 255 of key = keys[perm_in[i] * stride]. hist must hold
 // radix_hist_elems(n) int64, tmp scan_tmp_elems(radix_hist_elems(n)).
-int64_t radix_hist_elems(int64_t n);
+constexpr int RS_BLK = 256, RS_ITEMS = 8, RS_TILE = 2048;
+constexpr int64_t radix_hist_elems(int64_t n) { return 256 * ((n + RS_TILE - 1) / RS_TILE); }
 cudaError_t radix_pass(const uint32_t *keys, int64_t stride, const int32_t *perm_in,
                        int32_t *perm_out, int64_t n, int shift, int64_t *hist, int64_t *hist_scan,
                        int64_t *tmp, cudaStream_t s);

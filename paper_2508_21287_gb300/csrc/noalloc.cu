@@ -12,8 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "../../include/dm.h"
 #include "kernels.h"
 
@@ -21,30 +19,28 @@ namespace {
 
 constexpr int64_t kMaxRows = DM_SORT_STATIC_MAX_ROWS;
 constexpr int32_t kMaxWidth = 64;
-constexpr int64_t kHist = 256 * ((kMaxRows + 2047) / 2048);  // radix_hist_elems(kMaxRows)
-constexpr int64_t kScanTmp = 2 * ((kHist + 2047) / 2048) + 2;  // >= scan_tmp_elems(kHist)
+constexpr int64_t kHist = dmk::radix_hist_elems(kMaxRows);
+constexpr int64_t kScanTmp = dmk::scan_tmp_elems(kHist);
+// the radix passes of n <= kMaxRows rows use at most these many histogram and scan words
+static_assert(dmk::radix_hist_elems(kMaxRows) <= kHist, "histogram region too small");
+static_assert(dmk::scan_tmp_elems(dmk::radix_hist_elems(kMaxRows)) <= kScanTmp, "scan region too small");
+static_assert(kMaxRows % 2 == 0, "two int32 permutations per pair of 8-byte words");
 // layout in 8-byte words: perm A | perm B | hist | hist scan (+1) | scan temporaries
 constexpr int64_t kPermWords = kMaxRows / 2;
 constexpr int64_t kScratchWords = 2 * kPermWords + kHist + (kHist + 1) + kScanTmp;
 
 static __device__ __align__(256) unsigned long long g_sort_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned long long *g_ptr[kMaxDevices] = {};
-
-// Device address of g_sort_scratch on the current device, looked up once per device.
+// Device address of g_sort_scratch in the current device's context. It is looked up on every
+// call (a host-side lookup, no device work): an address cached across calls would go stale if
+// the context were reset and the module loaded again at another address.
 int scratch_for_current_device(unsigned long long **out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DM_E_CUDA;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
-    if (e != cudaSuccess || !p) return DM_E_CUDA;
-    g_ptr[dev] = (unsigned long long *)p;
-  }
-  *out = g_ptr[dev];
+  if (cudaGetDevice(&dev) != cudaSuccess) return DM_E_CUDA;
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+  if (e != cudaSuccess || !p) return DM_E_CUDA;
+  *out = (unsigned long long *)p;
   return DM_OK;
 }
 

@@ -8,6 +8,12 @@
 // arrival order as slots and pool memory free up; a request whose projection alone exceeds
 // the pool, or whose projected or actual candidate rows exceed the work cap, is answered
 // with DM_E_CAPACITY.
+//
+// Overlap on the device is measured, not assumed: every slot runs on a stream of its own and
+// brackets each request's device work with two CUDA events; their times against one reference
+// event give each request's interval on the GPU timeline, and a request whose interval
+// intersects that of another request counts as overlapped.
+#include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
@@ -59,7 +65,13 @@ struct dm_server {
   uint64_t pool_total = 0, pool_used = 0;
   bool stop = false;
   int64_t in_flight = 0;
+  int64_t running = 0;  // requests inside their device work right now
   dm_server_stats st{};
+  // device timeline: one stream and two events per slot, one reference event for all
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev_start, ev_end;
+  cudaEvent_t ev_ref = nullptr;
+  std::deque<std::pair<double, double>> recent;  // device intervals of the latest requests (ms)
 };
 
 namespace {
@@ -126,10 +138,26 @@ void worker(dm_server *s, int slot) {
       reserved = true;
     }
     auto start = Clock::now();
+    double dev_a = -1, dev_b = -1;
     if (rc == DM_OK) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->running++;
+        s->st.max_running = std::max(s->st.max_running, s->running);
+      }
       res.rows.assign((size_t)rq.k * rq.n_p, 0);
       res.scores.assign(rq.k, 0.f);
+      const bool timed = cudaEventRecord(s->ev_start[slot], s->streams[slot]) == cudaSuccess;
       rc = dm_score_topk(c, pl, rq.k, res.rows.data(), res.scores.data(), &res.n);
+      float a = 0.f, b = 0.f;
+      if (timed && cudaEventRecord(s->ev_end[slot], s->streams[slot]) == cudaSuccess &&
+          cudaEventSynchronize(s->ev_end[slot]) == cudaSuccess &&
+          cudaEventElapsedTime(&a, s->ev_ref, s->ev_start[slot]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, s->ev_ref, s->ev_end[slot]) == cudaSuccess) {
+        dev_a = a;
+        dev_b = b;
+      }
+      cudaGetLastError();
     }
     auto end = Clock::now();
     if (pl) dm_plan_free(pl);
@@ -140,6 +168,14 @@ void worker(dm_server *s, int slot) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (reserved) s->pool_used -= need;
+      if (reserved) s->running--;
+      if (dev_b > dev_a && dev_a >= 0) {
+        bool ov = false;
+        for (auto &iv : s->recent) ov |= iv.first < dev_b && dev_a < iv.second;
+        if (ov) s->st.overlapped++;
+        s->recent.emplace_back(dev_a, dev_b);
+        if (s->recent.size() > 4 * s->slots.size()) s->recent.pop_front();
+      }
       s->in_flight--;
       if (rc == DM_OK) s->st.completed++;
       else if (rc == DM_E_CAPACITY) s->st.rejected++;
@@ -165,6 +201,13 @@ int dm_server_create(dm_server **out, int device, const dm_server_opts *opts) {
   s->opts = o;
   if (o.motifs && o.n_motifs > 0) s->motifs.assign(o.motifs, o.motifs + o.n_motifs);
   s->opts.motifs = nullptr;
+  cudaSetDevice(device);
+  if (cudaEventCreate(&s->ev_ref) != cudaSuccess) {
+    cudaGetLastError();
+    s->ev_ref = nullptr;
+    dm_server_destroy(s);
+    return DM_E_CUDA;
+  }
   for (int i = 0; i < o.n_slots; i++) {
     dm_ctx *c = nullptr;
     int rc = dm_create(&c, device, 0);
@@ -173,6 +216,25 @@ int dm_server_create(dm_server **out, int device, const dm_server_opts *opts) {
       return rc;
     }
     s->slots.push_back(c);
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+        cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      if (st) cudaStreamDestroy(st);
+      if (a) cudaEventDestroy(a);
+      dm_server_destroy(s);
+      return DM_E_CUDA;
+    }
+    s->streams.push_back(st);
+    s->ev_start.push_back(a);
+    s->ev_end.push_back(b);
+    dm_set_stream(c, st);
+  }
+  if (cudaEventRecord(s->ev_ref, s->streams[0]) != cudaSuccess || cudaEventSynchronize(s->ev_ref) != cudaSuccess) {
+    cudaGetLastError();
+    dm_server_destroy(s);
+    return DM_E_CUDA;
   }
   uint64_t budget = o.mem_budget_bytes;
   if (budget == 0) budget = 16ull << 30;
@@ -268,6 +330,10 @@ int dm_server_destroy(dm_server *s) {
   s->cv_done.notify_all();
   for (auto &t : s->threads) t.join();
   for (dm_ctx *c : s->slots) dm_destroy(c);
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : s->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->ev_end) cudaEventDestroy(e);
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
   delete s;
   return DM_OK;
 }

@@ -507,3 +507,75 @@ def test_callback_cancel(ctx, B, hh):
     with pytest.raises(B.DMError) as e:
         B.dm_match(ctx.h, plan.h, B.DM_ALL, lambda r, s: 1)
     assert e.value.code == B.DM_E_CANCELLED
+
+
+# ------------------------------------------------------------------ weight preconditions ---
+def _with_negative_edges(g, frac_seed: int, value: float = -0.02):
+    """A copy of g whose every third undirected edge (in a seeded order) weighs `value`."""
+    import copy
+    h = copy.deepcopy(g)
+    edges = h.edges()
+    rng = I.SplitMix64(frac_seed)
+    neg = {e for e in edges if rng.below(3) == 0}
+    for u in range(h.n):
+        for k in range(h.row_ptr[u], h.row_ptr[u + 1]):
+            v = int(h.col_idx[k])
+            if (min(u, v), max(u, v)) in neg:
+                h.edge_err[k] = value
+    return h
+
+
+@pytest.mark.parametrize("chunk_rows", [0, 64])
+def test_negative_weights_topk_is_exact(ctx, B, chunk_rows):
+    # Sec. 5.4 ranks layouts by a sum of weights. With a negative weight a row's partial score
+    # is no lower bound of its final score, so the joins must not drop rows by partial score;
+    # the streamed plan (chunk_rows 64: many chunks, the k-th best known early) is the case
+    # where a pruning join would lose rows. FP32 sums are compared with the FP64 oracle within
+    # 1e-5 of the sum of the terms' magnitudes (the bound of a recursive sum of mixed signs).
+    base = I.lognormal_weights(I.heavy_hex(3, 4), seed=21, qubits=False)
+    g = _with_negative_edges(base, 99)
+    assert (g.edge_err < 0).any() and (g.edge_err > 0).any()
+    gid = ctx.load(g)
+    gabs = _with_negative_edges(base, 99, value=0.02)
+    for p in (I.path(9), I.sub_patch(g, 14, 3)):
+        allrows = oracle.enumerate(g, p).rows
+        s = oracle.scores(g, p, allrows)
+        mag = oracle.scores(gabs, p, allrows)  # sum of |terms| per row
+        for k in (1, 10, 50):
+            plan = ctx.plan(gid, p, chunk_rows=chunk_rows)
+            rows, scores = plan.topk(k)
+            m = min(k, len(allrows))
+            assert rows.shape == (m, p.n)
+            pos = {tuple(r): i for i, r in enumerate(allrows.tolist())}
+            idx = [pos.get(tuple(r)) for r in rows.tolist()]
+            assert None not in idx and len(set(idx)) == m
+            tol = RTOL * mag[idx]
+            assert np.all(np.abs(scores - s[idx]) <= tol)
+            order = oracle.topk(allrows, s, k)
+            band = RTOL * mag.max()
+            assert np.all(np.abs(scores - s[order]) <= band)
+            kth = s[order[-1]]
+            must = set(np.nonzero(s < kth - band)[0].tolist())
+            assert must <= set(idx)
+
+
+def test_non_finite_weights_rejected_and_not_registered(ctx, B):
+    # weights must be finite; a graph that fails to load takes no handle and holds nothing
+    g = I.lognormal_weights(I.heavy_hex(2, 3), seed=5)
+    gid0 = ctx.load(g)
+    for bad in (np.nan, np.inf, -np.inf):
+        h = I.lognormal_weights(I.heavy_hex(2, 3), seed=5)
+        h.edge_err = h.edge_err.copy()
+        h.edge_err[3] = bad
+        with pytest.raises(B.DMError) as e:
+            ctx.load(h)
+        assert e.value.code == B.DM_E_INVAL
+    q = I.lognormal_weights(I.heavy_hex(2, 3), seed=5, qubits=True)
+    q.qubit_err = q.qubit_err.copy()
+    q.qubit_err[0] = np.nan
+    with pytest.raises(B.DMError):
+        ctx.load(q)
+    gid1 = ctx.load(g)
+    assert gid1 == gid0 + 1
+    r = check_all(ctx, gid1, g, I.path(6))
+    assert r.count > 0
