@@ -230,12 +230,16 @@ int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void 
 int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, int mode,
                    uint64_t *out_counts, uint64_t *out_checksums);
 
-/* Launch shape of the last dm_match_batch, as picked by the autotuner: tile rows per CTA
- * step, root rows per work item, CTAs of the persistent launch, and how many plans (those
- * whose predicted largest table exceeds heavy_rows) ran step by step over the whole GPU
- * after the persistent launch instead of inside it. */
+/* Configuration of the last dm_match_batch, as picked by the autotuner (no counterpart in
+ * the paper): tile rows per CTA step, root rows per work item, CTAs of the persistent launch,
+ * how many plans (those whose predicted largest table exceeds heavy_rows) ran step by step
+ * over the whole GPU after the persistent launch instead of inside it, the block shape
+ * (threads per CTA, 128 or 256, and resident CTAs per SM) and the load factor of the two-key
+ * hash indices the joins probed. Every output pointer may be NULL. DM_E_INVAL if the context
+ * has run no batch. */
 int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid,
-                    int32_t *n_stepwise, double *heavy_rows);
+                    int32_t *n_stepwise, double *heavy_rows, int32_t *threads_per_cta,
+                    int32_t *ctas_per_sm, double *hash_load_factor);
 
 /* Completion time of each plan of the last dm_match_batch (all plans taken to arrive
  * together), in ms: for plans in the persistent launch, from the launch's start to the end
@@ -243,13 +247,20 @@ int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_
  * start of the call to their end (host clock). n must equal that call's n_plans. */
 int dm_batch_latency(dm_ctx *ctx, double *out_ms, int32_t n);
 
-/* Tuning knobs: autotune (1 = time the candidate launch shapes and the split between the
- * persistent launch and step-by-step execution on the first dm_match_batch of a new set of
- * plans, and keep the fastest), hash_load_factor (fill of two-key hash indices,
- * 0 < f <= 0.95; changing it rebuilds those indices; plans made before must be made again),
+/* Tuning knobs: autotune (1 = on the first dm_match_batch of a new set of plans, time the
+ * candidate configurations and keep the fastest: tile rows x root chunk, the split between
+ * the persistent launch and step-by-step execution, the block shape, then the two-key hash
+ * load factor among 0.25, 0.5 and 0.75, a coordinate search; the chosen load factor stays
+ * the context's for later calls), hash_load_factor (fill of two-key hash indices,
+ * 0 < f <= 0.95; changing it drops those indices, which are rebuilt when a plan next runs),
  * heavy_rows (without autotuning: plans whose predicted largest table exceeds it run step by
  * step; <= 0 = none). */
 int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor, double heavy_rows);
+
+/* Block shape of dm_match_batch when autotuning is off (no counterpart in the paper):
+ * threads_per_cta 128 or 256, ctas_per_sm resident CTAs per SM (0 = as many as fit).
+ * DM_E_INVAL otherwise. Takes effect at the next dm_match_batch. */
+int dm_set_batch_shape(dm_ctx *ctx, int32_t threads_per_cta, int32_t ctas_per_sm);
 
 /* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,
  * row) key, in that order. out_rows: k x n_p int32 host buffer; out_scores: k floats

@@ -112,7 +112,9 @@ _SIGS = {
     "dm_last_error": (ctypes.c_char_p, [_vp]),
     "dm_decompose": (_i32, [_i32, _i32p, _i32p, _i32p, _i32, _i32, _i32p, _i32]),
     "dm_sort_rows_static": (ctypes.c_int, [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp]),
-    "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p, _i32p, ctypes.POINTER(ctypes.c_double)]),
+    "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p, _i32p, ctypes.POINTER(ctypes.c_double),
+                                       _i32p, _i32p, ctypes.POINTER(ctypes.c_double)]),
+    "dm_set_batch_shape": (ctypes.c_int, [_vp, _i32, _i32]),
     "dm_batch_latency": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
     "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "dm_model_init": (ctypes.c_int, [_vp, _u64]),
@@ -453,10 +455,17 @@ def dm_match_batch(ctx, plans, mode: int = DM_COUNT):
 
 def dm_batch_config(ctx) -> dict:
     tr, ch, gr, nh, hv = _i32(), _i64(), _i32(), _i32(), ctypes.c_double()
+    th, cps, lf = _i32(), _i32(), ctypes.c_double()
     _check(_lib.dm_batch_config(ctx, ctypes.byref(tr), ctypes.byref(ch), ctypes.byref(gr), ctypes.byref(nh),
-                                ctypes.byref(hv)), "dm_batch_config", ctx)
+                                ctypes.byref(hv), ctypes.byref(th), ctypes.byref(cps), ctypes.byref(lf)),
+           "dm_batch_config", ctx)
     return {"tile_rows": tr.value, "root_chunk": ch.value, "grid": gr.value, "stepwise_plans": nh.value,
-            "heavy_rows": hv.value if hv.value < 1e300 else None}
+            "heavy_rows": hv.value if hv.value < 1e300 else None, "threads_per_cta": th.value,
+            "ctas_per_sm": cps.value, "hash_load_factor": lf.value}
+
+
+def dm_set_batch_shape(ctx, threads_per_cta: int = 256, ctas_per_sm: int = 0) -> None:
+    _check(_lib.dm_set_batch_shape(ctx, int(threads_per_cta), int(ctas_per_sm)), "dm_set_batch_shape", ctx)
 
 
 def dm_batch_latency(ctx, n: int) -> np.ndarray:

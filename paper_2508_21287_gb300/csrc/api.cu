@@ -95,6 +95,7 @@ struct dm_ctx {
   int autotune = 1;
   double hash_lf = 0.5;               // load factor of two-key hash indices
   double heavy_rows = 1e300;          // plans predicted to hold more rows run step by step
+  int batch_threads = 256, batch_ctas = 0;  // block shape of dm_match_batch without autotuning
   std::vector<double> batch_latency;  // per plan, ms from the start of the last dm_match_batch
 };
 
@@ -261,15 +262,19 @@ int stable_sort_perm_by_score(dm_ctx *c, const DevTable &t, int32_t *&perm) {
   int64_t n = t.n;
   int32_t *B = nullptr;
   int64_t *hist = nullptr, *hscan = nullptr, *tmp = nullptr;
+  uint32_t *keys = nullptr;  // scores as order-preserving unsigned keys (negative scores too)
   int64_t he = dmk::radix_hist_elems(n);
+  RET(dalloc_t(c, &keys, std::max<int64_t>(1, n)));
   RET(dalloc_t(c, &B, n));
   RET(dalloc_t(c, &hist, he));
   RET(dalloc_t(c, &hscan, he + 1));
   RET(dalloc_t(c, &tmp, dmk::scan_tmp_elems(he)));
+  CK(dmk::launch_score_keys(t.score, n, keys, c->stream));
   for (int shift = 0; shift < 32; shift += 8) {
-    CK(dmk::radix_pass((const uint32_t *)t.score, 1, perm, B, n, shift, hist, hscan, tmp, c->stream));
+    CK(dmk::radix_pass(keys, 1, perm, B, n, shift, hist, hscan, tmp, c->stream));
     std::swap(perm, B);
   }
+  dfree(c, keys);
   dfree(c, B);
   dfree(c, hist);
   dfree(c, hscan);
@@ -1061,7 +1066,7 @@ int topk_table(dm_ctx *c, DevGraph *g, const DevTable &t, int64_t k, DevTable *o
 // k best of a canonically sorted table (rows in pattern order + scores), in (score, row)
 // order; consumes t.
 int topk_of_sorted(dm_ctx *c, DevGraph *g, DevTable &t, int64_t k, DevTable *out) {
-  if (k > 1024) {  // large k: select by radix on the score bits, then sort the candidates
+  if (k > 1024) {  // large k: select by radix on the order-preserving score keys, then sort the candidates
     RET(topk_table(c, g, t, k, out));
     free_table(c, t);
     return DM_OK;
@@ -1227,6 +1232,8 @@ struct BatchState {
   std::vector<int32_t> light, heavy;  // plans in the persistent launch / run step by step
   int TR = 64;
   int64_t root_chunk = 16;
+  int threads = 256;                  // block shape of the persistent launch: threads per CTA
+  int ctas_per_sm = 0;                // ... and resident CTAs per SM (0 = as many as fit)
   void *d_left0 = nullptr;            // items per plan (copied into the live counters each run)
   dmk::BatchParams prm{};
   int grid = 0;
@@ -1256,7 +1263,7 @@ void batch_release(dm_ctx *c, BatchState *b) {
 }
 
 int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
-                double heavy_rows, BatchState **out);
+                double heavy_rows, int threads, int ctas_per_sm, BatchState **out);
 
 DevGraph *get_graph(dm_ctx *c, dm_graph g) {
   if (!c || g < 0 || g >= (int)c->graphs.size()) return nullptr;
@@ -1264,13 +1271,15 @@ DevGraph *get_graph(dm_ctx *c, dm_graph g) {
 }
 
 int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n, int TR, int64_t root_chunk,
-                double heavy_rows, BatchState **out) {
+                double heavy_rows, int threads, int ctas_per_sm, BatchState **out) {
   std::unique_ptr<BatchState> b(new BatchState());
   b->key.assign(plans, plans + n);
   b->hash_lf = c->hash_lf;
   b->heavy_rows = heavy_rows;
   b->TR = TR;
   b->root_chunk = root_chunk;
+  b->threads = threads;
+  b->ctas_per_sm = ctas_per_sm;
   b->n_plans = n;
   std::vector<uint64_t> items_per(n, 0);
   std::vector<JoinArgs> args;
@@ -1344,10 +1353,10 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   P.bm_words = 0;
   if (wide && g->V <= 2048) {
     const int bw = (g->V + 63) / 64;
-    if (dmk::batch_smem_bytes(TR, ws_max, bw) <= 160 * 1024) P.bm_words = bw;
+    if (dmk::batch_smem_bytes(TR, ws_max, bw, threads) <= 160 * 1024) P.bm_words = bw;
   }
   P.n_items = (int64_t)hitems.size();
-  b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms);
+  b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms, threads, ctas_per_sm);
   while (b->grid > c->num_sms && (uint64_t)b->grid * P.cta_bytes > c->budget / 2) b->grid /= 2;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) {
@@ -1404,7 +1413,7 @@ int batch_run(dm_ctx *c, DevGraph *g, BatchState *b) {
         cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long) * (2 + 2 * n), cs);
         cudaMemcpyAsync((unsigned long long *)b->d_work + 2 + 2 * n, b->d_left0, sizeof(unsigned long long) * n,
                         cudaMemcpyDeviceToDevice, cs);
-        dmk::launch_batch(b->prm, b->grid, cs);
+        dmk::launch_batch(b->prm, b->grid, b->threads, cs);
         cudaMemcpyAsync(b->h_out, b->d_work, wbytes, cudaMemcpyDeviceToHost, cs);
         e = cudaStreamEndCapture(cs, &b->graph);
       }
@@ -1666,6 +1675,27 @@ void finish_stats(dm_ctx *c, std::chrono::steady_clock::time_point t0) {
 }
 
 }  // namespace
+
+// Change the load factor of two-key hash indices: the existing ones are dropped (after the
+// stream drains) and rebuilt at the new factor when a plan next needs them.
+void set_hash_load_factor(dm_ctx *c, double lf) {
+  if (lf == c->hash_lf) return;
+  cudaStreamSynchronize(c->stream);
+  c->hash_lf = lf;
+  for (DevGraph *g : c->graphs) {
+    if (!g) continue;
+    for (auto it = g->indices.begin(); it != g->indices.end();) {
+      if (it->second.v.nkeys == 2 && !it->second.keys) {
+        dfree(c, it->second.rows);
+        if (it->second.score) dfree(c, it->second.score);
+        dfree(c, it->second.slots);
+        it = g->indices.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+}
 
 // Everything a data graph holds on the device: CSR, weights, bitmap, motif tables, indices.
 void free_graph(dm_ctx *c, DevGraph *g) {
@@ -2216,10 +2246,11 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
     int TR = 64;
     int64_t chunk = 16;
     double heavy = c->heavy_rows;
-    if (c->autotune) {  // time the candidate launch shapes on this batch, keep the fastest
-      auto trial = [&](int tr, int64_t ch, double hv, double *ms) {
+    int threads = c->batch_threads, ctas = c->batch_ctas;
+    if (c->autotune) {  // time the candidate configurations on this batch, keep the fastest
+      auto trial = [&](int tr, int64_t ch, double hv, int th, int cps, double *ms) {
         BatchState *t = nullptr;
-        int r = batch_build(c, g, plans, n_plans, tr, ch, hv, &t);
+        int r = batch_build(c, g, plans, n_plans, tr, ch, hv, th, cps, &t);
         if (r == DM_OK) {
           auto s0 = std::chrono::steady_clock::now();
           r = batch_run(c, g, t);
@@ -2228,22 +2259,41 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
         batch_release(c, t);
         return r;
       };
+      // coordinate search: tile rows x root chunk, then the split between the persistent
+      // launch and step-by-step execution, then the block shape, then the hash load factor
       double best = 1e300, ms = 0;
       for (int tr : {32, 64, 128})
         for (int64_t ch : {4, 16, 64})
-          if (trial(tr, ch, heavy, &ms) == DM_OK && ms < best) {
+          if (trial(tr, ch, heavy, threads, ctas, &ms) == DM_OK && ms < best) {
             best = ms;
             TR = tr;
             chunk = ch;
           }
-      // then the split between the persistent launch and step-by-step execution
       for (double hv : {1e300, 1048576.0, 262144.0, 65536.0, 16384.0})
-        if (trial(TR, chunk, hv, &ms) == DM_OK && ms < best) {
+        if (trial(TR, chunk, hv, threads, ctas, &ms) == DM_OK && ms < best) {
           best = ms;
           heavy = hv;
         }
+      const int shapes[4][2] = {{256, 1}, {128, 0}, {128, 2}, {256, 0}};
+      for (auto &sh : shapes)
+        if (trial(TR, chunk, heavy, sh[0], sh[1], &ms) == DM_OK && ms < best) {
+          best = ms;
+          threads = sh[0];
+          ctas = sh[1];
+        }
+      const double lf0 = c->hash_lf;
+      double lf_best = lf0;
+      for (double lf : {0.25, 0.5, 0.75}) {
+        if (lf == lf0) continue;
+        set_hash_load_factor(c, lf);
+        if (trial(TR, chunk, heavy, threads, ctas, &ms) == DM_OK && ms < best) {
+          best = ms;
+          lf_best = lf;
+        }
+      }
+      set_hash_load_factor(c, lf_best);
     }
-    RET(batch_build(c, g, plans, n_plans, TR, chunk, heavy, &b));
+    RET(batch_build(c, g, plans, n_plans, TR, chunk, heavy, threads, ctas, &b));
     b->tuned = c->autotune != 0;
     c->batch = b;
   }
@@ -2257,8 +2307,11 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
 }
 
 int dm_batch_config(dm_ctx *c, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid, int32_t *n_stepwise,
-                    double *heavy_rows) {
+                    double *heavy_rows, int32_t *threads_per_cta, int32_t *ctas_per_sm, double *hash_load_factor) {
   if (!c || !c->batch) return DM_E_INVAL;
+  if (threads_per_cta) *threads_per_cta = c->batch->threads;
+  if (ctas_per_sm) *ctas_per_sm = c->batch->grid / std::max(1, c->num_sms);
+  if (hash_load_factor) *hash_load_factor = c->batch->hash_lf;
   if (tile_rows) *tile_rows = c->batch->TR;
   if (root_chunk) *root_chunk = c->batch->root_chunk;
   if (grid) *grid = c->batch->grid;
@@ -2273,6 +2326,17 @@ int dm_batch_latency(dm_ctx *c, double *out_ms, int32_t n) {
   return DM_OK;
 }
 
+int dm_set_batch_shape(dm_ctx *c, int32_t threads_per_cta, int32_t ctas_per_sm) {
+  if (!c || (threads_per_cta != 128 && threads_per_cta != 256) || ctas_per_sm < 0) return DM_E_INVAL;
+  c->batch_threads = threads_per_cta;
+  c->batch_ctas = ctas_per_sm;
+  if (c->batch) {
+    batch_release(c, c->batch);
+    c->batch = nullptr;
+  }
+  return DM_OK;
+}
+
 int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor, double heavy_rows) {
   if (!c || hash_load_factor <= 0.0 || hash_load_factor > 0.95) return DM_E_INVAL;
   c->autotune = autotune;
@@ -2281,22 +2345,7 @@ int dm_set_tuning(dm_ctx *c, int autotune, double hash_load_factor, double heavy
     batch_release(c, c->batch);
     c->batch = nullptr;
   }
-  if (hash_load_factor != c->hash_lf) {
-    c->hash_lf = hash_load_factor;
-    for (DevGraph *g : c->graphs) {  // two-key indices are rebuilt at the new load factor
-      if (!g) continue;
-      for (auto it = g->indices.begin(); it != g->indices.end();) {
-        if (it->second.v.nkeys == 2 && !it->second.keys) {
-          dfree(c, it->second.rows);
-          if (it->second.score) dfree(c, it->second.score);
-          dfree(c, it->second.slots);
-          it = g->indices.erase(it);
-        } else {
-          ++it;
-        }
-      }
-    }
-  }
+  set_hash_load_factor(c, hash_load_factor);
   return DM_OK;
 }
 

@@ -7,7 +7,8 @@
 // than TR * (largest key group of step j) rows. The last step is counted, not written. No CTA
 // ever waits for another; load balance comes from small root chunks taken in order of the
 // plans' estimated cost. Join, filter, score and compaction are the same device code as the
-// per-step kernel (join_device.cuh).
+// per-step kernel (join_device.cuh). The kernel exists for two block shapes (128 and 256
+// threads); the autotuner picks the shape and how many CTAs run per SM.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,7 +17,6 @@
 
 namespace dmk {
 
-constexpr int BATCH_BLK = 256;
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -24,6 +24,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+template <int BATCH_BLK>
 __device__ __forceinline__ void batch_tile(const JoinArgs &a, const JoinSmem &S, int TR, const int32_t *src,
                                            int nr, int64_t m0, int seedC, const TileOut &o, int *s_warp,
                                            unsigned long long *s_red, long long *s_base, unsigned long long &ar,
@@ -53,7 +54,8 @@ __device__ __forceinline__ void load_args(JoinArgs *dst, const JoinArgs *src) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ BatchParams P) {
+template <int BATCH_BLK>
+__global__ void __launch_bounds__(BATCH_BLK, 512 / BATCH_BLK) k_batch(const __grid_constant__ BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) JoinArgs sa;
   __shared__ int s_warp[BATCH_BLK / 32];
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
     __syncthreads();
     o.out = (int32_t *)(mine + P.lvl_off[0]);
     o.cap = P.lvl_cap[0];
-    batch_tile(sa, S, P.TR, nullptr, 0, item.lo, (int)(item.hi - item.lo), o, s_warp, s_red, &s_base, ar, as, ac);
+    batch_tile<BATCH_BLK>(sa, S, P.TR, nullptr, 0, item.lo, (int)(item.hi - item.lo), o, s_warp, s_red, &s_base, ar, as, ac);
     if (threadIdx.x == 0) {
       n_lvl[0] = s_lctr;
       cur[0] = 0;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
       __syncthreads();
       o.out = (int32_t *)(mine + P.lvl_off[j]);
       o.cap = P.lvl_cap[j];
-      batch_tile(sa, S, P.TR, lv + c0 * sa.w, nr, 0, 0, o, s_warp, s_red, &s_base, ar, as, ac);
+      batch_tile<BATCH_BLK>(sa, S, P.TR, lv + c0 * sa.w, nr, 0, 0, o, s_warp, s_red, &s_base, ar, as, ac);
       __syncthreads();
       if (threadIdx.x == 0) {
         cur[top] = c0 + nr;
@@ -141,25 +143,32 @@ __global__ void __launch_bounds__(BATCH_BLK, 2) k_batch(const __grid_constant__ 
   }
 }
 
-size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words) {
+typedef void (*BatchKernel)(BatchParams);
+
+static BatchKernel batch_kernel(int threads) { return threads == 128 ? k_batch<128> : k_batch<256>; }
+
+size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words, int threads) {
   size_t offs[7];
-  return join_smem_layout(tile_rows, ws_max, BATCH_BLK * 4, 1, offs) + (size_t)tile_rows * bm_words * 8;
+  return join_smem_layout(tile_rows, ws_max, threads * 4, 1, offs) + (size_t)tile_rows * bm_words * 8;
 }
 
-int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms) {
-  size_t smem = batch_smem_bytes(tile_rows, ws_max, bm_words);
-  cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms, int threads, int max_per_sm) {
+  size_t smem = batch_smem_bytes(tile_rows, ws_max, bm_words, threads);
+  BatchKernel k = batch_kernel(threads);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_BLK, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
   if (per_sm < 1) per_sm = 1;
+  if (max_per_sm > 0 && per_sm > max_per_sm) per_sm = max_per_sm;
   return num_sms * per_sm;
 }
 
-cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s) {
-  size_t smem = batch_smem_bytes(p.TR, p.ws_max, p.bm_words);
-  cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream_t s) {
+  size_t smem = batch_smem_bytes(p.TR, p.ws_max, p.bm_words, threads);
+  BatchKernel k = batch_kernel(threads);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   g_launches++;
-  k_batch<<<grid, BATCH_BLK, smem, s>>>(p);
+  k<<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

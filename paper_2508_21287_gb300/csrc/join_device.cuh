@@ -42,6 +42,15 @@ __device__ __forceinline__ unsigned long long dmix64(unsigned long long z) {
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Order-preserving key of an FP32 score: unsigned comparison of the keys orders the scores by
+// value for either sign (negative scores have their bits inverted, non-negative ones get the
+// sign bit set); -0 and +0 share one key. Scores are finite (weights are checked on load).
+__device__ __forceinline__ uint32_t score_key(float f) {
+  uint32_t b = __float_as_uint(f);
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

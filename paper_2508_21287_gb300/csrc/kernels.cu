@@ -395,7 +395,7 @@ __global__ void k_score_hist(const float *sc, int64_t n, uint32_t prefix, uint32
   h[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t b = __float_as_uint(__ldg(sc + i));
+    uint32_t b = score_key(__ldg(sc + i));
     if ((b & pmask) == prefix) atomicAdd(&h[(b >> shift) & 255u], 1u);
   }
   __syncthreads();
@@ -412,9 +412,21 @@ cudaError_t launch_score_hist(const float *sc, int64_t n, uint32_t prefix, uint3
 
 __global__ void k_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx, unsigned long long *ctr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t b = __float_as_uint(__ldg(sc + i));
+    uint32_t b = score_key(__ldg(sc + i));
     if (b <= T) out_idx[atomicAdd(ctr, 1ull)] = (int32_t)i;
   }
+}
+
+__global__ void k_score_keys(const float *sc, int64_t n, uint32_t *keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = score_key(__ldg(sc + i));
+}
+
+cudaError_t launch_score_keys(const float *sc, int64_t n, uint32_t *keys, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  g_launches++;
+  k_score_keys<<<(int)imin64((n + 255) / 256, 4096), 256, 0, s>>>(sc, n, keys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx, unsigned long long *ctr,

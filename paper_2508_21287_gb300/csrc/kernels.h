@@ -93,12 +93,15 @@ cudaError_t launch_hash_build(const int32_t *rows, int32_t mw, int32_t kp0, int3
                               dmi::HashSlot *slots, uint32_t log2cap, unsigned long long *ctr,
                               cudaStream_t s);
 
-// Top-k support: histogram of the 8-bit digit at `shift` of the FP32 score bits, over the
-// scores whose bits agree with `prefix` on `pmask`; and compaction of indices with bits <= T.
+// Top-k support: histogram of the 8-bit digit at `shift` of the scores' order-preserving keys, over the
+// scores whose keys agree with `prefix` on `pmask`; and compaction of indices with key <= T.
 cudaError_t launch_score_hist(const float *sc, int64_t n, uint32_t prefix, uint32_t pmask, int shift,
                               unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx,
                              unsigned long long *ctr, cudaStream_t s);
+// keys[i] = order-preserving unsigned key of sc[i] (the bits of both functions above are
+// these keys, not the raw FP32 bits).
+cudaError_t launch_score_keys(const float *sc, int64_t n, uint32_t *keys, cudaStream_t s);
 
 // Sum over rows of the checksum hash H(row) into ctr[CTR_SUM] (count = n).
 cudaError_t launch_hash_rows(const int32_t *rows, int64_t n, int32_t w, unsigned long long *ctr, cudaStream_t s);
@@ -118,7 +121,7 @@ cudaError_t msort_rows_into(const int32_t *rows, const float *scores, int64_t n,
 cudaError_t msort_rows(const int32_t *rows, int64_t n, int32_t w, int bits, void *tmp, int32_t **perm_out,
                        unsigned long long *sum, cudaStream_t s);
 
-// The min(k, n) smallest (score bits, row index) of a canonically sorted table, k <= 1024,
+// The min(k, n) smallest (score key, row index) of a canonically sorted table, k <= 1024,
 // gathered into orows / osc in that order. tmp holds topk_tmp_bytes(n) bytes.
 int64_t topk_tmp_bytes(int64_t n);
 cudaError_t topk_sorted(const int32_t *rows, const float *sc, int64_t n, int32_t w, int32_t k, void *tmp,
@@ -161,9 +164,11 @@ struct BatchParams {
   unsigned long long *plan_done;  // GPU global-timer time at which each plan's last item ended
   unsigned long long *start_ns;   // GPU global-timer time at the start of the launch
 };
-size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words);
-int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms);
-cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t s);
+// threads: 128 or 256 per CTA. batch_grid: SMs x resident CTAs per SM (at most max_per_sm when
+// it is > 0).
+size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words, int threads);
+int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms, int threads, int max_per_sm);
+cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream_t s);
 
 // Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.
 int64_t mlp_param_count();

@@ -12,8 +12,9 @@
 // key-packing kernel can also add the rows' checksum hashes (the same H as the join's count
 // mode) into a counter, so that delivering a table needs no separate hashing pass.
 //
-// Top-k runs on a canonically sorted table: the key of row i is (FP32 score bits, i); scores
-// are non-negative, so the bit pattern orders like the value, and i orders like the row.
+// Top-k runs on a canonically sorted table: the key of row i is (score_key(score), i), where
+// score_key maps an FP32 score to an unsigned key that orders like its value (either sign),
+// and i orders like the row.
 // Each block sorts a tile of keys and keeps its k smallest; the candidates shrink by that
 // factor per pass until one tile holds them all.
 #include <cuda_runtime.h>
@@ -396,7 +397,7 @@ constexpr int TK_TILE = 2048;
 
 __global__ void k_topk_keys_from_scores(const float *sc, int64_t n, unsigned long long *key) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    key[i] = ((unsigned long long)__float_as_uint(__ldg(sc + i)) << 32) | (uint32_t)i;
+    key[i] = ((unsigned long long)score_key(__ldg(sc + i)) << 32) | (uint32_t)i;
 }
 
 // Each block sorts TK_TILE keys and writes its k smallest (k <= TK_TILE).
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(TK_SBLK) k_topk_small(const float *sc, int32_t
   griddep_wait();
   griddep_launch_dependents();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < n; i += TK_SBLK) K[i] = ((unsigned long long)__float_as_uint(__ldg(sc + i)) << 32) | (uint32_t)i;
+  for (int i = tid; i < n; i += TK_SBLK) K[i] = ((unsigned long long)score_key(__ldg(sc + i)) << 32) | (uint32_t)i;
   const int kk = k < n ? k : n;
   if (tid == 0) {
     s_prefix = 0;

@@ -30,6 +30,14 @@ def _run(B, ctx, gid, pats, **kw):
     return counts, sums, single
 
 
+def _run_shape(B, ctx, gid, pats, threads):
+    B.dm_set_batch_shape(ctx.h, threads, 1 if threads == 256 else 0)
+    try:
+        return _run(B, ctx, gid, pats)
+    finally:
+        B.dm_set_batch_shape(ctx.h, 256, 0)
+
+
 def _check(g, pats, counts, sums, single):
     for p, c, s, (c1, s1) in zip(pats, counts.tolist(), sums.tolist(), single):
         ref = oracle.enumerate(g, p, rows=False, threads=8)
@@ -46,9 +54,18 @@ def test_batch_mixed_heavy_hex(B):
         _check(g, pats, counts, sums, single)
         cfg = B.dm_batch_config(ctx.h)
         assert cfg["tile_rows"] in (32, 64, 128) and cfg["root_chunk"] in (4, 16, 64)
+        # the autotuner also picked a block shape and a two-key hash load factor
+        assert cfg["threads_per_cta"] in (128, 256) and cfg["ctas_per_sm"] >= 1
+        assert cfg["hash_load_factor"] in (0.25, 0.5, 0.75)
         # the same plans again: the cached device image and graph are replayed
         counts2, sums2, _ = _run(B, ctx, gid, pats)
         assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
+        # every block shape and load factor gives the oracle's counts and checksums
+        for th, lf in ((128, 0.25), (256, 0.75)):
+            B.dm_set_tuning(ctx.h, autotune=False, hash_load_factor=lf)
+            counts3, sums3, _ = _run_shape(B, ctx, gid, pats, th)
+            assert np.array_equal(counts, counts3) and np.array_equal(sums, sums3)
+            assert B.dm_batch_config(ctx.h)["hash_load_factor"] == lf
 
 
 def test_batch_candidate_plans_with_wide_steps(B):

@@ -526,22 +526,31 @@ def _with_negative_edges(g, frac_seed: int, value: float = -0.02):
 
 
 @pytest.mark.parametrize("chunk_rows", [0, 64])
-def test_negative_weights_topk_is_exact(ctx, B, chunk_rows):
+@pytest.mark.parametrize("case", ["hh3x4", "hh4x6_p18"])
+def test_negative_weights_topk_is_exact(ctx, B, chunk_rows, case):
     # Sec. 5.4 ranks layouts by a sum of weights. With a negative weight a row's partial score
-    # is no lower bound of its final score, so the joins must not drop rows by partial score;
-    # the streamed plan (chunk_rows 64: many chunks, the k-th best known early) is the case
-    # where a pruning join would lose rows. FP32 sums are compared with the FP64 oracle within
-    # 1e-5 of the sum of the terms' magnitudes (the bound of a recursive sum of mixed signs).
-    base = I.lognormal_weights(I.heavy_hex(3, 4), seed=21, qubits=False)
+    # is no lower bound of its final score, so the joins must not drop rows by partial score
+    # (the streamed plan, chunk_rows 64, is where a pruning join would lose rows), and every
+    # selection must order negative scores by value (the single-block select, the tile passes
+    # and, for k > 1024, the radix select with the stable score sort). FP32 sums are compared
+    # with the FP64 oracle within 1e-5 of the sum of the terms' magnitudes (the error bound of
+    # a recursive sum of mixed signs).
+    if case == "hh3x4":
+        base = I.lognormal_weights(I.heavy_hex(3, 4), seed=21, qubits=False)
+        pats, ks = (I.path(9), I.sub_patch(base, 14, 3)), (1, 10, 50)
+    else:
+        base = I.lognormal_weights(I.heavy_hex(4, 6), seed=22, qubits=False)
+        pats, ks = (I.path(18),), (7, 1100)
     g = _with_negative_edges(base, 99)
     assert (g.edge_err < 0).any() and (g.edge_err > 0).any()
     gid = ctx.load(g)
     gabs = _with_negative_edges(base, 99, value=0.02)
-    for p in (I.path(9), I.sub_patch(g, 14, 3)):
+    for p in pats:
         allrows = oracle.enumerate(g, p).rows
         s = oracle.scores(g, p, allrows)
         mag = oracle.scores(gabs, p, allrows)  # sum of |terms| per row
-        for k in (1, 10, 50):
+        assert (s < 0).any()
+        for k in ks:
             plan = ctx.plan(gid, p, chunk_rows=chunk_rows)
             rows, scores = plan.topk(k)
             m = min(k, len(allrows))
@@ -554,6 +563,7 @@ def test_negative_weights_topk_is_exact(ctx, B, chunk_rows):
             order = oracle.topk(allrows, s, k)
             band = RTOL * mag.max()
             assert np.all(np.abs(scores - s[order]) <= band)
+            assert np.all(np.diff(scores) >= 0)
             kth = s[order[-1]]
             must = set(np.nonzero(s < kth - band)[0].tolist())
             assert must <= set(idx)

@@ -106,7 +106,7 @@ def test_serving_answers_equal_the_oracle_and_overlap_on_the_device(B):
         g = graphs[gi]
         p = I.mixed_pattern(40000 + s, 5, 8) if s % 2 else I.sub_patch(g, 5 + s % 5, s)
         reqs.append((gi, p))
-    srv = B.dm_server_create(0, n_slots=6, mem_budget_bytes=16 << 30, max_rows=4_000_000)
+    srv = B.dm_server_create(0, n_slots=6, mem_budget_bytes=32 << 30)  # no work cap: all must finish
     try:
         gids = [B.dm_server_load_graph(srv, g.n, g.row_ptr, g.col_idx, g.edge_err, g.qubit_err) for g in graphs]
         ids = [B.dm_server_submit(srv, gids[gi], p.n, p.row_ptr, p.col_idx, 10) for gi, p in reqs]
@@ -114,6 +114,7 @@ def test_serving_answers_equal_the_oracle_and_overlap_on_the_device(B):
         st = B.dm_server_stats_get(srv)
     finally:
         B.dm_server_destroy(srv)
+    assert [a["status"] for a in answers] == [0] * len(reqs)
     assert st["completed"] == len(reqs) and st["rejected"] == 0 and st["failed"] == 0
     # requests really ran at the same time: on the host and on the GPU timeline
     assert st["max_running"] > 1
