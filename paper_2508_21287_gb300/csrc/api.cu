@@ -2328,6 +2328,7 @@ int dm_batch_latency(dm_ctx *c, double *out_ms, int32_t n) {
 
 int dm_set_batch_shape(dm_ctx *c, int32_t threads_per_cta, int32_t ctas_per_sm) {
   if (!c || (threads_per_cta != 128 && threads_per_cta != 256) || ctas_per_sm < 0) return DM_E_INVAL;
+  if (c->batch_threads == threads_per_cta && c->batch_ctas == ctas_per_sm) return DM_OK;
   c->batch_threads = threads_per_cta;
   c->batch_ctas = ctas_per_sm;
   if (c->batch) {

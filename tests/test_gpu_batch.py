@@ -31,9 +31,11 @@ def _run(B, ctx, gid, pats, **kw):
 
 
 def _run_shape(B, ctx, gid, pats, threads):
+    """_run with a fixed block shape (autotuning off); also returns the batch's configuration."""
     B.dm_set_batch_shape(ctx.h, threads, 1 if threads == 256 else 0)
     try:
-        return _run(B, ctx, gid, pats)
+        counts, sums, single = _run(B, ctx, gid, pats)
+        return counts, sums, B.dm_batch_config(ctx.h)
     finally:
         B.dm_set_batch_shape(ctx.h, 256, 0)
 
@@ -63,9 +65,9 @@ def test_batch_mixed_heavy_hex(B):
         # every block shape and load factor gives the oracle's counts and checksums
         for th, lf in ((128, 0.25), (256, 0.75)):
             B.dm_set_tuning(ctx.h, autotune=False, hash_load_factor=lf)
-            counts3, sums3, _ = _run_shape(B, ctx, gid, pats, th)
+            counts3, sums3, cfg3 = _run_shape(B, ctx, gid, pats, th)
             assert np.array_equal(counts, counts3) and np.array_equal(sums, sums3)
-            assert B.dm_batch_config(ctx.h)["hash_load_factor"] == lf
+            assert cfg3["hash_load_factor"] == lf and cfg3["threads_per_cta"] == th
 
 
 def test_batch_candidate_plans_with_wide_steps(B):
