@@ -15,6 +15,9 @@ What each function follows:
       converse condition of the literal "iff").
   scores - Sec. 5.4: the layout score accumulated over the mapped edges (sum of errors,
       the log-domain form of the product of fidelities), FP64.
+  scores_directed - the direction-aware post-processing of Sec. 5.4's footnote: every
+      pattern slot p -> q weighted by its gate count times the device's cost in the direction
+      f(p) -> f(q), FP64.
   topk   - Sec. 5.4 ranking: the k rows with the smallest (score, row).
   images - the distinct vertex sets of the embeddings (deduplication).
   checksum - the library's order-independent checksum (no counterpart in the paper).
@@ -74,6 +77,10 @@ def _load():
             lib.or_scores.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_double)]
+            lib.or_scores_directed.restype = ctypes.c_int32
+            lib.or_scores_directed.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, _i32p,
+                                               ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
             lib.or_topk.restype = ctypes.c_int64
             lib.or_topk.argtypes = [_i32p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                     ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
@@ -192,6 +199,30 @@ def scores(data, pattern, rows: np.ndarray, form: int = 0) -> np.ndarray:
                        _ptr(rows), rows.shape[0], int(form), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise ValueError("scores: a row maps a pattern edge onto a non-edge")
+    return out
+
+
+def scores_directed(data, e_dir, pattern, w_dir, rows: np.ndarray) -> np.ndarray:
+    """FP64 direction-aware score per row (Sec. 5.4 footnote): sum over pattern slots p -> q
+    of w_dir[slot] * e_dir[slot of f(p) -> f(q)], plus data.qubit_err[f(u)] over pattern
+    vertices when the data graph has vertex errors. e_dir is aligned with data.col_idx (cost
+    of a gate from the row vertex to the column vertex), w_dir with pattern.col_idx."""
+    lib = _load()
+    rows = _i32(rows).reshape(-1, int(pattern.n))
+    ed = np.ascontiguousarray(e_dir, dtype=np.float32)
+    wd = np.ascontiguousarray(w_dir, dtype=np.float32)
+    if len(ed) != len(data.col_idx) or len(wd) != len(pattern.col_idx):
+        raise ValueError("e_dir / w_dir must be aligned with the data / pattern col_idx")
+    qe = None if getattr(data, "qubit_err", None) is None else np.ascontiguousarray(data.qubit_err, np.float32)
+    out = np.empty(rows.shape[0], dtype=np.float64)
+    rp_d, ci_d = _i32(data.row_ptr), _i32(data.col_idx)
+    rp_p, ci_p = _i32(pattern.row_ptr), _i32(pattern.col_idx)
+    rc = lib.or_scores_directed(int(data.n), _ptr(rp_d), _ptr(ci_d), ed.ctypes.data,
+                                None if qe is None else qe.ctypes.data, int(pattern.n), _ptr(rp_p), _ptr(ci_p),
+                                wd.ctypes.data, _ptr(rows), rows.shape[0],
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("scores_directed: a row maps a pattern edge onto a non-edge")
     return out
 
 

@@ -31,7 +31,8 @@
  * Score of a row (layout fidelity, Sec. 5.4): sum over pattern edges {u, v} of the edge
  * error w_e(f(u), f(v)) plus sum over pattern vertices of the vertex error w_q(f(u)),
  * accumulated in FP64. This is the log-domain form of the paper's product of fidelities;
- * lower is better.
+ * lower is better. or_scores_directed is the direction-aware form (per-direction device
+ * costs, per-direction pattern weights) of the same sum.
  */
 #include <math.h>
 #include <pthread.h>
@@ -435,6 +436,37 @@ int32_t or_scores(int32_t nd, const int32_t *rp_d, const int32_t *ci_d, const fl
             }
         if (qubit_err)
             for (int32_t u = 0; u < np; u++) s += score_term((double)qubit_err[f[u]], form);
+        out[r] = s;
+    }
+    return 0;
+}
+
+/* Direction-aware score of each row (the post-processing of Sec. 5.4's footnote: layouts are
+ * enumerated on the undirected coupling graph, and a two-qubit gate whose control and target
+ * land on a device edge is costed in the direction it runs there):
+ *   score(f) = sum over pattern slots p -> q (every ordered pair with {p, q} in E_p) of
+ *              w_dir[slot] * e_dir(f(p) -> f(q))
+ *            + sum over pattern vertices u of qubit_err[f(u)]   (when given)
+ * where w_dir is aligned with the pattern's col_idx (the number of gates run from p to q, or
+ * any weight) and e_dir with the data graph's col_idx (the cost of a gate from the row's
+ * vertex to the column's vertex; not symmetric in general). FP64. Returns -1 when a row maps
+ * a pattern edge onto a non-edge. */
+int32_t or_scores_directed(int32_t nd, const int32_t *rp_d, const int32_t *ci_d, const float *e_dir,
+                           const float *qubit_err, int32_t np, const int32_t *rp_p, const int32_t *ci_p,
+                           const float *w_dir, const int32_t *rows, int64_t nrows, double *out) {
+    csr_t d = {nd, rp_d, ci_d};
+    for (int64_t r = 0; r < nrows; r++) {
+        const int32_t *f = rows + r * np;
+        double s = 0.0;
+        for (int32_t p = 0; p < np; p++)
+            for (int32_t k = rp_p[p]; k < rp_p[p + 1]; k++) {
+                int found;
+                double e = edge_weight(&d, e_dir, f[p], f[ci_p[k]], &found);
+                if (!found) return -1;
+                s += (double)w_dir[k] * e;
+            }
+        if (qubit_err)
+            for (int32_t u = 0; u < np; u++) s += (double)qubit_err[f[u]];
         out[r] = s;
     }
     return 0;

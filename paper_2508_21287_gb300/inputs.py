@@ -286,6 +286,50 @@ def lognormal_weights(g: Graph, seed: int, mu: float = -5.0, sigma: float = 0.5,
     return g
 
 
+def directed_errors(g: Graph, seed: int, mu: float = -5.0, sigma: float = 0.5,
+                    reverse_mu: float = -7.0) -> np.ndarray:
+    """Per-direction two-qubit gate costs aligned with ``g.col_idx`` (slot k of row u = a gate
+    from u to col_idx[k]), as on hardware whose two-qubit gate runs natively one way per
+    coupling: every undirected edge (u < v, sorted order) gets a seeded native direction and a
+    log-normal(mu, sigma) error e; the other direction costs e plus two single-qubit gates of
+    log-normal(reverse_mu, sigma) error each (the basis change that turns the gate around)."""
+    edges = g.edges()
+    m = len(edges)
+    x = splitmix64_block(seed, 6 * m)
+    u = ((x >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+    z = np.sqrt(-2.0 * np.log(u[0::2])) * np.cos(2.0 * math.pi * u[1::2])  # 3m normals
+    e = np.exp(mu + sigma * z[:m])
+    extra = np.exp(reverse_mu + sigma * z[m:2 * m]) + np.exp(reverse_mu + sigma * z[2 * m:3 * m])
+    forward = (x[:m] & np.uint64(1)) == 0  # native direction u -> v (else v -> u)
+    cost = {}
+    for i, (a, b) in enumerate(edges):
+        nat, rev = float(e[i]), float(e[i] + extra[i])
+        cost[(a, b)] = nat if forward[i] else rev
+        cost[(b, a)] = rev if forward[i] else nat
+    out = np.empty(len(g.col_idx), dtype=np.float32)
+    for a in range(g.n):
+        for k in range(g.row_ptr[a], g.row_ptr[a + 1]):
+            out[k] = cost[(a, int(g.col_idx[k]))]
+    return out
+
+
+def gate_directions(p: Graph, seed: int, max_gates: int = 3) -> np.ndarray:
+    """Per-direction two-qubit gate counts of a circuit aligned with ``p.col_idx``: every
+    pattern edge (u < v) carries 1..max_gates seeded gates, each run from u to v or from v to
+    u."""
+    rng = SplitMix64(seed)
+    cnt = {}
+    for a, b in p.edges():
+        n = 1 + rng.below(max_gates)
+        fwd = sum(1 for _ in range(n) if rng.below(2) == 0)
+        cnt[(a, b)], cnt[(b, a)] = fwd, n - fwd
+    out = np.empty(len(p.col_idx), dtype=np.float32)
+    for a in range(p.n):
+        for k in range(p.row_ptr[a], p.row_ptr[a + 1]):
+            out[k] = cnt[(a, int(p.col_idx[k]))]
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 # Pattern graphs
 # ---------------------------------------------------------------------------------------

@@ -275,6 +275,64 @@ def test_scores_linear_weights_closed_form():
         assert np.array_equal(s, want)
 
 
+def _slot_weights(g, fn):
+    """A col_idx-aligned array with fn(u, v) at the slot of u -> v."""
+    out = np.empty(len(g.col_idx), dtype=np.float32)
+    for u in range(g.n):
+        for k in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            out[k] = fn(u, int(g.col_idx[k]))
+    return out
+
+
+def _transposed(g, a):
+    """The slot array whose u -> v entry is a's v -> u entry."""
+    pos = {(u, int(g.col_idx[k])): k for u in range(g.n) for k in range(g.row_ptr[u], g.row_ptr[u + 1])}
+    return np.array([a[pos[(int(g.col_idx[k]), u)]] for u in range(g.n)
+                     for k in range(g.row_ptr[u], g.row_ptr[u + 1])], dtype=np.float32)
+
+
+def test_directed_scores_reduce_to_undirected():
+    # symmetric device costs and one gate per pattern edge, run from the lower to the higher
+    # pattern vertex: the direction-aware score is the undirected score of Sec. 5.4
+    g = I.lognormal_weights(I.heavy_hex(2, 3), seed=4, qubits=True)
+    for p in (I.path(7), I.sub_patch(g, 9, 2), I.cycle(12)):
+        rows = oracle.enumerate(g, p).rows
+        w = _slot_weights(p, lambda a, b: 1.0 if a < b else 0.0)
+        np.testing.assert_array_equal(oracle.scores_directed(g, g.edge_err, p, w, rows), oracle.scores(g, p, rows))
+
+
+def test_directed_scores_closed_form():
+    # cost(u -> v) = u + 2v on the device and one gate i -> i+1 along a path pattern:
+    # score(f) = f(0) + 3 (f(1) + ... + f(n-2)) + 2 f(n-1); with the gates reversed the end
+    # coefficients swap
+    g = I.grid(4, 5)
+    e = _slot_weights(g, lambda u, v: u + 2.0 * v)
+    p = I.path(6)
+    rows = oracle.enumerate(g, p).rows.astype(np.float64)
+    fwd = _slot_weights(p, lambda a, b: 1.0 if b == a + 1 else 0.0)
+    want = rows[:, 0] + 3.0 * rows[:, 1:-1].sum(axis=1) + 2.0 * rows[:, -1]
+    np.testing.assert_array_equal(oracle.scores_directed(g, e, p, fwd, rows), want)
+    bwd = _slot_weights(p, lambda a, b: 1.0 if a == b + 1 else 0.0)
+    want = 2.0 * rows[:, 0] + 3.0 * rows[:, 1:-1].sum(axis=1) + rows[:, -1]
+    np.testing.assert_array_equal(oracle.scores_directed(g, e, p, bwd, rows), want)
+
+
+def test_directed_scores_transpose_and_linearity():
+    # turning every gate and every device cost around leaves the score unchanged; the score is
+    # linear in the gate counts
+    g = I.heavy_hex(2, 3)
+    e = I.directed_errors(g, seed=9)
+    assert not np.array_equal(e, _transposed(g, e))  # really direction dependent
+    for s_, p in enumerate((I.path(8), I.random_tree(9, 3), I.sub_patch(g, 10, 1))):
+        rows = oracle.enumerate(g, p).rows
+        w1, w2 = I.gate_directions(p, 2 * s_), I.gate_directions(p, 2 * s_ + 1)
+        a = oracle.scores_directed(g, e, p, w1, rows)
+        b = oracle.scores_directed(g, _transposed(g, e), p, _transposed(p, w1), rows)
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+        c = oracle.scores_directed(g, e, p, w1 + w2, rows)
+        np.testing.assert_allclose(c, a + oracle.scores_directed(g, e, p, w2, rows), rtol=1e-12)
+
+
 def test_topk_matches_full_sort():
     g = I.lognormal_weights(I.heavy_hex(2, 3), seed=3, qubits=True)
     p = I.path(6)
