@@ -271,6 +271,26 @@ int dm_set_batch_shape(dm_ctx *ctx, int32_t threads_per_cta, int32_t ctas_per_sm
 int dm_score_topk(dm_ctx *ctx, const dm_plan_t *plan, int32_t k, int32_t *out_rows,
                   float *out_scores, int32_t *out_n);
 
+/* Direction-aware layout scores (Sec. 5.4, its footnote on directed two-qubit gates: layouts
+ * are enumerated on the undirected coupling graph and the direction of each gate is handled
+ * afterwards). e_dir has row_ptr[n] floats aligned with the graph's col_idx: e_dir[slot of
+ * u -> v] is the cost of a two-qubit gate run from u to v (the native direction's error, or
+ * that error plus the cost of turning the gate around); it need not be symmetric and must be
+ * finite (else DM_E_INVAL). The library keeps a device copy with the graph, replacing any
+ * earlier one, until dm_destroy. DM_E_NOTFOUND for an unknown graph. */
+int dm_load_directed_errors(dm_ctx *ctx, dm_graph g, const float *e_dir);
+
+/* The k best layouts by their direction-aware score: score(f) = sum over the pattern's slots
+ * p -> q of w_dir[slot] * e_dir(f(p) -> f(q)), plus the graph's vertex errors of the images
+ * when it has them; FP32. w_dir (host, finite, aligned with the plan's pattern col_idx) is the
+ * circuit's number of gates run from p to q (0 for none; any weight works). The embeddings
+ * are those of dm_match (every one is scored after the joins; nothing is pruned by a partial
+ * score), then ranked as in dm_score_topk by (score, row). Needs dm_load_directed_errors on
+ * the plan's graph first (else DM_E_INVAL). out_rows: k x n_p int32 host buffer; out_scores:
+ * k floats (nullable); out_n receives the number written. */
+int dm_score_topk_directed(dm_ctx *ctx, const dm_plan_t *plan, const float *w_dir, int32_t k,
+                           int32_t *out_rows, float *out_scores, int32_t *out_n);
+
 /* DM_ALL and top-k from one pass of the joins: every embedding goes through cb exactly as
  * in dm_match, and the k best (score, row) rows are written to out_rows / out_scores as in
  * dm_score_topk. Needs edge weights. */

@@ -106,6 +106,8 @@ _SIGS = {
     "dm_match_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _u64p, _u64p]),
     "dm_score_topk": (ctypes.c_int, [_vp, _vp, _i32, _i32p, _fp, _i32p]),
     "dm_match_topk": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _i32, _i32p, _fp, _i32p, _u64p, _u64p]),
+    "dm_load_directed_errors": (ctypes.c_int, [_vp, _i32, _fp]),
+    "dm_score_topk_directed": (ctypes.c_int, [_vp, _vp, _fp, _i32, _i32p, _fp, _i32p]),
     "dm_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dm_stats)]),
     "dm_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -639,6 +641,22 @@ def dm_score_topk(ctx, plan, k: int, n_p: int):
     n = _i32()
     _check(_lib.dm_score_topk(ctx, plan, int(k), _p32(rows), scores.ctypes.data_as(_fp), ctypes.byref(n)),
            "dm_score_topk", ctx)
+    return rows[:n.value], scores[:n.value]
+
+
+def dm_load_directed_errors(ctx, graph: int, e_dir) -> None:
+    e = _f32(e_dir)
+    _check(_lib.dm_load_directed_errors(ctx, int(graph), _pf(e)), "dm_load_directed_errors", ctx)
+
+
+def dm_score_topk_directed(ctx, plan, w_dir, k: int, n_p: int):
+    """k best layouts by the direction-aware score; returns (rows [m, n_p], scores [m])."""
+    w = _f32(w_dir)
+    rows = np.zeros((k, n_p), dtype=np.int32)
+    scores = np.zeros(k, dtype=np.float32)
+    n = _i32()
+    _check(_lib.dm_score_topk_directed(ctx, plan, _pf(w), int(k), _p32(rows), _pf(scores), ctypes.byref(n)),
+           "dm_score_topk_directed", ctx)
     return rows[:n.value], scores[:n.value]
 
 

@@ -52,6 +52,7 @@ struct DevGraph {
   int64_t nnz = 0;
   int32_t *row_ptr = nullptr, *col_idx = nullptr;
   float *eerr = nullptr, *qerr = nullptr;
+  float *edir = nullptr;  // per-direction gate costs aligned with col_idx (direction-aware scores)
   unsigned long long *adj = nullptr;
   int32_t adj_words = 0;
   double avg_deg = 0;
@@ -1128,6 +1129,29 @@ struct TopkSink : Sink {
 
 int topk_take(dm_ctx *c, TopkSink *t, DevTable tab) { return t->take(c, tab); }
 
+// Direction-aware post-processing (Sec. 5.4 footnote): every delivered table gets its rows'
+// direction-aware scores (k_rescore_directed over the pattern's weighted slots) in place of the
+// undirected ones, then goes to the top-k.
+struct DirectedSink : Sink {
+  DevGraph *g = nullptr;
+  TopkSink *tk = nullptr;
+  int32_t np = 0, nslots = 0;
+  const int32_t *sp = nullptr, *sq = nullptr;
+  const float *sw = nullptr;
+  int take(dm_ctx *c, DevTable t) override {
+    float *dsc = nullptr;
+    RET(dalloc_t(c, &dsc, std::max<int64_t>(1, t.n)));
+    CK(dmk::launch_rescore_directed(t.rows, t.n, np, sp, sq, sw, nslots, g->row_ptr, g->col_idx, g->edir, g->qerr,
+                                    dsc, c->stream));
+    if (!t.borrowed) dfree(c, t.score);
+    DevTable s = t;
+    s.score = dsc;
+    const int r = tk->take(c, s);
+    if (t.borrowed) dfree(c, dsc);  // the top-k keeps copies; a borrowed table's holder frees nothing
+    return r;
+  }
+};
+
 bool topk_small_enough(const TopkSink *t) { return !t->have && t->k <= 1024; }
 
 // Top-k of a canonically sorted table straight into the caller's host buffers (enqueued on
@@ -1715,6 +1739,7 @@ void free_graph(dm_ctx *c, DevGraph *g) {
   cudaFree(g->col_idx);
   cudaFree(g->eerr);
   cudaFree(g->qerr);
+  cudaFree(g->edir);
   cudaFree(g->adj);
   delete g;
 }
@@ -2386,6 +2411,102 @@ int dm_score_topk(dm_ctx *c, const dm_plan_t *pl, int32_t k, int32_t *out_rows, 
     *out_n = (int32_t)m;
   }
   if (sink.have) free_table(c, sink.best);
+  cudaStreamSynchronize(c->stream);
+  finish_stats(c, t0);
+  return r;
+}
+
+int dm_load_directed_errors(dm_ctx *c, dm_graph gh, const float *e_dir) {
+  DevGraph *g = get_graph(c, gh);
+  if (!g || !e_dir) return g ? DM_E_INVAL : DM_E_NOTFOUND;
+  for (int64_t i = 0; i < g->nnz; i++)
+    if (!std::isfinite(e_dir[i])) return DM_E_INVAL;
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->stream));  // no queued work still reads the previous array
+  float *d = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * std::max<int64_t>(1, g->nnz)) != cudaSuccess) {
+    cudaGetLastError();
+    return DM_E_NOMEM;
+  }
+  if (cudaMemcpy(d, e_dir, sizeof(float) * g->nnz, cudaMemcpyHostToDevice) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    cudaFree(d);
+    return cuda_fail(c, e, "directed errors upload");
+  }
+  cudaFree(g->edir);
+  g->edir = d;
+  return DM_OK;
+}
+
+int dm_score_topk_directed(dm_ctx *c, const dm_plan_t *pl, const float *w_dir, int32_t k, int32_t *out_rows,
+                           float *out_scores, int32_t *out_n) {
+  if (!c || !pl || !w_dir || k < 1 || !out_rows || !out_n) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  if (!g->edir) return DM_E_INVAL;
+  const Plan &P = pl->p;
+  std::vector<int32_t> hp, hq;  // the pattern's weighted slots p -> q
+  std::vector<float> hw;
+  for (int32_t u = 0; u < P.n_p; u++)
+    for (int32_t e = P.rp[u]; e < P.rp[u + 1]; e++) {
+      if (!std::isfinite(w_dir[e])) return DM_E_INVAL;
+      if (w_dir[e] != 0.f) {
+        hp.push_back(u);
+        hq.push_back(P.ci[e]);
+        hw.push_back(w_dir[e]);
+      }
+    }
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  const size_t ns = hw.size();
+  int32_t *dp = nullptr, *dq = nullptr;
+  float *dw = nullptr;
+  int r = dalloc_t(c, &dp, std::max<size_t>(1, ns));
+  if (r == DM_OK) r = dalloc_t(c, &dq, std::max<size_t>(1, ns));
+  if (r == DM_OK) r = dalloc_t(c, &dw, std::max<size_t>(1, ns));
+  if (r == DM_OK && ns) {
+    if (cudaMemcpyAsync(dp, hp.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dq, hq.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dw, hw.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      r = cuda_fail(c, cudaGetLastError(), "directed slots upload");
+  }
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &P;
+  ex.mode = DM_ALL;
+  ex.use_qerr = false;
+  ex.chunk_rows = P.chunk_rows;
+  ex.max_rows = P.max_rows;
+  c->inflight = 0;
+  TopkSink tk;  // no bound pruning: partial undirected scores bound nothing here
+  tk.g = g;
+  tk.k = k;
+  DirectedSink ds;
+  ds.g = g;
+  ds.tk = &tk;
+  ds.np = P.n_p;
+  ds.nslots = (int32_t)ns;
+  ds.sp = dp;
+  ds.sq = dq;
+  ds.sw = dw;
+  ex.sink = &ds;
+  if (r == DM_OK) r = ex.run();
+  if (r == DM_OK) {
+    const int64_t m = tk.have ? tk.best.n : 0;
+    if (m > 0) {
+      CK(cudaMemcpyAsync(out_rows, tk.best.rows, sizeof(int32_t) * m * tk.best.w, cudaMemcpyDeviceToHost, c->stream));
+      if (out_scores)
+        CK(cudaMemcpyAsync(out_scores, tk.best.score, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *out_n = (int32_t)m;
+  }
+  if (tk.have) free_table(c, tk.best);
+  dfree(c, dp);
+  dfree(c, dq);
+  dfree(c, dw);
   cudaStreamSynchronize(c->stream);
   finish_stats(c, t0);
   return r;

@@ -362,14 +362,15 @@ static size_t wjoin_smem(const JoinArgs &a) { return (size_t)WJ_WARPS * warp_sme
 // device that launches the kernels (contexts on several threads may race here harmlessly,
 // the call is idempotent).
 static void set_wjoin_attrs() {
-  static std::atomic<unsigned long long> done{0};
+  static std::atomic<unsigned long long> done{0};  // one bit per device ordinal below 64
   int dev = 0;
   cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (done.load() & bit) return;
+  const bool cached = dev >= 0 && dev < 64;  // higher ordinals set the attributes on every call
+  const unsigned long long bit = cached ? 1ull << dev : 0ull;
+  if (cached && (done.load() & bit)) return;
   WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>, k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
   for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  done.fetch_or(bit);
+  if (cached) done.fetch_or(bit);
 }
 
 int wjoin_grid(const JoinArgs &a, int num_sms) {

@@ -417,6 +417,46 @@ __global__ void k_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out
   }
 }
 
+// Direction-aware score of each row (one thread per row): the sum over the pattern's weighted
+// slots p -> q of w * edir[slot of f(p) -> f(q) in the data graph's CSR], plus the vertex
+// errors of the row's images when qerr is given; FP32, slots in the order given.
+__global__ void k_rescore_directed(const int32_t *rows, int64_t n, int32_t np, const int32_t *sp, const int32_t *sq,
+                                   const float *sw, int32_t nslots, const int32_t *row_ptr, const int32_t *col_idx,
+                                   const float *edir, const float *qerr, float *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t *f = rows + i * np;
+    float s = 0.f;
+    for (int32_t e = 0; e < nslots; e++) {
+      const int32_t u = __ldg(f + __ldg(sp + e)), v = __ldg(f + __ldg(sq + e));
+      int32_t lo = __ldg(row_ptr + u), hi = __ldg(row_ptr + u + 1);
+      float c = 0.f;
+      while (lo < hi) {  // the slot of u -> v (present: the row is an embedding)
+        const int32_t mid = (lo + hi) >> 1, x = __ldg(col_idx + mid);
+        if (x == v) {
+          c = __ldg(edir + mid);
+          break;
+        }
+        if (x < v) lo = mid + 1;
+        else hi = mid;
+      }
+      s += __ldg(sw + e) * c;
+    }
+    if (qerr)
+      for (int32_t u = 0; u < np; u++) s += __ldg(qerr + __ldg(f + u));
+    out[i] = s;
+  }
+}
+
+cudaError_t launch_rescore_directed(const int32_t *rows, int64_t n, int32_t np, const int32_t *sp, const int32_t *sq,
+                                    const float *sw, int32_t nslots, const int32_t *row_ptr, const int32_t *col_idx,
+                                    const float *edir, const float *qerr, float *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  g_launches++;
+  k_rescore_directed<<<(int)imin64((n + 255) / 256, 8192), 256, 0, s>>>(rows, n, np, sp, sq, sw, nslots, row_ptr,
+                                                                          col_idx, edir, qerr, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_score_keys(const float *sc, int64_t n, uint32_t *keys) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     keys[i] = score_key(__ldg(sc + i));

@@ -99,6 +99,11 @@ cudaError_t launch_score_hist(const float *sc, int64_t n, uint32_t prefix, uint3
                               unsigned long long *hist, cudaStream_t s);
 cudaError_t launch_select_le(const float *sc, int64_t n, uint32_t T, int32_t *out_idx,
                              unsigned long long *ctr, cudaStream_t s);
+// Direction-aware scores (Sec. 5.4 footnote): out[i] = sum_e sw[e] * edir[slot of
+// rows[i][sp[e]] -> rows[i][sq[e]]] (+ sum_u qerr[rows[i][u]] when qerr is set), FP32.
+cudaError_t launch_rescore_directed(const int32_t *rows, int64_t n, int32_t np, const int32_t *sp, const int32_t *sq,
+                                    const float *sw, int32_t nslots, const int32_t *row_ptr, const int32_t *col_idx,
+                                    const float *edir, const float *qerr, float *out, cudaStream_t s);
 // keys[i] = order-preserving unsigned key of sc[i] (the bits of both functions above are
 // these keys, not the raw FP32 bits).
 cudaError_t launch_score_keys(const float *sc, int64_t n, uint32_t *keys, cudaStream_t s);
