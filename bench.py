@@ -79,6 +79,10 @@ def parse_args():
     ap.add_argument("--graph", default="heavyhex", choices=["heavyhex", "grid", "rr3"],
                     help="c3: data graph family (heavy-hex m x n, square grid 60x60, random 3-regular V=4096)")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
+    ap.add_argument("--shard-r0", action="store_true",
+                    help="c3 under torchrun: every rank runs the same queries, each on its shard of the first "
+                         "table R_0 (dm_match_shard), and the counts and checksums are summed across ranks "
+                         "(strong scaling); default: each rank its own queries (weak scaling)")
     ap.add_argument("--contexts", type=int, default=0,
                     help="c2/c3: library contexts (each its own stream and host thread) the queries of a step "
                          "are spread over; 0 = 8 for c2, 1 for c3")
@@ -145,6 +149,26 @@ def combine_ranks(ms: float, units: float, device: str = "cuda") -> tuple[float,
     u = torch.tensor([float(units)], dtype=torch.float64, device=device)
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(t.item()), float(u.item())
+
+
+def combine_counts_many(pairs, device: str = "cuda") -> list[tuple[int, int]]:
+    """Sum every (count, checksum) pair mod 2^64 over ranks in one all-reduce: the one exchange
+    of counts sharded over R_0 (dm_match_shard). Each u64 travels as two 32-bit limbs in int64,
+    so the sums are exact for any number of ranks below 2^31; a single process gets its own
+    numbers back."""
+    import torch
+    import torch.distributed as dist
+    pairs = [(int(c), int(s_)) for c, s_ in pairs]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return pairs
+    m32, m64 = (1 << 32) - 1, (1 << 64) - 1
+    t = torch.tensor([[c & m32, c >> 32, s_ & m32, s_ >> 32] for c, s_ in pairs], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [((v[0] + (v[1] << 32)) & m64, (v[2] + (v[3] << 32)) & m64) for v in t.tolist()]
+
+
+def combine_counts(count: int, checksum: int, device: str = "cuda") -> tuple[int, int]:
+    return combine_counts_many([(count, checksum)], device)[0]
 
 
 class ClockSampler:
@@ -298,8 +322,9 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
     import torch
     B, rank, world, local = init_run()
     hh = tuple(int(x) for x in args.hh.split(","))
-    g, pats = workload(rank, args.batch, kind, hh, args.only_path, args.graph)
     count_mode = kind == "c3"
+    shard = count_mode and world > 1 and getattr(args, "shard_r0", False)
+    g, pats = workload(0 if shard else rank, args.batch, kind, hh, args.only_path, args.graph)
     n_ctx = args.contexts or (1 if count_mode else 8)
     # independent queries: each context (own CUDA stream, arena and graph copy) is driven by its
     # own host thread, so one query's dependent launches overlap with the others'
@@ -319,6 +344,7 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
     acc = {"emb": 0, "join_ms": 0.0, "join_bytes": 0.0, "join_launches": 0, "launches": 0, "d2h": 0, "chunks": 0,
            "max_rows": 0}
     qpats = B.QueryBatch([(p.n, p.row_ptr, p.col_idx) for p in pats], K_TOP)  # marshalled once, reused
+    shard_sums = [(0, 0) for _ in pats]  # sharded runs: this rank's count and checksum per query
     # count mode: plans are made once, outside the timed steps (the e2e leg plans inside)
     plans = [[B.dm_plan(ctxs[t].h, gids[t], p.n, p.row_ptr, p.col_idx) if i % n_ctx == t else None
               for i, p in enumerate(pats)] for t in range(n_ctx)] if count_mode else None
@@ -360,7 +386,12 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
             if i % n_ctx != t:
                 continue
             plan = B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx) if host else plans[t][i]
-            cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
+            if shard:  # this rank's part of R_0; the 2 x u64 sums are combined after the steps
+                cnt, cs = B.dm_match_shard(ctx.h, plan, rank, world)
+                with lock:
+                    shard_sums[i] = ((shard_sums[i][0] + cnt), (shard_sums[i][1] + cs) & ((1 << 64) - 1))
+            else:
+                cnt, _ = B.dm_match(ctx.h, plan, B.DM_COUNT)
             if host:
                 B.dm_plan_free(plan)
             if rec is not None:
@@ -400,6 +431,9 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
             ev[i][0].record(stream)
             fork()
             acc["emb"] += step(False, acc)
+            if shard:  # the one exchange: an exact 2 x u64 sum per query over the ranks' shards
+                combine_counts_many(shard_sums)
+                shard_sums = [(0, 0) for _ in pats]
             join()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
@@ -453,7 +487,8 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
                           "separate pass, one context, queries in sequence")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if shard else "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": wl_name(args, kind), "queries_per_step": len(pats),
                        "embeddings_per_step": emb_total / args.steps / world,
@@ -464,7 +499,8 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
                        "output": "count + 64-bit checksum" if count_mode else "all embeddings + FP32 scores + top-100",
                        "l2": "flushed between steps (256 MiB write); intermediate tables far larger than L2"
                              if count_mode else "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas x{world}", "contexts": n_ctx,
+                       "parallelism": (f"R_0 shards x{world} (2 x u64 sum per query)" if shard
+                                       else f"replicas x{world}"), "contexts": n_ctx,
                        "join_chunks_per_step": acc["chunks"] / args.steps, "largest_table_rows": acc["max_rows"]},
             "e2e": e2e, "gpu_launches": acc["launches"], "clocks": clocks, "roofline": roofline}
     if with_cpu and rank == 0 and world == 1:

@@ -221,6 +221,16 @@ typedef int (*dm_chunk_cb)(void *user, const int32_t *rows, const float *scores,
 int dm_match(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, void *user,
              uint64_t *out_count, uint64_t *out_checksum);
 
+/* One shard of dm_match(DM_COUNT) (Alg. 1 over a slice of its first table R_0; the paper
+ * runs one GPU): the count and checksum of the embeddings whose image of the plan's first
+ * slice vertex (dm_plan_describe: step 0, slice[0]) is congruent to shard modulo n_shards.
+ * The shards 0 .. n_shards - 1 partition Emb: their counts and checksums sum (mod 2^64) to
+ * dm_match's, so GPUs that each run one shard combine their results with one 2 x u64 sum.
+ * Each shard reads the whole motif table of the first step and keeps its rows; the later
+ * steps see only the shard's rows. DM_E_INVAL unless 0 <= shard < n_shards. */
+int dm_match_shard(dm_ctx *ctx, const dm_plan_t *plan, int32_t shard, int32_t n_shards,
+                   uint64_t *out_count, uint64_t *out_checksum);
+
 /* Count + checksum for n_plans plans on the same data graph in one persistent launch
  * (captured in a CUDA graph). Each plan is Alg. 1 (Sec. 3.2) as in dm_match; running many
  * plans in one launch has no counterpart in the paper (it answers one pattern at a time).

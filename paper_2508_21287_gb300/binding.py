@@ -104,6 +104,7 @@ _SIGS = {
     "dm_plan_describe": (_i32, [_vp, _i32p, _i32]),
     "dm_match": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _u64p, _u64p]),
     "dm_match_batch": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.c_int, _u64p, _u64p]),
+    "dm_match_shard": (ctypes.c_int, [_vp, _vp, _i32, _i32, _u64p, _u64p]),
     "dm_score_topk": (ctypes.c_int, [_vp, _vp, _i32, _i32p, _fp, _i32p]),
     "dm_match_topk": (ctypes.c_int, [_vp, _vp, ctypes.c_int, DM_CHUNK_CB, _vp, _i32, _i32p, _fp, _i32p, _u64p, _u64p]),
     "dm_load_directed_errors": (ctypes.c_int, [_vp, _i32, _fp]),
@@ -442,6 +443,14 @@ def dm_match(ctx, plan, mode: int = DM_ALL, cb=None):
     if err:
         raise err[0]
     _check(rc, "dm_match", ctx)
+    return cnt.value, cs.value
+
+
+def dm_match_shard(ctx, plan, shard: int, n_shards: int):
+    """Count and checksum of one shard of R_0 (see include/dm.h); returns (count, checksum)."""
+    cnt, cs = _u64(), _u64()
+    _check(_lib.dm_match_shard(ctx, plan, int(shard), int(n_shards), ctypes.byref(cnt), ctypes.byref(cs)),
+           "dm_match_shard", ctx)
     return cnt.value, cs.value
 
 

@@ -447,6 +447,7 @@ struct Exec {
   const Plan *p;
   int mode;          // DM_ALL / DM_COUNT
   bool use_qerr;
+  int32_t shard = 0, n_shards = 1;  // one shard of R_0 (count runs over several GPUs)
   float prune = INFINITY;
   Sink *sink = nullptr;
   int64_t chunk_rows = 0, max_rows = 0;
@@ -511,6 +512,10 @@ struct Exec {
       a.prune = prune;
       a.mode = (j == S - 1 && mode == DM_COUNT) ? 1 : 0;
       a.nx.nkeys = -1;
+      if (j == 0 && n_shards > 1) {
+        a.shard = shard;
+        a.n_shards = n_shards;
+      }
     }
     for (int j = 0; j + 1 < S; j++) {
       st[j].base.nx = st[j + 1].base.ix;
@@ -2248,6 +2253,34 @@ int dm_match(dm_ctx *c, const dm_plan_t *pl, int mode, dm_chunk_cb cb, void *use
   log_plan_steps(c, pl->p);
   if (out_count) *out_count = cnt;
   if (out_checksum) *out_checksum = cs;
+  return DM_OK;
+}
+
+int dm_match_shard(dm_ctx *c, const dm_plan_t *pl, int32_t shard, int32_t n_shards, uint64_t *out_count,
+                   uint64_t *out_checksum) {
+  if (!c || !pl || n_shards < 1 || shard < 0 || shard >= n_shards) return DM_E_INVAL;
+  DevGraph *g = get_graph(c, pl->p.graph);
+  if (!g) return DM_E_NOTFOUND;
+  cudaSetDevice(c->device);
+  auto t0 = std::chrono::steady_clock::now();
+  reset_stats(c);
+  Exec ex;
+  ex.c = c;
+  ex.g = g;
+  ex.p = &pl->p;
+  ex.mode = DM_COUNT;
+  ex.use_qerr = false;
+  ex.shard = shard;
+  ex.n_shards = n_shards;
+  ex.chunk_rows = pl->p.chunk_rows;
+  ex.max_rows = pl->p.max_rows;
+  c->inflight = 0;
+  const int r = ex.run();
+  cudaStreamSynchronize(c->stream);
+  finish_stats(c, t0);
+  if (r != DM_OK) return r;
+  if (out_count) *out_count = ex.count;
+  if (out_checksum) *out_checksum = ex.checksum;
   return DM_OK;
 }
 

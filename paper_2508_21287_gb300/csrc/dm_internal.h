@@ -175,6 +175,9 @@ struct JoinArgs {
   int32_t nx_key_col[2];
   // seed mode (R == nullptr): motif rows [seed_lo, seed_hi) are the candidates
   int64_t seed_lo, seed_hi;
+  // seed mode with n_shards > 1: keep only motif rows whose position-0 vertex is congruent to
+  // shard modulo n_shards (one shard of the first table R_0)
+  int32_t shard, n_shards;
 };
 
 }  // namespace dmi

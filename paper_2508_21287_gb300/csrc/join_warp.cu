@@ -63,6 +63,12 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int wsv) {
   return m;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16); the data
+// stays in global memory, nothing waits for it.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Check one candidate against row r of the warp tile (new vertices preloaded).
 template <int MAXNEW>
 __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int wsv, bool seed, int r, int m,
@@ -70,6 +76,7 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
   const int32_t *rrow = W.rows + r * wsv;
   const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
   bool ok = true;
+  if (seed && a.n_shards > 1) ok = (uint32_t)nv[0] % (uint32_t)a.n_shards == (uint32_t)a.shard;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
   if (ok && !seed) {  // FilterOverlappingNodes: one pass over the row for all new vertices
     const int4 *r4 = (const int4 *)rrow;
@@ -102,6 +109,38 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
   if (ok && a.induced) ok = induced_ok<MAXNEW>(a, rrow, nv);
   if (sc > a.prune) ok = false;
   return ok;
+}
+
+// Sum of the checksum terms of a tile row in a counted last step, where every working column
+// is an output column: tq[c] = 1 + the output position of column c (int4-aligned, padded), so
+// one 16-byte read gives the positions of four columns; two accumulators keep eight terms
+// independent per iteration.
+__device__ __forceinline__ unsigned long long row_terms_last(const int32_t *row, int w, const int32_t *tq) {
+  const int4 *r4 = (const int4 *)row;
+  const int4 *q4 = (const int4 *)tq;
+  unsigned long long p0 = 0, p1 = 0;
+  const int nq = w >> 2;
+  int c4 = 0;
+  for (; c4 + 1 < nq; c4 += 2) {
+    const int4 x = r4[c4], y = r4[c4 + 1], qx = q4[c4], qy = q4[c4 + 1];
+    p0 += dmix64(((unsigned long long)(uint32_t)qx.x << 32) | (uint32_t)x.x) +
+          dmix64(((unsigned long long)(uint32_t)qx.y << 32) | (uint32_t)x.y);
+    p1 += dmix64(((unsigned long long)(uint32_t)qx.z << 32) | (uint32_t)x.z) +
+          dmix64(((unsigned long long)(uint32_t)qx.w << 32) | (uint32_t)x.w);
+    p0 += dmix64(((unsigned long long)(uint32_t)qy.x << 32) | (uint32_t)y.x) +
+          dmix64(((unsigned long long)(uint32_t)qy.y << 32) | (uint32_t)y.y);
+    p1 += dmix64(((unsigned long long)(uint32_t)qy.z << 32) | (uint32_t)y.z) +
+          dmix64(((unsigned long long)(uint32_t)qy.w << 32) | (uint32_t)y.w);
+  }
+  if (c4 < nq) {
+    const int4 x = r4[c4], qx = q4[c4];
+    p0 += dmix64(((unsigned long long)(uint32_t)qx.x << 32) | (uint32_t)x.x) +
+          dmix64(((unsigned long long)(uint32_t)qx.y << 32) | (uint32_t)x.y);
+    p1 += dmix64(((unsigned long long)(uint32_t)qx.z << 32) | (uint32_t)x.z) +
+          dmix64(((unsigned long long)(uint32_t)qx.w << 32) | (uint32_t)x.w);
+  }
+  for (int c = 4 * nq; c < w; c++) p0 += dmix64(((unsigned long long)(uint32_t)tq[c] << 32) | (uint32_t)row[c]);
+  return p0 + p1;
 }
 
 // Word q of staged survivor s's output row. code[q] < 0x100: working column of the R row; else
@@ -181,6 +220,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
   __shared__ int16_t code[MAXW];
   __shared__ int8_t ipos[MAXW];  // R column -> output position (-1: none)
   __shared__ int8_t npos[MAXM];  // new vertex -> output position
+  __shared__ __align__(16) int32_t tq[MAXW];  // counted last step: 1 + output position of column c
   __shared__ unsigned long long s_red[WJ_WARPS];
   const bool seed = a.R == nullptr;
   const int w = a.w, wo = a.wo;
@@ -194,6 +234,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     code[q] = (int16_t)(col < w ? col : (0x100 | (col - w)));
     if (col < w) ipos[col] = (int8_t)q;
     else npos[col - w] = (int8_t)q;
+    if (MODE == 1 && col < w) tq[col] = q + 1;
   }
   for (int r = lane; r < WT; r += 32)  // padding words never change afterwards
     for (int c = w; c < wsv; c++) W.rows[r * wsv + c] = -1;
@@ -254,7 +295,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
       int start = 0, len = 0;
       if (lane < nr) {
         const int32_t *row = W.rows + lane * wsv;
-        if (MODE == 1) W.part[lane] = row_terms(row, w, ipos);
+        if (MODE == 1) W.part[lane] = row_terms_last(row, w, tq);
         ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
       }
       int incl = len;

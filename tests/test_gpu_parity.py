@@ -589,3 +589,25 @@ def test_non_finite_weights_rejected_and_not_registered(ctx, B):
     assert gid1 == gid0 + 1
     r = check_all(ctx, gid1, g, I.path(6))
     assert r.count > 0
+
+
+# ------------------------------------------------------------------ R_0 shards -------------
+@pytest.mark.parametrize("n_shards", [2, 3, 7])
+def test_r0_shards_partition_the_embeddings(ctx, B, hh, n_shards):
+    # each shard of the first table is the oracle's part (image of the shard vertex modulo the
+    # shard count), and the shards' counts and checksums sum (mod 2^64) to the whole
+    g, gid = hh
+    m64 = (1 << 64) - 1
+    for p, kw in ((I.path(14), {}), (I.sub_patch(g, 20, 4), {}), (I.path(12), {"chunk_rows": 500})):
+        plan = ctx.plan(gid, p, **kw)
+        v0 = plan.describe()[0]["slice"][0]
+        rows = oracle.enumerate(g, p).rows
+        tot_c, tot_s = 0, 0
+        for sh in range(n_shards):
+            c, s = B.dm_match_shard(ctx.h, plan.h, sh, n_shards)
+            part = rows[rows[:, v0] % n_shards == sh]
+            assert (c, s) == (len(part), oracle.checksum(part))
+            tot_c, tot_s = tot_c + c, (tot_s + s) & m64
+        assert (tot_c, tot_s) == plan.count()
+    with pytest.raises(B.DMError):
+        B.dm_match_shard(ctx.h, plan.h, 3, 3)
