@@ -255,6 +255,11 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     if (!seed) {
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
+      if (lane == 0 && t + nw < ntiles) {  // the warp's next tile: bring it into L2 meanwhile
+        const int32_t *nsrc = a.R + (t + nw) * WT * w;
+        const uint32_t nb = (uint32_t)(imin64(WT, N - (t + nw) * WT) * w * 4) & ~15u;
+        if (nb && (((uintptr_t)nsrc) & 15) == 0) l2_prefetch(nsrc, nb);
+      }
       if ((((uintptr_t)src) & 15) == 0) {  // 16-byte loads; their words go to the padded rows
         const int n4 = ne >> 2;
         int r = (lane * 4) / w, c = lane * 4 - r * w;  // first word 4 * k of the lane, with carry
