@@ -69,12 +69,20 @@ __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Number of new vertices of a step: exactly MAXNEW in the variants for 1 to 4 (so the loops over
+// them unroll without runtime guards), read from the arguments in the wide variant.
+template <int MAXNEW>
+__device__ __forceinline__ int nnew_of(const JoinArgs &a) {
+  return MAXNEW <= STAGE_NV ? MAXNEW : a.n_new;
+}
+
 // Check one candidate against row r of the warp tile (new vertices preloaded).
 template <int MAXNEW>
 __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int wsv, bool seed, int r, int m,
                                        const int32_t (&nv)[MAXNEW], float &sc) {
   const int32_t *rrow = W.rows + r * wsv;
   const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
+  const int nn = nnew_of<MAXNEW>(a);
   bool ok = true;
   if (seed && a.n_shards > 1) ok = (uint32_t)nv[0] % (uint32_t)a.n_shards == (uint32_t)a.shard;
   for (int i = 0; i < a.n_chk; i++) ok &= __ldg(trow + a.chk_mpos[i]) == rrow[a.chk_col[i]];
@@ -86,7 +94,7 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
       const int4 x = r4[c4];
 #pragma unroll
       for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new) hit |= (x.x == nv[i]) | (x.y == nv[i]) | (x.z == nv[i]) | (x.w == nv[i]);
+        if (i < nn) hit |= (x.x == nv[i]) | (x.y == nv[i]) | (x.z == nv[i]) | (x.w == nv[i]);
     }
     ok = !hit;
   }
@@ -97,7 +105,7 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
     if (a.qerr) {
 #pragma unroll
       for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new) sc += __ldg(a.qerr + nv[i]);
+        if (i < nn) sc += __ldg(a.qerr + nv[i]);
     }
   }
   for (int e = 0; e < a.n_be && ok; e++) {
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
       const int32_t *trow = mrows + (int64_t)m * mw;  // row 0 for idle lanes: a valid address
 #pragma unroll
       for (int i = 0; i < MAXNEW; i++)
-        if (i < a.n_new) nv[i] = __ldg(trow + a.new_mpos[i]);
+        if (i < nnew_of<MAXNEW>(a)) nv[i] = __ldg(trow + a.new_mpos[i]);
       float sc = 0.f;
       const bool ok = valid && wcheck<MAXNEW>(a, W, wsv, seed, r, m, nv, sc);
       if (MODE == 1) {
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
           unsigned long long p = seed ? 0ull : W.part[r];
 #pragma unroll
           for (int i = 0; i < MAXNEW; i++)
-            if (i < a.n_new) p += col_term(npos[i], nv[i]);
+            if (i < nnew_of<MAXNEW>(a)) p += col_term(npos[i], nv[i]);
           acc_sum += dmix64(p + (unsigned long long)(uint32_t)wo);
           acc_rows++;
         }
@@ -362,7 +370,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
           W.st_s[pos] = sc;
 #pragma unroll
           for (int i = 0; i < (STG ? MAXNEW : 0); i++)
-            if (i < a.n_new) W.st_nv[pos * STAGE_NV + i] = nv[i];
+            if (i < nnew_of<MAXNEW>(a)) W.st_nv[pos * STAGE_NV + i] = nv[i];
         }
         nst += __popc(bal);
         __syncwarp();
@@ -394,11 +402,15 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
 
 typedef void (*WJoinKernel)(JoinArgs);
 
-static int wjoin_variant(const JoinArgs &a) { return (a.mode == 1 ? 0 : 3) + (a.n_new <= 1 ? 0 : a.n_new <= 4 ? 1 : 2); }
+// Variants: count or write mode x exactly 1, 2, 3 or 4 new vertices, or any other number (the
+// wide variant, which reads it at run time; a step that maps no new vertex goes there too).
+static int wjoin_variant(const JoinArgs &a) {
+  return (a.mode == 1 ? 0 : 5) + (a.n_new >= 1 && a.n_new <= 4 ? a.n_new - 1 : 4);
+}
 
 static WJoinKernel pick_wjoin(const JoinArgs &a) {
-  static const WJoinKernel ks[6] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>,
-                                    k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
+  static const WJoinKernel ks[10] = {k_joinw<1, 1>, k_joinw<2, 1>, k_joinw<3, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>,
+                                     k_joinw<1, 0>, k_joinw<2, 0>, k_joinw<3, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
   return ks[wjoin_variant(a)];
 }
 
@@ -414,7 +426,8 @@ static void set_wjoin_attrs() {
   const bool cached = dev >= 0 && dev < 64;  // higher ordinals set the attributes on every call
   const unsigned long long bit = cached ? 1ull << dev : 0ull;
   if (cached && (done.load() & bit)) return;
-  WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>, k_joinw<1, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
+  WJoinKernel ks[] = {k_joinw<1, 1>, k_joinw<2, 1>, k_joinw<3, 1>, k_joinw<4, 1>, k_joinw<MAXM, 1>,
+                      k_joinw<1, 0>, k_joinw<2, 0>, k_joinw<3, 0>, k_joinw<4, 0>, k_joinw<MAXM, 0>};
   for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (cached) done.fetch_or(bit);
 }
@@ -427,7 +440,7 @@ int wjoin_grid(const JoinArgs &a, int num_sms) {
   // resident blocks per SM for this variant and row stride, asked of the runtime once (the
   // query costs host time on every launch otherwise); every device of the process is taken to
   // be of one architecture
-  static std::atomic<int> occ[6][MAXW / 4 + 2];
+  static std::atomic<int> occ[10][MAXW / 4 + 2];
   const int slot = join_row_stride(a.w) / 4;
   int per_sm = occ[wjoin_variant(a)][slot].load(std::memory_order_relaxed);
   if (per_sm <= 0) {
