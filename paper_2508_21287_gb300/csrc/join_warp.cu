@@ -69,6 +69,47 @@ __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Whether any of the four ids of x equals one of nv[0 .. NN), folded into hit: the compares
+// accumulate into one predicate (setp with .or), one instruction a compare.
+template <int NN>
+__device__ __forceinline__ bool any_eq4(bool hit, const int4 x, const int32_t *nv) {
+  uint32_t r;
+  if (NN == 1)
+    asm("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+        " setp.eq.or.s32 p, %2, %6, p;\n setp.eq.or.s32 p, %3, %6, p;\n"
+        " setp.eq.or.s32 p, %4, %6, p;\n setp.eq.or.s32 p, %5, %6, p;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r) : "r"((uint32_t)hit), "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w), "r"(nv[0]));
+  else if (NN == 2)
+    asm("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+        " setp.eq.or.s32 p, %2, %6, p;\n setp.eq.or.s32 p, %3, %6, p;\n"
+        " setp.eq.or.s32 p, %4, %6, p;\n setp.eq.or.s32 p, %5, %6, p;\n"
+        " setp.eq.or.s32 p, %2, %7, p;\n setp.eq.or.s32 p, %3, %7, p;\n"
+        " setp.eq.or.s32 p, %4, %7, p;\n setp.eq.or.s32 p, %5, %7, p;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r) : "r"((uint32_t)hit), "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w), "r"(nv[0]), "r"(nv[1]));
+  else if (NN == 3)
+    asm("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+        " setp.eq.or.s32 p, %2, %6, p;\n setp.eq.or.s32 p, %3, %6, p;\n"
+        " setp.eq.or.s32 p, %4, %6, p;\n setp.eq.or.s32 p, %5, %6, p;\n"
+        " setp.eq.or.s32 p, %2, %7, p;\n setp.eq.or.s32 p, %3, %7, p;\n"
+        " setp.eq.or.s32 p, %4, %7, p;\n setp.eq.or.s32 p, %5, %7, p;\n"
+        " setp.eq.or.s32 p, %2, %8, p;\n setp.eq.or.s32 p, %3, %8, p;\n"
+        " setp.eq.or.s32 p, %4, %8, p;\n setp.eq.or.s32 p, %5, %8, p;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r) : "r"((uint32_t)hit), "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w), "r"(nv[0]), "r"(nv[1]), "r"(nv[2]));
+  else
+    asm("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+        " setp.eq.or.s32 p, %2, %6, p;\n setp.eq.or.s32 p, %3, %6, p;\n"
+        " setp.eq.or.s32 p, %4, %6, p;\n setp.eq.or.s32 p, %5, %6, p;\n"
+        " setp.eq.or.s32 p, %2, %7, p;\n setp.eq.or.s32 p, %3, %7, p;\n"
+        " setp.eq.or.s32 p, %4, %7, p;\n setp.eq.or.s32 p, %5, %7, p;\n"
+        " setp.eq.or.s32 p, %2, %8, p;\n setp.eq.or.s32 p, %3, %8, p;\n"
+        " setp.eq.or.s32 p, %4, %8, p;\n setp.eq.or.s32 p, %5, %8, p;\n"
+        " setp.eq.or.s32 p, %2, %9, p;\n setp.eq.or.s32 p, %3, %9, p;\n"
+        " setp.eq.or.s32 p, %4, %9, p;\n setp.eq.or.s32 p, %5, %9, p;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)hit), "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w), "r"(nv[0]), "r"(nv[1]), "r"(nv[2]), "r"(nv[3]));
+  return r != 0;
+}
+
 // Number of new vertices of a step: exactly MAXNEW in the variants for 1 to 4 (so the loops over
 // them unroll without runtime guards), read from the arguments in the wide variant.
 template <int MAXNEW>
@@ -92,9 +133,13 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
 #pragma unroll 2
     for (int c4 = 0; c4 < (a.w + 3) >> 2; c4++) {
       const int4 x = r4[c4];
+      if (MAXNEW <= STAGE_NV) {
+        hit = any_eq4<MAXNEW>(hit, x, nv);
+      } else {
 #pragma unroll
-      for (int i = 0; i < MAXNEW; i++)
-        if (i < nn) hit |= (x.x == nv[i]) | (x.y == nv[i]) | (x.z == nv[i]) | (x.w == nv[i]);
+        for (int i = 0; i < MAXNEW; i++)
+          if (i < nn) hit |= (x.x == nv[i]) | (x.y == nv[i]) | (x.z == nv[i]) | (x.w == nv[i]);
+      }
     }
     ok = !hit;
   }
