@@ -319,7 +319,7 @@ def init_run():
     return B, rank, world, local
 
 
-def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
+def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool, fuse: bool = False):
     """One workload of independent queries (c3: count + checksum; c2: every embedding with its
     score plus the top-100), timed over args.steps steps; returns the JSON line (dict)."""
     import torch
@@ -336,6 +336,7 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool):
     gids = []
     for c, st_ in zip(ctxs, streams):
         B.dm_set_stream(c.h, st_)
+        B.dm_set_fusion(c.h, fuse)
         gids.append(c.load(g))
         B.dm_enable_timing(c.h, n_ctx == 1)  # with several contexts the kernels are timed in a pass of their own
     stream = torch.cuda.Stream()
@@ -526,6 +527,15 @@ def run_ours(args):
     if kind == "c3" and world == 1 and not args.no_extras and not args.only_path:
         line["extras_note"] = ("c2, c4 and c5 below are the other configurations, each measured in this run "
                                "after the headline")
+        fz = measure_queries(args, "c3", with_e2e=False, with_cpu=False, fuse=True)
+        line["c3_fused"] = {"value": fz["value"], "unit": UNIT, "ms_per_step": fz["ms_per_step"],
+                            "gpu_launches": fz["gpu_launches"],
+                            "roofline": {k: fz["roofline"][k] for k in ("achieved", "frac", "avg_launch_us", "launches",
+                                                                        "algorithmic_bytes_per_launch")},
+                            "note": "the same queries with each plan's last two joins in one kernel "
+                                    "(dm_set_fusion): the table between them stays in shared memory, "
+                                    "so fewer bytes move and the fraction of the HBM peak falls while "
+                                    "embeddings/s rise"}
         line["c2"] = summary_c2(measure_queries(args_for(args, "c2"), "c2", with_e2e=True, with_cpu=False))
         line["c4"] = summary_c4(run_c4(args_for(args, "c4"), emit=False))
         line["c5"] = summary_c5(run_c5(args_for(args, "c5"), emit=False))

@@ -267,6 +267,14 @@ int dm_batch_latency(dm_ctx *ctx, double *out_ms, int32_t n);
  * step; <= 0 = none). */
 int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor, double heavy_rows);
 
+/* on = 1: counted matches (DM_COUNT, dm_match_shard) on the device-driven path run their
+ * plan's last two joins as one kernel when both map 1 to 4 new vertices: the survivors of the
+ * second-to-last join are joined and counted in shared memory, so the table between the two
+ * joins (the largest of a path-like plan) is never written to or read from device memory.
+ * on = 0 (the default) runs every join as its own launch (Alg. 1 step by step). Results are
+ * identical either way. No counterpart in the paper (its joins are library calls). */
+int dm_set_fusion(dm_ctx *ctx, int on);
+
 /* Block shape of dm_match_batch when autotuning is off (no counterpart in the paper):
  * threads_per_cta 128 or 256, ctas_per_sm resident CTAs per SM (0 = as many as fit).
  * DM_E_INVAL otherwise. Takes effect at the next dm_match_batch. */

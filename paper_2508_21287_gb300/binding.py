@@ -118,6 +118,7 @@ _SIGS = {
     "dm_batch_config": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64), _i32p, _i32p, ctypes.POINTER(ctypes.c_double),
                                        _i32p, _i32p, ctypes.POINTER(ctypes.c_double)]),
     "dm_set_batch_shape": (ctypes.c_int, [_vp, _i32, _i32]),
+    "dm_set_fusion": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dm_batch_latency": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _i32]),
     "dm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "dm_model_init": (ctypes.c_int, [_vp, _u64]),
@@ -477,6 +478,10 @@ def dm_batch_config(ctx) -> dict:
 
 def dm_set_batch_shape(ctx, threads_per_cta: int = 256, ctas_per_sm: int = 0) -> None:
     _check(_lib.dm_set_batch_shape(ctx, int(threads_per_cta), int(ctas_per_sm)), "dm_set_batch_shape", ctx)
+
+
+def dm_set_fusion(ctx, on: bool = True) -> None:
+    _check(_lib.dm_set_fusion(ctx, int(bool(on))), "dm_set_fusion", ctx)
 
 
 def dm_batch_latency(ctx, n: int) -> np.ndarray:

@@ -97,6 +97,7 @@ struct dm_ctx {
   double hash_lf = 0.5;               // load factor of two-key hash indices
   double heavy_rows = 1e300;          // plans predicted to hold more rows run step by step
   int batch_threads = 256, batch_ctas = 0;  // block shape of dm_match_batch without autotuning
+  bool fuse_last = false;  // counted plans: the last two joins in one launch when they qualify
   std::vector<double> batch_latency;  // per plan, ms from the start of the last dm_match_batch
 };
 
@@ -451,6 +452,7 @@ struct Exec {
   float prune = INFINITY;
   Sink *sink = nullptr;
   int64_t chunk_rows = 0, max_rows = 0;
+  bool fused = false;  // the last run_fast ran the plan's last two joins as one kernel
   std::vector<StepRT> st;
   uint64_t count = 0, checksum = 0;
 
@@ -508,7 +510,7 @@ struct Exec {
       a.col_idx = g->col_idx;
       a.eerr = g->eerr;
       a.qerr = use_qerr ? g->qerr : nullptr;
-      a.scored = g->eerr != nullptr;
+      a.scored = g->eerr != nullptr && mode != DM_COUNT;  // a count needs no scores
       a.prune = prune;
       a.mode = (j == S - 1 && mode == DM_COUNT) ? 1 : 0;
       a.nx.nkeys = -1;
@@ -768,6 +770,11 @@ struct Exec {
     int32_t *prev_rows = nullptr;
     float *prev_score = nullptr;
     int64_t prev_cap = 0;
+    // a counted plan's last two joins run as one kernel when they qualify: the table between
+    // them stays in shared memory
+    const bool fuse = c->fuse_last && S >= 2 && st[S - 1].base.mode == 1 &&
+                      dmk::fused_ok(st[S - 2].base, st[S - 1].base);
+    fused = fuse;
     for (int j = 0; j < S; j++) {
       JoinArgs a = st[j].base;
       a.prune = prune;
@@ -792,6 +799,18 @@ struct Exec {
         a.n_dev = c->d_ctr_steps + (size_t)(j - 1) * CTR_N + CTR_ROWS;
         a.in_cap = prev_cap;
       }
+      if (fuse && j == S - 2) {
+        JoinArgs b = st[S - 1].base;
+        b.prune = prune;
+        b.ctr = c->d_ctr_steps + (size_t)(S - 1) * CTR_N;
+        b.out_next = nullptr;
+        b.nx.nkeys = -1;
+        a.out = nullptr;
+        a.outs = nullptr;
+        a.out_cap = 0;
+        CK(dmk::launch_fused(a, b, c->num_sms, c->stream, j > 0));
+        break;
+      }
       int grid = dmk::wjoin_grid(a, c->num_sms);
       CK(dmk::launch_wjoin(a, grid, c->stream, j > 0));  // steps chain kernel to kernel
       prev_rows = orows;
@@ -815,10 +834,13 @@ struct Exec {
       const unsigned long long *h = c->h_ctr_steps + (size_t)j * CTR_N;
       const JoinArgs &a = st[j].base;
       int64_t rows = (int64_t)h[CTR_ROWS];
-      double bytes = (double)st[j].motif_bytes + (j ? (double)nin * (4.0 * a.w + (a.scored ? 4 : 0)) : 0.0);
-      if (a.mode == 0) bytes += (double)rows * (4.0 * a.wo + (a.scored ? 4 : 0));
+      // fused last two joins: the table between them is neither written nor read
+      const bool in_smem = fused && j == S - 1, out_smem = fused && j == S - 2;
+      double bytes = (double)st[j].motif_bytes;
+      if (j && !in_smem) bytes += (double)nin * (4.0 * a.w + (a.scored ? 4 : 0));
+      if (a.mode == 0 && !out_smem) bytes += (double)rows * (4.0 * a.wo + (a.scored ? 4 : 0));
       c->stats.join_bytes += bytes;
-      c->stats.join_launches++;
+      if (!in_smem) c->stats.join_launches++;
       c->stats.chunks++;
       if (j < DM_MAX_STEPS) {
         c->stats.rows[j] += rows;
@@ -2393,6 +2415,12 @@ int dm_set_batch_shape(dm_ctx *c, int32_t threads_per_cta, int32_t ctas_per_sm) 
     batch_release(c, c->batch);
     c->batch = nullptr;
   }
+  return DM_OK;
+}
+
+int dm_set_fusion(dm_ctx *c, int on) {
+  if (!c) return DM_E_INVAL;
+  c->fuse_last = on != 0;
   return DM_OK;
 }
 

@@ -507,4 +507,280 @@ cudaError_t launch_wjoin(const JoinArgs &a, int grid, cudaStream_t s, bool pdl) 
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------------
+// The last two steps of a counted plan in one kernel. Step A (the plan's second-to-last join,
+// written in working-column order) and step B (the last join, counted) run back to back on
+// every tile: each survivor of A is assembled straight into a shared-memory tile of B rows
+// (the A row, then A's new vertices, padded with -1 like any tile), together with the sum of
+// its checksum terms (the A row's terms, summed once per A row, plus those of the new
+// vertices), and when B's tile cannot take another round of A it is joined and counted as in
+// k_joinw's counted step. The table between A and B, the largest of a path-like plan, is
+// never written to or read from global memory.
+
+// Key groups of a tile's rows and the tile row of each candidate of a round.
+struct TileGroups {
+  int32_t *gstart, *goff, *cand_row;  // WT, WT + 1, 32
+};
+
+struct FSmem {
+  int32_t *rowsA, *rowsB;               // WT x wsA, WT x wsB
+  unsigned long long *partA, *partB;    // checksum terms of each A row / B row
+  TileGroups ga, gb;                    // A's tile (live across B's joins) and B's tile
+};
+
+__host__ __device__ __forceinline__ size_t fused_warp_bytes(int wsA, int wsB) {
+  size_t b = (size_t)WT * wsA * 4 + (size_t)WT * wsB * 4;
+  b += (size_t)WT * 8 * 2;
+  b += 2 * ((size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4);
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ FSmem fused_smem(unsigned char *base, int wsA, int wsB) {
+  FSmem m;
+  size_t off = 0;
+  m.rowsA = (int32_t *)(base + off);
+  off += (size_t)WT * wsA * 4;
+  m.rowsB = (int32_t *)(base + off);
+  off += (size_t)WT * wsB * 4;
+  m.partA = (unsigned long long *)(base + off);
+  m.partB = m.partA + WT;
+  off += (size_t)WT * 8 * 2;
+  m.ga.gstart = (int32_t *)(base + off);
+  m.ga.goff = m.ga.gstart + WT;
+  m.ga.cand_row = m.ga.goff + WT + 1;
+  m.gb.gstart = m.ga.cand_row + 32;
+  m.gb.goff = m.gb.gstart + WT;
+  m.gb.cand_row = m.gb.goff + WT + 1;
+  return m;
+}
+
+struct FusedArgs {
+  JoinArgs a, b;
+};
+
+// Look up the key groups of the nr rows of a shared tile (lane = row) and scan their sizes;
+// returns the number of candidates.
+__device__ __forceinline__ int tile_groups(const JoinArgs &a, const int32_t *rows, int ws, int nr, const TileGroups &F) {
+  const int lane = threadIdx.x & 31;
+  int start = 0, len = 0;
+  if (lane < nr) {
+    const int32_t *row = rows + lane * ws;
+    ix_lookup(a.ix, row[a.key_col[0]], a.ix.nkeys == 2 ? row[a.key_col[1]] : 0, start, len);
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int C = __shfl_sync(FULL_MASK, incl, 31);
+  F.gstart[lane] = start;
+  F.goff[lane] = incl - len;
+  if (lane == 0) F.goff[WT] = C;
+  __syncwarp();
+  return C;
+}
+
+// Candidate c (this lane's, of the round starting at cb) of a tile: its row and motif row.
+__device__ __forceinline__ void round_rows(const TileGroups &F, int nr, int cb, int C, int &r, int &m) {
+  const int lane = threadIdx.x & 31;
+  if (lane < nr) {
+    const int lo = max(F.goff[lane], cb), hi = min(F.goff[lane + 1], cb + 32);
+    for (int c = lo; c < hi; c++) F.cand_row[c - cb] = lane;
+  }
+  __syncwarp();
+  r = 0;
+  m = 0;
+  const int c = cb + lane;
+  if (c < C) {
+    r = F.cand_row[lane];
+    m = F.gstart[r] + (c - F.goff[r]);
+  }
+}
+
+// Join and count the nb rows of the B tile (step B, its rows' checksum terms in partB).
+template <int NB>
+__device__ __forceinline__ void count_b_tile(const JoinArgs &b, const FSmem &F, int wsB, int nb, const int32_t *tq,
+                                             unsigned long long &acc_rows, unsigned long long &acc_sum,
+                                             unsigned long long &acc_cand) {
+  const int lane = threadIdx.x & 31;
+  const int C = tile_groups(b, F.rowsB, wsB, nb, F.gb);
+  acc_cand += lane == 0 ? (unsigned long long)C : 0ull;
+  WarpSmem W{};
+  W.rows = F.rowsB;
+  const int w = b.w;
+  for (int cb = 0; cb < C; cb += 32) {
+    int r, m;
+    round_rows(F.gb, nb, cb, C, r, m);
+    const bool valid = cb + lane < C;
+    int32_t nv[NB];
+    const int32_t *trow = b.ix.rows + (int64_t)m * b.ix.mw;
+#pragma unroll
+    for (int i = 0; i < NB; i++) nv[i] = __ldg(trow + b.new_mpos[i]);
+    float sc = 0.f;
+    if (valid && wcheck<NB>(b, W, wsB, false, r, m, nv, sc)) {
+      unsigned long long p = F.partB[r];
+#pragma unroll
+      for (int i = 0; i < NB; i++) p += dmix64(((unsigned long long)(uint32_t)tq[w + i] << 32) | (uint32_t)nv[i]);
+      acc_sum += dmix64(p + (unsigned long long)(uint32_t)b.wo);
+      acc_rows++;
+    }
+    __syncwarp();  // cand_row is rewritten by the next round
+  }
+}
+
+template <int NA, int NB>
+__global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ FusedArgs f) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) int32_t tq[MAXW];  // 1 + B's output position of each B working column
+  __shared__ unsigned long long s_red[WJ_WARPS];
+  const JoinArgs &a = f.a, &b = f.b;
+  const bool seed = a.R == nullptr;
+  const int wA = a.w, wB = b.w;  // wB = wA + NA
+  const int wsA = join_row_stride(wA), wsB = join_row_stride(wB);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const FSmem F = fused_smem(smem + (size_t)wid * fused_warp_bytes(wsA, wsB), wsA, wsB);
+  for (int q = threadIdx.x; q < b.wo; q += WJ_BLK) tq[b.src_col[q]] = q + 1;
+  for (int r = lane; r < WT; r += 32) {  // padding words never change afterwards
+    for (int c = wA; c < wsA; c++) F.rowsA[r * wsA + c] = -1;
+    for (int c = wB; c < wsB; c++) F.rowsB[r * wsB + c] = -1;
+  }
+  __syncthreads();
+  griddep_wait();  // everything above touched shared memory only
+  griddep_launch_dependents();
+  const int64_t N = seed ? (a.seed_hi - a.seed_lo) : (a.n_dev ? imin64((int64_t)*a.n_dev, a.in_cap) : a.N);
+  const int64_t ntiles = (N + WT - 1) / WT;
+  const int64_t gw = (int64_t)blockIdx.x * WJ_WARPS + wid, nw = (int64_t)gridDim.x * WJ_WARPS;
+  unsigned long long rows_a = 0, cand_a = 0, acc_rows = 0, acc_sum = 0, cand_b = 0;
+  WarpSmem W{};
+  W.rows = F.rowsA;
+  int nb = 0;  // rows in the B tile
+  for (int64_t t = gw; t < ntiles; t += nw) {
+    const int64_t r0 = t * WT;
+    const int nr = (int)imin64(WT, N - r0);
+    int C;
+    if (!seed) {
+      const int32_t *src = a.R + r0 * wA;
+      if (lane == 0 && t + nw < ntiles) {  // the warp's next tile: bring it into L2 meanwhile
+        const int32_t *nsrc = a.R + (t + nw) * WT * wA;
+        const uint32_t nbytes = (uint32_t)(imin64(WT, N - (t + nw) * WT) * wA * 4) & ~15u;
+        if (nbytes && (((uintptr_t)nsrc) & 15) == 0) l2_prefetch(nsrc, nbytes);
+      }
+      int r = lane / wA, c = lane % wA;  // element e = r * wA + c, advanced with carry
+      const int dr = 32 / wA, dc = 32 % wA;
+      for (int e = lane; e < nr * wA; e += 32) {
+        F.rowsA[r * wsA + c] = __ldg(src + e);
+        r += dr;
+        c += dc;
+        if (c >= wA) {
+          c -= wA;
+          r++;
+        }
+      }
+      __syncwarp();
+      if (lane < nr) F.partA[lane] = row_terms_last(F.rowsA + lane * wsA, wA, tq);  // B positions
+      C = tile_groups(a, F.rowsA, wsA, nr, F.ga);
+    } else {
+      C = nr;
+    }
+    cand_a += lane == 0 ? (unsigned long long)C : 0ull;
+    for (int cb = 0; cb < C; cb += 32) {
+      int r = 0, m = 0;
+      if (seed) {
+        if (cb + lane < C) m = (int)(a.seed_lo + r0 + cb + lane);
+      } else {
+        round_rows(F.ga, nr, cb, C, r, m);
+      }
+      const bool valid = cb + lane < C;
+      int32_t nv[NA];
+      const int32_t *trow = a.ix.rows + (int64_t)m * a.ix.mw;
+#pragma unroll
+      for (int i = 0; i < NA; i++) nv[i] = __ldg(trow + a.new_mpos[i]);
+      float sc = 0.f;
+      const bool ok = valid && wcheck<NA>(a, W, wsA, seed, r, m, nv, sc);
+      const unsigned bal = __ballot_sync(FULL_MASK, ok);
+      const int K = __popc(bal);
+      if (nb + K > WT) {  // B's tile is full: join and count it first
+        count_b_tile<NB>(b, F, wsB, nb, tq, acc_rows, acc_sum, cand_b);
+        nb = 0;
+      }
+      if (ok) {  // the survivor's row in B's tile: the A row, then A's new vertices
+        const int slot = nb + __popc(bal & lanemask_lt());
+        int32_t *d = F.rowsB + slot * wsB;
+        unsigned long long p = seed ? 0ull : F.partA[r];
+        if (!seed) {
+          const int4 *s4 = (const int4 *)(F.rowsA + r * wsA);
+          int4 *d4 = (int4 *)d;
+          for (int c4 = 0; c4 < (wA + 3) >> 2; c4++) d4[c4] = s4[c4];  // -1 beyond wA, overwritten below
+        }
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+          d[wA + i] = nv[i];
+          p += dmix64(((unsigned long long)(uint32_t)tq[wA + i] << 32) | (uint32_t)nv[i]);
+        }
+        F.partB[slot] = p;
+      }
+      nb += K;
+      rows_a += lane == 0 ? (unsigned long long)K : 0ull;
+      __syncwarp();  // B's tile and cand_row are read next
+    }
+    __syncwarp();  // the next tile overwrites this warp's A rows
+  }
+  if (nb > 0) count_b_tile<NB>(b, F, wsB, nb, tq, acc_rows, acc_sum, cand_b);
+  unsigned long long t0 = block_sum_u64<WJ_BLK>(rows_a, s_red);
+  unsigned long long t1 = block_sum_u64<WJ_BLK>(cand_a, s_red);
+  unsigned long long t2 = block_sum_u64<WJ_BLK>(cand_b, s_red);
+  unsigned long long t3 = block_sum_u64<WJ_BLK>(acc_rows, s_red);
+  unsigned long long t4 = block_sum_u64<WJ_BLK>(acc_sum, s_red);
+  if (threadIdx.x == 0) {
+    if (t0) atomicAdd(a.ctr + CTR_ROWS, t0);
+    if (t1) atomicAdd(a.ctr + CTR_CAND, t1);
+    if (t2) atomicAdd(b.ctr + CTR_CAND, t2);
+    if (t3) atomicAdd(b.ctr + CTR_ROWS, t3);
+    atomicAdd(b.ctr + CTR_SUM, t4);
+  }
+}
+
+typedef void (*FJoinKernel)(FusedArgs);
+
+static FJoinKernel pick_fused(int na, int nb) {
+  static const FJoinKernel ks[4][4] = {
+      {k_joinf<1, 1>, k_joinf<1, 2>, k_joinf<1, 3>, k_joinf<1, 4>},
+      {k_joinf<2, 1>, k_joinf<2, 2>, k_joinf<2, 3>, k_joinf<2, 4>},
+      {k_joinf<3, 1>, k_joinf<3, 2>, k_joinf<3, 3>, k_joinf<3, 4>},
+      {k_joinf<4, 1>, k_joinf<4, 2>, k_joinf<4, 3>, k_joinf<4, 4>}};
+  return ks[na - 1][nb - 1];
+}
+
+static size_t fused_smem(const JoinArgs &a, const JoinArgs &b) {
+  return (size_t)WJ_WARPS * fused_warp_bytes(join_row_stride(a.w), join_row_stride(b.w));
+}
+
+bool fused_ok(const JoinArgs &a, const JoinArgs &b) {
+  return a.mode == 0 && b.mode == 1 && a.n_new >= 1 && a.n_new <= 4 && b.n_new >= 1 && b.n_new <= 4 &&
+         b.w == a.w + a.n_new && a.wo == b.w && b.R == nullptr && !a.scored && !b.scored && a.n_shards <= 1 &&
+         fused_smem(a, b) <= 200 * 1024;
+}
+
+cudaError_t launch_fused(const JoinArgs &a, const JoinArgs &b, int num_sms, cudaStream_t s, bool pdl) {
+  FJoinKernel k = pick_fused(a.n_new, b.n_new);
+  const size_t smem = fused_smem(a, b);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WJ_BLK, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t rows = a.R == nullptr ? a.seed_hi - a.seed_lo : (a.n_dev ? INT64_MAX / 2 : a.N);
+  int64_t g = (int64_t)num_sms * per_sm, need = (rows + (int64_t)WT * WJ_WARPS - 1) / ((int64_t)WT * WJ_WARPS);
+  if (need < g) g = need;
+  if (g < 1) g = 1;
+  FusedArgs fa;
+  fa.a = a;
+  fa.b = b;
+  g_launches++;
+  if (pdl) return launch_pdl(k, dim3((unsigned)g), dim3(WJ_BLK), smem, s, fa);
+  k<<<(unsigned)g, WJ_BLK, smem, s>>>(fa);
+  return cudaGetLastError();
+}
+
 }  // namespace dmk

@@ -45,6 +45,13 @@ cudaError_t launch_wjoin(const dmi::JoinArgs &a, int grid, cudaStream_t s, bool 
 // One full wave for a launch that reads its input row count on the device (n_dev), else the
 // blocks its rows need, at most one wave.
 int wjoin_grid(const dmi::JoinArgs &a, int num_sms);
+// The last two steps of a counted plan in one kernel (join_warp.cu): a = the second-to-last
+// step (writes, identity column order), b = the last (counted); b's rows are a's survivors,
+// which never reach global memory (b.R is ignored). Counts go to a.ctr (a's survivors and
+// candidates) and b.ctr (the count, checksum and b's candidates). fused_ok tells whether the
+// pair qualifies (1 to 4 new vertices each, no scores, no shards, shared memory fits).
+bool fused_ok(const dmi::JoinArgs &a, const dmi::JoinArgs &b);
+cudaError_t launch_fused(const dmi::JoinArgs &a, const dmi::JoinArgs &b, int num_sms, cudaStream_t s, bool pdl);
 
 // Data-graph preparation.
 cudaError_t launch_csr_to_m2(const int32_t *row_ptr, const int32_t *col_idx, const float *eerr,

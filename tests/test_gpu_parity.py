@@ -611,3 +611,32 @@ def test_r0_shards_partition_the_embeddings(ctx, B, hh, n_shards):
         assert (tot_c, tot_s) == plan.count()
     with pytest.raises(B.DMError):
         B.dm_match_shard(ctx.h, plan.h, 3, 3)
+
+
+# ------------------------------------------------------------------ fused last two joins ----
+@pytest.mark.parametrize("graph", ["hh", "grid", "rr3"])
+def test_fused_last_two_joins_equal_unfused_and_oracle(ctx, B, hh, graph):
+    # a counted plan's last two joins run as one kernel (the table between them stays in
+    # shared memory); counts and checksums must equal the step-by-step run and the oracle,
+    # also when the pair starts at the seed step (two-step plans) and with back-edges
+    if graph == "hh":
+        g, gid = hh
+        pats = [I.path(7), I.path(10), I.path(13), I.path(22), I.cycle(12), I.sub_patch(g, 16, 2),
+                I.sub_patch(g, 25, 9), I.layout_query(g, 3)]
+    elif graph == "grid":
+        g = I.grid(9, 9)
+        gid = ctx.load(g)
+        pats = [I.path(5), I.path(8), I.cycle(4), I.cycle(8), I.grid(2, 3), I.sub_patch(g, 9, 1)]
+    else:
+        g = I.random_regular3(200, 7)
+        gid = ctx.load(g)
+        pats = [I.path(6), I.path(9), I.star(3), I.random_tree(8, 5), I.sub_patch(g, 10, 4)]
+    for p in pats:
+        plan = ctx.plan(gid, p)
+        ref = oracle.enumerate(g, p, rows=False, threads=8)
+        B.dm_set_fusion(ctx.h, True)
+        fused = plan.count()
+        B.dm_set_fusion(ctx.h, False)
+        plain = plan.count()
+        B.dm_set_fusion(ctx.h, True)
+        assert fused == plain == (ref.count, ref.checksum), p.name
