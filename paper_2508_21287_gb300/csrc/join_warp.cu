@@ -2,8 +2,10 @@
 //
 // Every warp owns 32-row tiles of R: it copies a tile into its own slice of shared memory
 // (row stride join_row_stride(w), padding -1), looks up each row's key group (one row per lane),
-// scans the group sizes with shuffles, and walks the candidates 32 at a time (one per lane):
-// motif-row loads, extra key equalities, injectivity of the new vertices against the whole row
+// scans the group sizes with shuffles, and walks the candidates 32 at a time (one per lane; a
+// candidate finds its tile row by a binary search, with shuffles, over the rows' first-candidate
+// offsets held in registers): motif-row loads, extra key equalities, injectivity of the new
+// vertices against the whole row
 // with int4 compares, back-edge bitmap tests, FP32 score. Survivors are appended to the warp's
 // staging list with a ballot, new vertices included; when it fills, and at the end of the
 // tile, the warp reserves its output range with one atomic and writes the rows element by
@@ -27,8 +29,6 @@ struct WarpSmem {
   int32_t *rows;              // WT x wsv
   unsigned long long *part;   // WT checksum partial sums (count mode)
   float *rs;                  // WT scores
-  int32_t *gstart, *goff;     // WT, WT + 1
-  int32_t *cand_row;          // 32
   int32_t *st_r, *st_m;       // WSTAGE survivors: tile row, motif row
   float *st_s;                // WSTAGE scores
   int32_t *st_nv;             // WSTAGE x STAGE_NV new vertices
@@ -36,7 +36,7 @@ struct WarpSmem {
 
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int wsv) {
   size_t b = (size_t)WT * wsv * 4;
-  b += (size_t)WT * 8 + (size_t)WT * 4 + (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
+  b += (size_t)WT * 8 + (size_t)WT * 4;
   b = (b + 15) / 16 * 16;
   b += (size_t)WSTAGE * 12 + (size_t)WSTAGE * STAGE_NV * 4;
   return (b + 15) / 16 * 16;
@@ -51,10 +51,6 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int wsv) {
   off += (size_t)WT * 8;
   m.rs = (float *)(base + off);
   off += (size_t)WT * 4;
-  m.gstart = (int32_t *)(base + off);
-  m.goff = m.gstart + WT;
-  m.cand_row = m.goff + WT + 1;
-  off += (size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4;
   off = (off + 15) / 16 * 16;
   m.st_r = (int32_t *)(base + off);
   m.st_m = m.st_r + WSTAGE;
@@ -305,6 +301,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     const int64_t r0 = t * WT;
     const int nr = (int)imin64(WT, N - r0);
     int C;
+    int g_start = 0, g_off = 0;  // this lane's tile row: its key group's first motif row and first candidate
     if (!seed) {
       const int32_t *src = a.R + r0 * w;
       const int ne = nr * w;
@@ -363,9 +360,8 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
         if (lane >= o) incl += v;
       }
       C = __shfl_sync(FULL_MASK, incl, 31);
-      W.gstart[lane] = start;
-      W.goff[lane] = incl - len;
-      if (lane == 0) W.goff[WT] = C;
+      g_start = start;
+      g_off = incl - len;  // nondecreasing over the lanes; C for lanes past the tile
       __syncwarp();
     } else {
       C = nr;
@@ -373,22 +369,18 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     acc_cand += lane == 0 ? (unsigned long long)C : 0ull;
     int nst = 0;
     for (int cb = 0; cb < C; cb += 32) {
-      if (!seed) {  // tile row of each candidate of this chunk
-        if (lane < nr) {
-          int lo = max(W.goff[lane], cb), hi = min(W.goff[lane + 1], cb + 32);
-          for (int c = lo; c < hi; c++) W.cand_row[c - cb] = lane;
-        }
-        __syncwarp();
-      }
       const int c = cb + lane;
       const bool valid = c < C;
       int r = 0, m = 0;
-      if (valid) {
-        if (seed) m = (int)(a.seed_lo + r0 + c);
-        else {
-          r = W.cand_row[lane];
-          m = W.gstart[r] + (c - W.goff[r]);
-        }
+      if (!seed) {  // tile row of candidate c: the last row whose first candidate is at or before c
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+          if (__shfl_sync(FULL_MASK, g_off, r + step) <= c) r += step;
+        const int ms = __shfl_sync(FULL_MASK, g_start, r), mo = __shfl_sync(FULL_MASK, g_off, r);
+        if (valid) m = ms + (c - mo);
+        else r = 0;
+      } else if (valid) {
+        m = (int)(a.seed_lo + r0 + c);
       }
       int32_t nv[MAXNEW];
       const int32_t *trow = mrows + (int64_t)m * mw;  // row 0 for idle lanes: a valid address
@@ -424,7 +416,6 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
           nst = 0;
         }
       }
-      __syncwarp();  // cand_row is rewritten by the next chunk
     }
     if (MODE == 0 && nst > 0) wflush<STG>(a, W, code, wsv, nst, nsum);
     __syncwarp();  // the next tile overwrites this warp's rows
@@ -518,21 +509,14 @@ cudaError_t launch_wjoin(const JoinArgs &a, int grid, cudaStream_t s, bool pdl) 
 // k_joinw's counted step. The table between A and B, the largest of a path-like plan, is
 // never written to or read from global memory.
 
-// Key groups of a tile's rows and the tile row of each candidate of a round.
-struct TileGroups {
-  int32_t *gstart, *goff, *cand_row;  // WT, WT + 1, 32
-};
-
 struct FSmem {
   int32_t *rowsA, *rowsB;               // WT x wsA, WT x wsB
   unsigned long long *partA, *partB;    // checksum terms of each A row / B row
-  TileGroups ga, gb;                    // A's tile (live across B's joins) and B's tile
 };
 
 __host__ __device__ __forceinline__ size_t fused_warp_bytes(int wsA, int wsB) {
   size_t b = (size_t)WT * wsA * 4 + (size_t)WT * wsB * 4;
   b += (size_t)WT * 8 * 2;
-  b += 2 * ((size_t)WT * 4 + (size_t)(WT + 1) * 4 + 32 * 4);
   return (b + 15) / 16 * 16;
 }
 
@@ -545,13 +529,6 @@ __device__ __forceinline__ FSmem fused_smem(unsigned char *base, int wsA, int ws
   off += (size_t)WT * wsB * 4;
   m.partA = (unsigned long long *)(base + off);
   m.partB = m.partA + WT;
-  off += (size_t)WT * 8 * 2;
-  m.ga.gstart = (int32_t *)(base + off);
-  m.ga.goff = m.ga.gstart + WT;
-  m.ga.cand_row = m.ga.goff + WT + 1;
-  m.gb.gstart = m.ga.cand_row + 32;
-  m.gb.goff = m.gb.gstart + WT;
-  m.gb.cand_row = m.gb.goff + WT + 1;
   return m;
 }
 
@@ -559,9 +536,11 @@ struct FusedArgs {
   JoinArgs a, b;
 };
 
-// Look up the key groups of the nr rows of a shared tile (lane = row) and scan their sizes;
-// returns the number of candidates.
-__device__ __forceinline__ int tile_groups(const JoinArgs &a, const int32_t *rows, int ws, int nr, const TileGroups &F) {
+// Look up the key groups of the nr rows of a shared tile (lane = row): g_start = the first motif
+// row of the lane's group, g_off = the lane's first candidate (nondecreasing over the lanes; C
+// for lanes past the tile). Returns the number of candidates C.
+__device__ __forceinline__ int tile_groups(const JoinArgs &a, const int32_t *rows, int ws, int nr, int &g_start,
+                                           int &g_off) {
   const int lane = threadIdx.x & 31;
   int start = 0, len = 0;
   if (lane < nr) {
@@ -574,29 +553,24 @@ __device__ __forceinline__ int tile_groups(const JoinArgs &a, const int32_t *row
     const int v = __shfl_up_sync(FULL_MASK, incl, o);
     if (lane >= o) incl += v;
   }
-  const int C = __shfl_sync(FULL_MASK, incl, 31);
-  F.gstart[lane] = start;
-  F.goff[lane] = incl - len;
-  if (lane == 0) F.goff[WT] = C;
-  __syncwarp();
-  return C;
+  g_start = start;
+  g_off = incl - len;
+  __syncwarp();  // shared words the lanes wrote before (checksum terms) are read by others next
+  return __shfl_sync(FULL_MASK, incl, 31);
 }
 
-// Candidate c (this lane's, of the round starting at cb) of a tile: its row and motif row.
-__device__ __forceinline__ void round_rows(const TileGroups &F, int nr, int cb, int C, int &r, int &m) {
-  const int lane = threadIdx.x & 31;
-  if (lane < nr) {
-    const int lo = max(F.goff[lane], cb), hi = min(F.goff[lane + 1], cb + 32);
-    for (int c = lo; c < hi; c++) F.cand_row[c - cb] = lane;
-  }
-  __syncwarp();
+// Candidate c = cb + lane of a tile: its tile row r (the last row whose first candidate is at or
+// before c, found by binary search over the lanes' g_off) and its motif row m; 0 and 0 past C.
+__device__ __forceinline__ void round_rows(int g_start, int g_off, int cb, int C, int &r, int &m) {
+  const int c = cb + (threadIdx.x & 31);
   r = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1)
+    if (__shfl_sync(FULL_MASK, g_off, r + step) <= c) r += step;
+  const int ms = __shfl_sync(FULL_MASK, g_start, r), mo = __shfl_sync(FULL_MASK, g_off, r);
   m = 0;
-  const int c = cb + lane;
-  if (c < C) {
-    r = F.cand_row[lane];
-    m = F.gstart[r] + (c - F.goff[r]);
-  }
+  if (c < C) m = ms + (c - mo);
+  else r = 0;
 }
 
 // Join and count the nb rows of the B tile (step B, its rows' checksum terms in partB).
@@ -605,14 +579,15 @@ __device__ __forceinline__ void count_b_tile(const JoinArgs &b, const FSmem &F, 
                                              unsigned long long &acc_rows, unsigned long long &acc_sum,
                                              unsigned long long &acc_cand) {
   const int lane = threadIdx.x & 31;
-  const int C = tile_groups(b, F.rowsB, wsB, nb, F.gb);
+  int g_start, g_off;
+  const int C = tile_groups(b, F.rowsB, wsB, nb, g_start, g_off);
   acc_cand += lane == 0 ? (unsigned long long)C : 0ull;
   WarpSmem W{};
   W.rows = F.rowsB;
   const int w = b.w;
   for (int cb = 0; cb < C; cb += 32) {
     int r, m;
-    round_rows(F.gb, nb, cb, C, r, m);
+    round_rows(g_start, g_off, cb, C, r, m);
     const bool valid = cb + lane < C;
     int32_t nv[NB];
     const int32_t *trow = b.ix.rows + (int64_t)m * b.ix.mw;
@@ -626,8 +601,8 @@ __device__ __forceinline__ void count_b_tile(const JoinArgs &b, const FSmem &F, 
       acc_sum += dmix64(p + (unsigned long long)(uint32_t)b.wo);
       acc_rows++;
     }
-    __syncwarp();  // cand_row is rewritten by the next round
   }
+  __syncwarp();  // the B tile is refilled next
 }
 
 template <int NA, int NB>
@@ -660,6 +635,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
     const int64_t r0 = t * WT;
     const int nr = (int)imin64(WT, N - r0);
     int C;
+    int ga_start = 0, ga_off = 0;
     if (!seed) {
       const int32_t *src = a.R + r0 * wA;
       if (lane == 0 && t + nw < ntiles) {  // the warp's next tile: bring it into L2 meanwhile
@@ -680,7 +656,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
       }
       __syncwarp();
       if (lane < nr) F.partA[lane] = row_terms_last(F.rowsA + lane * wsA, wA, tq);  // B positions
-      C = tile_groups(a, F.rowsA, wsA, nr, F.ga);
+      C = tile_groups(a, F.rowsA, wsA, nr, ga_start, ga_off);
     } else {
       C = nr;
     }
@@ -690,7 +666,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
       if (seed) {
         if (cb + lane < C) m = (int)(a.seed_lo + r0 + cb + lane);
       } else {
-        round_rows(F.ga, nr, cb, C, r, m);
+        round_rows(ga_start, ga_off, cb, C, r, m);
       }
       const bool valid = cb + lane < C;
       int32_t nv[NA];
@@ -723,7 +699,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
       }
       nb += K;
       rows_a += lane == 0 ? (unsigned long long)K : 0ull;
-      __syncwarp();  // B's tile and cand_row are read next
+      __syncwarp();  // B's tile is read next
     }
     __syncwarp();  // the next tile overwrites this warp's A rows
   }
