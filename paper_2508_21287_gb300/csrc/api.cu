@@ -770,6 +770,7 @@ struct Exec {
     int32_t *prev_rows = nullptr;
     float *prev_score = nullptr;
     int64_t prev_cap = 0;
+    int32_t prev_rs = 0;
     // a counted plan's last two joins run as one kernel when they qualify: the table between
     // them stays in shared memory
     const bool fuse = c->fuse_last && S >= 2 && st[S - 1].base.mode == 1 &&
@@ -781,10 +782,16 @@ struct Exec {
       a.ctr = c->d_ctr_steps + (size_t)j * CTR_N;
       a.out_next = nullptr;
       a.nx.nkeys = -1;
-      int64_t rb = 4ll * a.wo + (a.scored ? 4 : 0);
+      // a table the next launch reads has rows padded to 16 bytes (whole-int4 loads and stores)
+      bool identity = true;
+      for (int q = 0; q < a.wo; q++) identity &= a.src_col[q] == q;
+      const bool pad = a.mode == 0 && j + 1 < S && a.n_new >= 1 && a.n_new <= 4 && a.wo == a.w + a.n_new && identity;
+      a.rs_out = pad ? (a.wo + 3) / 4 * 4 : 0;
+      const int64_t ows = a.rs_out ? a.rs_out : a.wo;  // output row stride in words
+      int64_t rb = 4ll * ows + (a.scored ? 4 : 0);
       int64_t cap = std::max<int64_t>(1, ((int64_t)half - 512) / rb);
       int32_t *orows = (int32_t *)buf[j & 1];
-      float *oscore = (float *)(buf[j & 1] + ((size_t)cap * a.wo * 4 + 255) / 256 * 256);
+      float *oscore = (float *)(buf[j & 1] + ((size_t)cap * ows * 4 + 255) / 256 * 256);
       a.out = a.mode == 0 ? orows : nullptr;
       a.outs = (a.mode == 0 && a.scored) ? oscore : nullptr;
       a.out_cap = cap;
@@ -798,6 +805,7 @@ struct Exec {
         a.N = 0;
         a.n_dev = c->d_ctr_steps + (size_t)(j - 1) * CTR_N + CTR_ROWS;
         a.in_cap = prev_cap;
+        a.rs_in = prev_rs;
       }
       if (fuse && j == S - 2) {
         JoinArgs b = st[S - 1].base;
@@ -816,6 +824,7 @@ struct Exec {
       prev_rows = orows;
       prev_score = a.outs;
       prev_cap = cap;
+      prev_rs = a.rs_out;
     }
     if (c->timing) CK(cudaEventRecord(c->ev1, c->stream));
     CK(cudaMemcpyAsync(c->h_ctr_steps, c->d_ctr_steps, sizeof(unsigned long long) * CTR_N * S,

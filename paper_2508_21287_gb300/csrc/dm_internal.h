@@ -178,6 +178,12 @@ struct JoinArgs {
   // seed mode with n_shards > 1: keep only motif rows whose position-0 vertex is congruent to
   // shard modulo n_shards (one shard of the first table R_0)
   int32_t shard, n_shards;
+  // padded layouts of the intermediate tables a device-driven chain passes from launch to
+  // launch: rows of rs_in (R) / rs_out (out) words, a multiple of 4, so every row starts on a
+  // 16-byte boundary; the words past w (past wo) are -1. 0: rows are packed (stride w / wo).
+  // A padded output needs the working-column order (the row's w words, then the n_new <= 4 new
+  // vertices).
+  int32_t rs_in, rs_out;
 };
 
 }  // namespace dmi

@@ -175,9 +175,18 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x
   return t;  // valid in thread 0
 }
 
+// Checksum term of value v at output position p - 1 (p = 1 + position < 2^30): SplitMix64's
+// finaliser of (p << 32) | v, whose first xorshift leaves the high word p unchanged.
+__device__ __forceinline__ unsigned long long pos_term(uint32_t p, int32_t v) {
+  const uint32_t lo = (uint32_t)v ^ ((uint32_t)v >> 30) ^ (p << 2);
+  unsigned long long z = (((unsigned long long)p << 32) | lo) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // Checksum term of vertex v at output position q.
 __device__ __forceinline__ unsigned long long col_term(int q, int32_t v) {
-  return dmix64(((unsigned long long)(uint32_t)(q + 1) << 32) | (uint32_t)v);
+  return pos_term((uint32_t)(q + 1), v);
 }
 
 // true when v equals one of the first w words of a shared-memory row (stride join_row_stride,

@@ -172,24 +172,49 @@ __device__ __forceinline__ unsigned long long row_terms_last(const int32_t *row,
   int c4 = 0;
   for (; c4 + 1 < nq; c4 += 2) {
     const int4 x = r4[c4], y = r4[c4 + 1], qx = q4[c4], qy = q4[c4 + 1];
-    p0 += dmix64(((unsigned long long)(uint32_t)qx.x << 32) | (uint32_t)x.x) +
-          dmix64(((unsigned long long)(uint32_t)qx.y << 32) | (uint32_t)x.y);
-    p1 += dmix64(((unsigned long long)(uint32_t)qx.z << 32) | (uint32_t)x.z) +
-          dmix64(((unsigned long long)(uint32_t)qx.w << 32) | (uint32_t)x.w);
-    p0 += dmix64(((unsigned long long)(uint32_t)qy.x << 32) | (uint32_t)y.x) +
-          dmix64(((unsigned long long)(uint32_t)qy.y << 32) | (uint32_t)y.y);
-    p1 += dmix64(((unsigned long long)(uint32_t)qy.z << 32) | (uint32_t)y.z) +
-          dmix64(((unsigned long long)(uint32_t)qy.w << 32) | (uint32_t)y.w);
+    p0 += pos_term(qx.x, x.x) +
+          pos_term(qx.y, x.y);
+    p1 += pos_term(qx.z, x.z) +
+          pos_term(qx.w, x.w);
+    p0 += pos_term(qy.x, y.x) +
+          pos_term(qy.y, y.y);
+    p1 += pos_term(qy.z, y.z) +
+          pos_term(qy.w, y.w);
   }
   if (c4 < nq) {
     const int4 x = r4[c4], qx = q4[c4];
-    p0 += dmix64(((unsigned long long)(uint32_t)qx.x << 32) | (uint32_t)x.x) +
-          dmix64(((unsigned long long)(uint32_t)qx.y << 32) | (uint32_t)x.y);
-    p1 += dmix64(((unsigned long long)(uint32_t)qx.z << 32) | (uint32_t)x.z) +
-          dmix64(((unsigned long long)(uint32_t)qx.w << 32) | (uint32_t)x.w);
+    p0 += pos_term(qx.x, x.x) +
+          pos_term(qx.y, x.y);
+    p1 += pos_term(qx.z, x.z) +
+          pos_term(qx.w, x.w);
   }
-  for (int c = 4 * nq; c < w; c++) p0 += dmix64(((unsigned long long)(uint32_t)tq[c] << 32) | (uint32_t)row[c]);
+  for (int c = 4 * nq; c < w; c++) p0 += pos_term(tq[c], row[c]);
   return p0 + p1;
+}
+
+// Copy nr rows of a padded table (stride rs = 4q words, 16-byte aligned rows, padding -1) into a
+// warp tile (stride wsv >= rs, a multiple of 4): whole int4s; the tile's words past rs keep
+// their -1.
+__device__ __forceinline__ void load_padded_tile(int32_t *rows, int wsv, const int32_t *src, int nr, int rs) {
+  const int lane = threadIdx.x & 31;
+  const int q = rs >> 2, qs = wsv >> 2, n4 = nr * q;
+  const int4 *s4 = (const int4 *)src;
+  int4 *d4 = (int4 *)rows;
+  if (qs == q) {
+    for (int k = lane; k < n4; k += 32) d4[k] = __ldg(s4 + k);
+  } else {
+    int r = lane / q, c = lane - r * q;  // int4 k = r * q + c, advanced with carry
+    const int dr = 32 / q, dc = 32 % q;
+    for (int k = lane; k < n4; k += 32) {
+      d4[r * qs + c] = __ldg(s4 + k);
+      r += dr;
+      c += dc;
+      if (c >= q) {
+        c -= q;
+        r++;
+      }
+    }
+  }
 }
 
 // Word q of staged survivor s's output row. code[q] < 0x100: working column of the R row; else
@@ -205,15 +230,16 @@ __device__ __forceinline__ int32_t out_word(const JoinArgs &a, const WarpSmem &W
 
 // Write the warp's staged survivors: one reservation, then coalesced stores, 16 bytes per lane
 // from the first 16-byte boundary of the reserved range (scalar head and tail).
-template <bool STG>
-__device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int wsv, int n,
-                                       unsigned long long &nsum) {
+// Reserve the output range of n staged survivors (one atomic); returns its first row and sets Kc
+// to the rows that fit the output (the overflow flag is raised for the rest). Writes the
+// survivors' scores and next-step candidate counts.
+__device__ __forceinline__ long long wreserve(const JoinArgs &a, const WarpSmem &W, int wsv, int n, int &Kc,
+                                              unsigned long long &nsum) {
   const int lane = threadIdx.x & 31;
-  const int wo = a.wo;
   long long base = 0;
   if (lane == 0) base = (long long)atomicAdd(a.ctr + CTR_ROWS, (unsigned long long)n);
   base = __shfl_sync(FULL_MASK, base, 0);
-  int Kc = n;
+  Kc = n;
   if (base + n > a.out_cap) {
     Kc = (int)imax64(0, a.out_cap - base);
     if (lane == 0) atomicOr(a.ctr + CTR_OVF, 1ull);
@@ -232,6 +258,53 @@ __device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, con
       nsum += (unsigned long long)ln;
     }
   }
+  return base;
+}
+
+// Write the warp's staged survivors into a padded output (row stride a.rs_out = 4 q4 words, the
+// rows 16-byte aligned): output int4 k of survivor s is int4 k of its tile row (the row's w
+// words, then -1 padding) with the survivor's new vertices put at positions w .. w + NN - 1;
+// int4s past the tile row are -1. Lanes write consecutive int4s.
+template <int NN>
+__device__ __forceinline__ void wflush_padded(const JoinArgs &a, const WarpSmem &W, int wsv, int n,
+                                              unsigned long long &nsum) {
+  const int lane = threadIdx.x & 31;
+  int Kc;
+  const long long base = wreserve(a, W, wsv, n, Kc, nsum);
+  const int q4 = a.rs_out >> 2, wq = wsv >> 2, w = a.w;
+  int4 *dst = (int4 *)(a.out + base * a.rs_out);
+  const int n4 = Kc * q4;
+  int s = lane / q4, k = lane - s * q4;  // int4 e = s * q4 + k, advanced with carry
+  const int ds = 32 / q4, dk = 32 % q4;
+  for (int e = lane; e < n4; e += 32) {
+    int4 v = make_int4(-1, -1, -1, -1);
+    if (k < wq) v = *(const int4 *)(W.rows + W.st_r[s] * wsv + 4 * k);
+    const int p = 4 * k - w;  // new-vertex index of v.x
+    if (p > -4 && p < NN) {
+      const int32_t *nvs = W.st_nv + s * STAGE_NV;
+      if (p >= 0) v.x = nvs[p];
+      if (p + 1 >= 0 && p + 1 < NN) v.y = nvs[p + 1];
+      if (p + 2 >= 0 && p + 2 < NN) v.z = nvs[p + 2];
+      if (p + 3 < NN) v.w = nvs[p + 3];
+    }
+    dst[e] = v;
+    s += ds;
+    k += dk;
+    if (k >= q4) {
+      k -= q4;
+      s++;
+    }
+  }
+  __syncwarp();
+}
+
+template <bool STG>
+__device__ __forceinline__ void wflush(const JoinArgs &a, const WarpSmem &W, const int16_t *code, int wsv, int n,
+                                       unsigned long long &nsum) {
+  const int lane = threadIdx.x & 31;
+  const int wo = a.wo;
+  int Kc;
+  const long long base = wreserve(a, W, wsv, n, Kc, nsum);
   int32_t *dst = a.out + base * wo;
   const int ne = Kc * wo;
   const int h = min((int)((4 - (((uintptr_t)dst >> 2) & 3)) & 3), ne);  // words before a 16-byte boundary
@@ -303,14 +376,17 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
     int C;
     int g_start = 0, g_off = 0;  // this lane's tile row: its key group's first motif row and first candidate
     if (!seed) {
-      const int32_t *src = a.R + r0 * w;
+      const int rsi = a.rs_in ? a.rs_in : w;  // row stride of R
+      const int32_t *src = a.R + r0 * rsi;
       const int ne = nr * w;
       if (lane == 0 && t + nw < ntiles) {  // the warp's next tile: bring it into L2 meanwhile
-        const int32_t *nsrc = a.R + (t + nw) * WT * w;
-        const uint32_t nb = (uint32_t)(imin64(WT, N - (t + nw) * WT) * w * 4) & ~15u;
+        const int32_t *nsrc = a.R + (t + nw) * WT * rsi;
+        const uint32_t nb = (uint32_t)(imin64(WT, N - (t + nw) * WT) * rsi * 4) & ~15u;
         if (nb && (((uintptr_t)nsrc) & 15) == 0) l2_prefetch(nsrc, nb);
       }
-      if ((((uintptr_t)src) & 15) == 0) {  // 16-byte loads; their words go to the padded rows
+      if (a.rs_in) {
+        load_padded_tile(W.rows, wsv, src, nr, rsi);
+      } else if ((((uintptr_t)src) & 15) == 0) {  // 16-byte loads; their words go to the padded rows
         const int n4 = ne >> 2;
         int r = (lane * 4) / w, c = lane * 4 - r * w;  // first word 4 * k of the lane, with carry
         const int dr = 128 / w, dc = 128 % w;
@@ -394,7 +470,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
           unsigned long long p = seed ? 0ull : W.part[r];
 #pragma unroll
           for (int i = 0; i < MAXNEW; i++)
-            if (i < nnew_of<MAXNEW>(a)) p += col_term(npos[i], nv[i]);
+            if (i < nnew_of<MAXNEW>(a)) p += pos_term(npos[i] + 1, nv[i]);
           acc_sum += dmix64(p + (unsigned long long)(uint32_t)wo);
           acc_rows++;
         }
@@ -412,12 +488,16 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinw(const __grid_constant__ Joi
         nst += __popc(bal);
         __syncwarp();
         if (nst > WSTAGE - 32) {
-          wflush<STG>(a, W, code, wsv, nst, nsum);
+          if (STG && a.rs_out) wflush_padded<STG ? MAXNEW : 1>(a, W, wsv, nst, nsum);
+          else wflush<STG>(a, W, code, wsv, nst, nsum);
           nst = 0;
         }
       }
     }
-    if (MODE == 0 && nst > 0) wflush<STG>(a, W, code, wsv, nst, nsum);
+    if (MODE == 0 && nst > 0) {
+      if (STG && a.rs_out) wflush_padded<STG ? MAXNEW : 1>(a, W, wsv, nst, nsum);
+      else wflush<STG>(a, W, code, wsv, nst, nsum);
+    }
     __syncwarp();  // the next tile overwrites this warp's rows
   }
   unsigned long long tc = block_sum_u64<WJ_BLK>(acc_cand, s_red);
@@ -597,7 +677,7 @@ __device__ __forceinline__ void count_b_tile(const JoinArgs &b, const FSmem &F, 
     if (valid && wcheck<NB>(b, W, wsB, false, r, m, nv, sc)) {
       unsigned long long p = F.partB[r];
 #pragma unroll
-      for (int i = 0; i < NB; i++) p += dmix64(((unsigned long long)(uint32_t)tq[w + i] << 32) | (uint32_t)nv[i]);
+      for (int i = 0; i < NB; i++) p += pos_term(tq[w + i], nv[i]);
       acc_sum += dmix64(p + (unsigned long long)(uint32_t)b.wo);
       acc_rows++;
     }
@@ -637,21 +717,26 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
     int C;
     int ga_start = 0, ga_off = 0;
     if (!seed) {
-      const int32_t *src = a.R + r0 * wA;
+      const int rsi = a.rs_in ? a.rs_in : wA;  // row stride of R
+      const int32_t *src = a.R + r0 * rsi;
       if (lane == 0 && t + nw < ntiles) {  // the warp's next tile: bring it into L2 meanwhile
-        const int32_t *nsrc = a.R + (t + nw) * WT * wA;
-        const uint32_t nbytes = (uint32_t)(imin64(WT, N - (t + nw) * WT) * wA * 4) & ~15u;
+        const int32_t *nsrc = a.R + (t + nw) * WT * rsi;
+        const uint32_t nbytes = (uint32_t)(imin64(WT, N - (t + nw) * WT) * rsi * 4) & ~15u;
         if (nbytes && (((uintptr_t)nsrc) & 15) == 0) l2_prefetch(nsrc, nbytes);
       }
-      int r = lane / wA, c = lane % wA;  // element e = r * wA + c, advanced with carry
-      const int dr = 32 / wA, dc = 32 % wA;
-      for (int e = lane; e < nr * wA; e += 32) {
-        F.rowsA[r * wsA + c] = __ldg(src + e);
-        r += dr;
-        c += dc;
-        if (c >= wA) {
-          c -= wA;
-          r++;
+      if (a.rs_in) {
+        load_padded_tile(F.rowsA, wsA, src, nr, rsi);
+      } else {
+        int r = lane / wA, c = lane % wA;  // element e = r * wA + c, advanced with carry
+        const int dr = 32 / wA, dc = 32 % wA;
+        for (int e = lane; e < nr * wA; e += 32) {
+          F.rowsA[r * wsA + c] = __ldg(src + e);
+          r += dr;
+          c += dc;
+          if (c >= wA) {
+            c -= wA;
+            r++;
+          }
         }
       }
       __syncwarp();
@@ -693,7 +778,7 @@ __global__ void __launch_bounds__(WJ_BLK, 4) k_joinf(const __grid_constant__ Fus
 #pragma unroll
         for (int i = 0; i < NA; i++) {
           d[wA + i] = nv[i];
-          p += dmix64(((unsigned long long)(uint32_t)tq[wA + i] << 32) | (uint32_t)nv[i]);
+          p += pos_term(tq[wA + i], nv[i]);
         }
         F.partB[slot] = p;
       }
