@@ -23,7 +23,7 @@
 
 namespace dmk {
 
-constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 64, STAGE_NV = 4;
+constexpr int WJ_BLK = 256, WJ_WARPS = WJ_BLK / 32, WT = 32, WSTAGE = 96, STAGE_NV = 4;
 
 struct WarpSmem {
   int32_t *rows;              // WT x wsv
