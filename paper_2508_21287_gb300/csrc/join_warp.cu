@@ -113,6 +113,16 @@ __device__ __forceinline__ int nnew_of(const JoinArgs &a) {
   return MAXNEW <= STAGE_NV ? MAXNEW : a.n_new;
 }
 
+// New vertex i (uniform over the warp) of a candidate, from the preloaded registers.
+template <int MAXNEW>
+__device__ __forceinline__ int32_t pick_nv(const int32_t (&nv)[MAXNEW], int i) {
+  int32_t v = nv[0];
+#pragma unroll
+  for (int k = 1; k < MAXNEW; k++)
+    if (i == k) v = nv[k];
+  return v;
+}
+
 // Check one candidate against row r of the warp tile (new vertices preloaded).
 template <int MAXNEW>
 __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int wsv, bool seed, int r, int m,
@@ -150,8 +160,15 @@ __device__ __forceinline__ bool wcheck(const JoinArgs &a, const WarpSmem &W, int
     }
   }
   for (int e = 0; e < a.n_be && ok; e++) {
-    int32_t va = join_value(a, rrow, trow, a.be_a[e]);
-    int32_t vb = join_value(a, rrow, trow, a.be_b[e]);
+    const int ca = a.be_a[e], cb = a.be_b[e];
+    int32_t va, vb;
+    if (MAXNEW <= STAGE_NV) {  // new vertices from the registers
+      va = ca < a.w ? rrow[ca] : pick_nv<MAXNEW>(nv, ca - a.w);
+      vb = cb < a.w ? rrow[cb] : pick_nv<MAXNEW>(nv, cb - a.w);
+    } else {
+      va = join_value(a, rrow, trow, ca);
+      vb = join_value(a, rrow, trow, cb);
+    }
     ok = adjacent(a, va, vb);
     if (ok && a.scored && a.eerr) sc += edge_weight(a, va, vb);
   }
