@@ -47,10 +47,11 @@ BATCH = 32
 WORKLOAD_C2 = ("C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step of 10-30 vertices, all "
                "embeddings + FP32 scores + top-100")
 
-# Mean DRAM bytes (read + write) per k_joinw launch, from the ncu capture of one step of the
-# workload (the profiles/ summary of that workload gives the command), keyed by workload and by
-# the digest of the join kernel's sources at capture time: after any change to those sources
-# the number no longer describes the kernel and the line reports null.
+# Mean DRAM bytes (read + write) per k_joinw launch over the join launches of one step of the
+# workload, from one ncu pass (metrics dram__bytes_read.sum and dram__bytes_write.sum, with
+# --clock-control none) over `bench.py --steps 1 --warmup 0 --no-extras --no-cpu --no-e2e`,
+# keyed by workload and by the digest of the join kernel's sources at capture time: after any
+# change to those sources the number no longer describes the kernel and the line reports null.
 JOIN_SOURCES = ("join_warp.cu", "join_device.cuh", "dm_internal.h")
 JOIN_TRAFFIC_BYTES_PER_LAUNCH: dict[tuple[str, str], float] = {
     # C3 heavy-hex 53x59, the default workload: 283 join launches of one step
