@@ -273,6 +273,17 @@ def wl_name(args, kind=None):
     return WORKLOAD_C3.format(m=m, n=n, V=5 * m * n + 4 * m + 4 * n - 1)
 
 
+def workload_config(args, kind, n_queries):
+    """The keys of `config` that describe the workload itself (both arms report them)."""
+    cfg = {"workload": wl_name(args, kind), "queries_per_step": n_queries}
+    if kind in ("c2", "c3"):
+        cfg["data_graph"] = ("heavy-hex 4x6" if kind == "c2" else
+                             {"grid": "grid 60x60", "rr3": "random 3-regular V=4096"}.get(
+                                 args.graph, "heavy-hex " + args.hh.replace(",", "x")))
+        cfg["output"] = "count + 64-bit checksum" if kind == "c3" else "all embeddings + FP32 scores + top-100"
+    return cfg
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -290,7 +301,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl_name(args), "parallelism": "host cores"},
+            "config": dict(workload_config(args, args.workload, len(pats)), parallelism="host cores"),
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -495,13 +506,9 @@ def measure_queries(args, kind: str, with_e2e: bool, with_cpu: bool, fuse: bool 
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong" if shard else "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl_name(args, kind), "queries_per_step": len(pats),
+            "config": {**workload_config(args, kind, len(pats)),
                        "embeddings_per_step": emb_total / args.steps / world,
-                       "data_graph": ("heavy-hex 4x6" if not count_mode else
-                                      {"grid": "grid 60x60", "rr3": "random 3-regular V=4096"}.get(
-                                          args.graph, "heavy-hex " + args.hh.replace(",", "x"))),
                        "motifs": "M4-O,M6-O,M2" if count_mode and args.graph == "grid" else "M4,M2",
-                       "output": "count + 64-bit checksum" if count_mode else "all embeddings + FP32 scores + top-100",
                        "l2": "flushed between steps (256 MiB write); intermediate tables far larger than L2"
                              if count_mode else "flushed between steps (256 MiB write)",
                        "parallelism": (f"R_0 shards x{world} (2 x u64 sum per query)" if shard
