@@ -56,7 +56,12 @@ def check_all(ctx, gid, g, p, motifs=None, order=0, chunk_rows=0, scores=True, j
 def check_topk(ctx, gid, g, p, k, score_form=0, **kw):
     plan = ctx.plan(gid, p, **kw)
     rows, scores = plan.topk(k)
-    allrows = oracle.enumerate(g, p).rows
+    assert_topk(g, p, oracle.enumerate(g, p).rows, rows, scores, k, score_form)
+
+
+def assert_topk(g, p, allrows, rows, scores, k, score_form=0):
+    """rows/scores are a correct top-k of the embeddings allrows (oracle order): scores equal the
+    oracle's k best within RTOL, and every row scoring clearly below the k-th one is present."""
     m = min(k, len(allrows))
     assert rows.shape == (m, p.n)
     if m == 0:
@@ -372,6 +377,53 @@ def test_largest_heavy_hex_p24(ctx):
     cnt, cs = plan.count()
     ref = oracle.enumerate(g, I.path(24), rows=False, threads=16)
     assert cnt == ref.count and cs == ref.checksum
+
+
+def test_c3_benchmark_queries_match_oracle(ctx, B):
+    # the benchmark's default workload at full size: heavy-hex 53x59 and its 32 seeded queries,
+    # each planned and counted as bench.py times them (one context, the device-driven chain of
+    # join launches with padded intermediate tables), unfused and with the last two joins fused;
+    # every count and checksum equals the oracle's
+    import bench
+    g, pats = bench.workload(0, bench.BATCH, "c3")
+    gid = ctx.load(g)
+    try:
+        for p in pats:
+            ref = oracle.enumerate(g, p, rows=False, threads=16)
+            plan = ctx.plan(gid, p)
+            for fuse in (0, 1):
+                B.dm_set_fusion(ctx.h, fuse)
+                assert plan.count() == (ref.count, ref.checksum), (p.n, fuse)
+                st = ctx.stats()
+                assert st["chunks"] == st["n_steps"]  # one device-driven chain, no streaming
+    finally:
+        B.dm_set_fusion(ctx.h, 0)
+
+
+def test_c2_benchmark_queries_match_oracle(B):
+    # the C2 benchmark step as bench.py times it: its 32 seeded layout queries on the weighted
+    # heavy-hex 4x6 graph, over 8 contexts, every embedding with its score and the top-100 of
+    # each; rows, scores, count, checksum and top-100 all agree with the oracle
+    import bench
+    g, pats = bench.workload(0, bench.BATCH, "c2")
+    ctxs = [B.Context(0) for _ in range(8)]
+    try:
+        gids = [c.load(g) for c in ctxs]
+        got = {}
+        res, _ = B.dm_match_topk_queries([c.h for c in ctxs], gids, [(q.n, q.row_ptr, q.col_idx) for q in pats],
+                                         bench.K_TOP, cb=lambda i, r, s: got.setdefault(i, []).append((r, s)) and 0)
+        for i, (q, (rows_k, sc_k, cnt, cs, status)) in enumerate(zip(pats, res)):
+            assert status == B.DM_OK
+            ref = oracle.enumerate(g, q)
+            assert (cnt, cs) == (ref.count, ref.checksum)
+            rows = np.concatenate([r for r, _ in got[i]]) if i in got else np.zeros((0, q.n), np.int32)
+            scores = np.concatenate([s for _, s in got[i]]) if i in got else np.zeros(0, np.float32)
+            _rows_equal(rows, ref.rows)
+            np.testing.assert_allclose(scores, oracle.scores(g, q, ref.rows), rtol=RTOL, atol=0)
+            assert_topk(g, q, ref.rows, rows_k, sc_k, bench.K_TOP)
+    finally:
+        for c in ctxs:
+            c.close()
 
 
 def test_streaming_far_beyond_the_budget_is_consistent(ctx, B):
