@@ -83,6 +83,9 @@ def parse_args():
     ap.add_argument("--graph", default="heavyhex", choices=["heavyhex", "grid", "rr3"],
                     help="c3: data graph family (heavy-hex m x n, square grid 60x60, random 3-regular V=4096)")
     ap.add_argument("--only-path", type=int, default=0, help="c3: the batch is one path of this many vertices")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="c4: only the batched arm with the heuristic's choice among the learned planner's "
+                         "candidates (no model training); its timed steps form a CUDA profiler range")
     ap.add_argument("--shard-r0", action="store_true",
                     help="c3 under torchrun: every rank runs the same queries, each on its shard of the first "
                          "table R_0 (dm_match_shard), and the counts and checksums are summed across ranks "
@@ -704,6 +707,8 @@ def run_c4(args, emit: bool = True):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         launches = 0
         sync_ranks()
+        if args.only_batched:
+            torch.cuda.profiler.start()  # a profiler started with --profile-from-start off records from here
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -712,6 +717,8 @@ def run_c4(args, emit: bool = True):
             ev[i][1].record(stream)
             launches += B.dm_get_stats(ctx.h)["kernel_launches"]
         sync_ranks()
+        if args.only_batched:
+            torch.cuda.profiler.stop()
         ms = [a.elapsed_time(b) for a, b in ev]
         emb = int(counts.sum())
         done = list(B.dm_batch_latency(ctx.h, len(plans)))  # completion of each pattern, last step
@@ -720,6 +727,29 @@ def run_c4(args, emit: bool = True):
                 "latency": "completion time of each pattern from the start of the batch (all arrive together)",
                 "launch": B.dm_batch_config(ctx.h), "embeddings_per_step": emb}, launches, ms
 
+    if args.only_batched:  # the batched arm with the heuristic's choice alone
+        plans = []
+        for p in pats:
+            cands = B.dm_plan_candidates(ctx.h, gid, p.n, p.row_ptr, p.col_idx)
+            costs = [B.dm_plan_cost(c)[0] for c in cands]
+            best = min(range(len(cands)), key=lambda i: costs[i])
+            plans.append(cands[best])
+            for i, c in enumerate(cands):
+                if i != best:
+                    B.dm_plan_free(c)
+        bh, launches, ms = batched(plans)
+        if rank == 0 and emit:
+            print(json.dumps({"metric": METRIC, "value": bh["value"], "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": bh["ms_per_step"],
+                              "higher_is_better": True, "config": {"workload": wl_name(args, "c4"),
+                                                                   "arm": "batched_heuristic_choice"},
+                              "launch": bh["launch"], "gpu_launches": launches,
+                              "p50_ms_per_pattern": bh["p50_ms_per_pattern"],
+                              "p99_ms_per_pattern": bh["p99_ms_per_pattern"]}))
+        for p in plans:
+            B.dm_plan_free(p)
+        ctx.close()
+        return None
     paper_plans, paper_plan_ms = make(B.DM_ORDER_PAPER)
     plain_paper, _, _ = plain(paper_plans)
     plain_paper["plan_ms_total"] = paper_plan_ms
