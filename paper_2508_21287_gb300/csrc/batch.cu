@@ -54,8 +54,9 @@ __device__ __forceinline__ void load_args(JoinArgs *dst, const JoinArgs *src) {
   __syncthreads();
 }
 
+// 128-thread CTAs: up to 5 per SM (at most 102 registers a thread; a few spill), 256-thread CTAs: 2
 template <int BATCH_BLK>
-__global__ void __launch_bounds__(BATCH_BLK, 512 / BATCH_BLK) k_batch(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(BATCH_BLK, 640 / BATCH_BLK) k_batch(const __grid_constant__ BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) JoinArgs sa;
   __shared__ int s_warp[BATCH_BLK / 32];
