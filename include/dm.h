@@ -244,8 +244,9 @@ int dm_match_batch(dm_ctx *ctx, const dm_plan_t *const *plans, int32_t n_plans, 
  * the paper): tile rows per CTA step, root rows per work item, CTAs of the persistent launch,
  * how many plans (those whose predicted largest table exceeds heavy_rows) ran step by step
  * over the whole GPU after the persistent launch instead of inside it, the block shape
- * (threads per CTA, 128 or 256, and resident CTAs per SM) and the load factor of the two-key
- * hash indices the joins probed. Every output pointer may be NULL. DM_E_INVAL if the context
+ * (threads per CTA, 128 or 256, and resident CTAs per SM; 32 = one depth-first walk per warp,
+ * two warps a CTA, 32-row tiles) and the load factor of the two-key hash indices the joins
+ * probed. Every output pointer may be NULL. DM_E_INVAL if the context
  * has run no batch. */
 int dm_batch_config(dm_ctx *ctx, int32_t *tile_rows, int64_t *root_chunk, int32_t *grid,
                     int32_t *n_stepwise, double *heavy_rows, int32_t *threads_per_cta,
@@ -276,8 +277,10 @@ int dm_set_tuning(dm_ctx *ctx, int autotune, double hash_load_factor, double hea
 int dm_set_fusion(dm_ctx *ctx, int on);
 
 /* Block shape of dm_match_batch when autotuning is off (no counterpart in the paper):
- * threads_per_cta 128 or 256, ctas_per_sm resident CTAs per SM (0 = as many as fit).
- * DM_E_INVAL otherwise. Takes effect at the next dm_match_batch. */
+ * threads_per_cta 128 or 256 (every CTA walks its work items through the plan's steps in
+ * tiles of the tuned row count), or 32 (every warp walks its own work items in 32-row tiles,
+ * with no block barrier; two warps a CTA), and ctas_per_sm resident CTAs per SM (0 = as many
+ * as fit). DM_E_INVAL otherwise. Takes effect at the next dm_match_batch. */
 int dm_set_batch_shape(dm_ctx *ctx, int32_t threads_per_cta, int32_t ctas_per_sm);
 
 /* The k best layouts (Sec. 5.4): the min(k, |Emb|) embeddings with the smallest (score,

@@ -1336,8 +1336,10 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   b->key.assign(plans, plans + n);
   b->hash_lf = c->hash_lf;
   b->heavy_rows = heavy_rows;
-  b->TR = TR;
   b->root_chunk = root_chunk;
+  const bool walk = threads == 32;  // one depth-first walk per warp (k_batchw): 32-row tiles
+  if (walk) TR = 32;
+  b->TR = TR;
   b->threads = threads;
   b->ctas_per_sm = ctas_per_sm;
   b->n_plans = n;
@@ -1346,7 +1348,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   std::vector<dmk::BatchPlan> bplans(n);
   std::vector<std::pair<double, dmk::BatchItem>> items;
   std::vector<int64_t> cap(MAXSTEPS, 0), maxw(MAXSTEPS, 0);
-  int ws_max = 1;
+  int ws_max = 1, max_steps = 1;
   bool wide = false;  // some step maps more than 4 new vertices
   for (int32_t i = 0; i < n; i++) {
     if (plans[i]->p.pred_max_rows > heavy_rows) {  // runs step by step after the launch
@@ -1364,6 +1366,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
     const int S = (int)ex.st.size();
     bplans[i].n_steps = S;
     bplans[i].args_off = (int32_t)args.size();
+    max_steps = std::max(max_steps, S);
     double cost = 0;
     for (int j = 0; j < S; j++) {
       JoinArgs a = ex.st[j].base;
@@ -1373,10 +1376,18 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
       a.out_next = nullptr;
       a.nx.nkeys = -1;
       a.prune = INFINITY;
+      a.rs_in = 0;
+      a.rs_out = 0;
+      if (walk && a.mode == 0 && j + 1 < S && a.n_new >= 1 && a.n_new <= 4 && a.wo == a.w + a.n_new) {
+        // warp walks keep a level's rows padded to 16 bytes when its columns are in working order
+        bool identity = true;
+        for (int q = 0; q < a.wo; q++) identity &= a.src_col[q] == q;
+        if (identity) a.rs_out = (a.wo + 3) / 4 * 4;
+      }
       args.push_back(a);
       ws_max = std::max(ws_max, join_row_stride(a.w));
       wide |= j > 0 && a.n_new > 4;
-      maxw[j] = std::max<int64_t>(maxw[j], a.wo);
+      maxw[j] = std::max<int64_t>(maxw[j], a.rs_out ? a.rs_out : a.wo);
       if (j > 0) cap[j] = std::max<int64_t>(cap[j], (int64_t)TR * ex.st[j].max_group);
       cost += ex.p->steps[j].est_rows;
     }
@@ -1406,18 +1417,25 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
     P.lvl_cap[j] = cap[j];
     off += (cap[j] * std::max<int64_t>(1, maxw[j]) * 4 + 255) / 256 * 256;
   }
-  P.cta_bytes = off;
+  P.cta_bytes = off;  // per CTA, or per warp for warp walks
   P.TR = TR;
   P.ws_max = ws_max;
+  P.max_steps = max_steps;
   // wide steps test injectivity in per-row id bitmaps when the graph is small enough for them
   P.bm_words = 0;
-  if (wide && g->V <= 2048) {
+  if (!walk && wide && g->V <= 2048) {
     const int bw = (g->V + 63) / 64;
     if (dmk::batch_smem_bytes(TR, ws_max, bw, threads) <= 160 * 1024) P.bm_words = bw;
   }
   P.n_items = (int64_t)hitems.size();
-  b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms, threads, ctas_per_sm);
-  while (b->grid > c->num_sms && (uint64_t)b->grid * P.cta_bytes > c->budget / 2) b->grid /= 2;
+  const int64_t slices = walk ? dmk::BW_WALK_WARPS : 1;  // scratch slices a CTA holds
+  if (walk) {
+    if (dmk::walk_smem_bytes(ws_max, max_steps) > 200 * 1024) return DM_E_CAPACITY;
+    b->grid = dmk::walk_grid(ws_max, max_steps, c->num_sms, ctas_per_sm);
+  } else {
+    b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms, threads, ctas_per_sm);
+  }
+  while (b->grid > c->num_sms && (uint64_t)b->grid * slices * P.cta_bytes > c->budget / 2) b->grid /= 2;
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     if (cudaMalloc(dst, std::max<size_t>(bytes, 16)) != cudaSuccess) {
       cudaGetLastError();
@@ -1437,7 +1455,7 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
     return DM_E_NOMEM;
   }
   RET(up(&b->d_left0, items_per.data(), sizeof(uint64_t) * n));
-  if (cudaMalloc(&b->scratch, std::max<size_t>(16, (size_t)b->grid * P.cta_bytes)) != cudaSuccess) {
+  if (cudaMalloc(&b->scratch, std::max<size_t>(16, (size_t)b->grid * slices * P.cta_bytes)) != cudaSuccess) {
     cudaGetLastError();
     return DM_E_NOMEM;
   }
@@ -1473,7 +1491,8 @@ int batch_run(dm_ctx *c, DevGraph *g, BatchState *b) {
         cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long) * (2 + 2 * n), cs);
         cudaMemcpyAsync((unsigned long long *)b->d_work + 2 + 2 * n, b->d_left0, sizeof(unsigned long long) * n,
                         cudaMemcpyDeviceToDevice, cs);
-        dmk::launch_batch(b->prm, b->grid, b->threads, cs);
+        if (b->threads == 32) dmk::launch_batch_walk(b->prm, b->grid, cs);
+        else dmk::launch_batch(b->prm, b->grid, b->threads, cs);
         cudaMemcpyAsync(b->h_out, b->d_work, wbytes, cudaMemcpyDeviceToHost, cs);
         e = cudaStreamEndCapture(cs, &b->graph);
       }
@@ -2363,13 +2382,16 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
           best = ms;
           heavy = hv;
         }
-      const int shapes[4][2] = {{256, 1}, {128, 0}, {128, 2}, {256, 0}};
+      const int shapes[5][2] = {{256, 1}, {128, 0}, {128, 2}, {256, 0}, {32, 0}};  // 32: warp walks
+      int TR_shape = TR;
       for (auto &sh : shapes)
         if (trial(TR, chunk, heavy, sh[0], sh[1], &ms) == DM_OK && ms < best) {
           best = ms;
           threads = sh[0];
           ctas = sh[1];
+          TR_shape = sh[0] == 32 ? 32 : TR;  // warp walks always take 32-row tiles
         }
+      TR = TR_shape;
       const double lf0 = c->hash_lf;
       double lf_best = lf0;
       for (double lf : {0.25, 0.5, 0.75}) {
@@ -2416,7 +2438,8 @@ int dm_batch_latency(dm_ctx *c, double *out_ms, int32_t n) {
 }
 
 int dm_set_batch_shape(dm_ctx *c, int32_t threads_per_cta, int32_t ctas_per_sm) {
-  if (!c || (threads_per_cta != 128 && threads_per_cta != 256) || ctas_per_sm < 0) return DM_E_INVAL;
+  if (!c || (threads_per_cta != 32 && threads_per_cta != 128 && threads_per_cta != 256) || ctas_per_sm < 0)
+    return DM_E_INVAL;
   if (c->batch_threads == threads_per_cta && c->batch_ctas == ctas_per_sm) return DM_OK;
   c->batch_threads = threads_per_cta;
   c->batch_ctas = ctas_per_sm;

@@ -8,7 +8,8 @@
 // ever waits for another; load balance comes from small root chunks taken in order of the
 // plans' estimated cost. Join, filter, score and compaction are the same device code as the
 // per-step kernel (join_device.cuh). The kernel exists for two block shapes (128 and 256
-// threads); the autotuner picks the shape and how many CTAs run per SM.
+// threads); a third shape, one walk per warp, is k_batchw (join_warp.cu). The autotuner picks
+// the shape and how many CTAs run per SM.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,12 +18,6 @@
 
 namespace dmk {
 
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 template <int BATCH_BLK>
 __device__ __forceinline__ void batch_tile(const JoinArgs &a, const JoinSmem &S, int TR, const int32_t *src,

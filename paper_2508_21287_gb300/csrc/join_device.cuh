@@ -36,6 +36,13 @@ __device__ __forceinline__ unsigned long long dmix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
+// GPU global timer (ns).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Programmatic dependent launch: wait until the previous grid in the stream has completed and
 // its writes are visible (a no-op when the kernel was launched without the attribute), and
 // allow the next grid to be scheduled.

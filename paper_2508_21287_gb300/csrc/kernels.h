@@ -164,7 +164,7 @@ struct BatchParams {
   unsigned long long *next_item;  // work counter (zeroed before the launch)
   unsigned long long *out;        // count, checksum per plan (zeroed before the launch)
   unsigned long long *ovf;
-  unsigned char *scratch;         // grid * cta_bytes
+  unsigned char *scratch;         // grid * cta_bytes (warp walks: one cta_bytes slice per warp)
   int64_t cta_bytes;
   int64_t lvl_off[dmi::MAXSTEPS]; // byte offset of level j inside a CTA's scratch
   int64_t lvl_cap[dmi::MAXSTEPS]; // rows level j can hold
@@ -175,12 +175,21 @@ struct BatchParams {
   unsigned long long *plan_left;  // work items still open per plan (set before the launch)
   unsigned long long *plan_done;  // GPU global-timer time at which each plan's last item ended
   unsigned long long *start_ns;   // GPU global-timer time at the start of the launch
+  int max_steps;                  // warp walks: the most steps of a plan (per-warp level state)
 };
 // threads: 128 or 256 per CTA. batch_grid: SMs x resident CTAs per SM (at most max_per_sm when
 // it is > 0).
 size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words, int threads);
 int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms, int threads, int max_per_sm);
 cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream_t s);
+// The same batch with one depth-first walk per warp (k_batchw, 64-thread CTAs): tiles of 32 rows
+// (TR = 32), the levels of each warp in its own cta_bytes slice of scratch, rows of level j of
+// stride args[j].rs_out (padded, working-column order) or args[j].wo. walk_grid: SMs x resident
+// CTAs per SM (at most max_per_sm when it is > 0); BW_WALK_WARPS warps a CTA.
+constexpr int BW_WALK_WARPS = 2;
+size_t walk_smem_bytes(int ws_max, int max_steps);
+int walk_grid(int ws_max, int max_steps, int num_sms, int max_per_sm);
+cudaError_t launch_batch_walk(const BatchParams &p, int grid, cudaStream_t s);
 
 // Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.
 int64_t mlp_param_count();

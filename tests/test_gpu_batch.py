@@ -57,22 +57,25 @@ def test_batch_mixed_heavy_hex(B):
         cfg = B.dm_batch_config(ctx.h)
         assert cfg["tile_rows"] in (32, 64, 128) and cfg["root_chunk"] in (4, 16, 64)
         # the autotuner also picked a block shape and a two-key hash load factor
-        assert cfg["threads_per_cta"] in (128, 256) and cfg["ctas_per_sm"] >= 1
+        assert cfg["threads_per_cta"] in (32, 128, 256) and cfg["ctas_per_sm"] >= 1
         assert cfg["hash_load_factor"] in (0.25, 0.5, 0.75)
         # the same plans again: the cached device image and graph are replayed
         counts2, sums2, _ = _run(B, ctx, gid, pats)
         assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
         # every block shape and load factor gives the oracle's counts and checksums
-        for th, lf in ((128, 0.25), (256, 0.75)):
+        for th, lf in ((128, 0.25), (256, 0.75), (32, 0.5)):
             B.dm_set_tuning(ctx.h, autotune=False, hash_load_factor=lf)
             counts3, sums3, cfg3 = _run_shape(B, ctx, gid, pats, th)
             assert np.array_equal(counts, counts3) and np.array_equal(sums, sums3)
             assert cfg3["hash_load_factor"] == lf and cfg3["threads_per_cta"] == th
+            if th == 32:  # warp walks take 32-row tiles
+                assert cfg3["tile_rows"] == 32
 
 
 def test_batch_candidate_plans_with_wide_steps(B):
     # every candidate plan of long cycles and mixed patterns: half-length path slices map up
-    # to 19 new vertices a step, tested in per-row id bitmaps inside the batch kernel
+    # to 19 new vertices a step, tested in per-row id bitmaps inside the CTA batch kernel and
+    # read lazily from the motif rows by the warp walks
     g = I.heavy_hex(12, 6)
     pats = [I.cycle(n) for n in (24, 30, 36, 39, 40)] + [I.mixed_pattern(s, 16, 40) for s in range(20)]
     with B.Context(0) as ctx:
@@ -83,10 +86,16 @@ def test_batch_candidate_plans_with_wide_steps(B):
                 plans.append(pl)
                 owner.append(i)
         assert any(max(s["motif"] for s in B.dm_plan_describe(pl)) > 8 for pl in plans)
-        counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
         refs = [oracle.enumerate(g, p, rows=False, threads=8) for p in pats]
-        for i, c, s in zip(owner, counts.tolist(), sums.tolist()):
-            assert (c, s) == (refs[i].count, refs[i].checksum), pats[i].name
+        for shape in (None, 32, 256):  # autotuned, warp walks, 256-thread CTAs
+            if shape is not None:  # plans predicted above 2^20 rows run step by step, as tuned
+                B.dm_set_tuning(ctx.h, autotune=False, hash_load_factor=0.5, heavy_rows=1048576.0)
+                B.dm_set_batch_shape(ctx.h, shape, 0)
+            counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+            if shape is not None:
+                assert B.dm_batch_config(ctx.h)["threads_per_cta"] == shape
+            for i, c, s in zip(owner, counts.tolist(), sums.tolist()):
+                assert (c, s) == (refs[i].count, refs[i].checksum), (pats[i].name, shape)
         for pl in plans:
             B.dm_plan_free(pl)
 
@@ -124,6 +133,14 @@ def test_c4_full_batch_matches_oracle(B):
             counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
             for p, r, c, s in zip(pats, refs, counts.tolist(), sums.tolist()):
                 assert (c, s) == (r.count, r.checksum), p.name
+        # both kernel forms on their own: CTA walks and warp walks
+        B.dm_set_tuning(ctx.h, autotune=False, hash_load_factor=0.5)
+        for shape in (256, 32):
+            B.dm_set_batch_shape(ctx.h, shape, 0)
+            for plans in (paper, cheap):
+                counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+                for p, r, c, s in zip(pats, refs, counts.tolist(), sums.tolist()):
+                    assert (c, s) == (r.count, r.checksum), (p.name, shape)
         for pl in paper + cheap:
             B.dm_plan_free(pl)
 
