@@ -52,7 +52,7 @@ WORKLOAD_C2 = ("C2 layout queries: heavy-hex 4x6 (V=159, E=182), 32 queries/step
 # --clock-control none) over `bench.py --steps 1 --warmup 0 --no-extras --no-cpu --no-e2e`,
 # keyed by workload and by the digest of the join kernel's sources at capture time: after any
 # change to those sources the number no longer describes the kernel and the line reports null.
-JOIN_SOURCES = ("join_warp.cu", "join_device.cuh", "dm_internal.h")
+JOIN_SOURCES = ("join_warp.cu", "join_warp.cuh", "join_device.cuh", "dm_internal.h")
 JOIN_TRAFFIC_BYTES_PER_LAUNCH: dict[tuple[str, str], float] = {
     # C3 heavy-hex 53x59, the default workload: 283 join launches of one step
     ("c3:heavyhex:53,59:0:32", "dccb37974904a207"): 252928731.0,
