@@ -370,6 +370,19 @@ def test_scaling_counts(ctx, m, n):
         assert cnt == ref.count and cs == ref.checksum
 
 
+def test_scaling_rows_heavy_hex_27x28(ctx):
+    # every embedding row, not only count and checksum, at the scaling workload's middle size
+    # (V = 3999): the device-driven chain with its 16-byte-padded intermediate tables, then the
+    # canonical sort, against the oracle's rows element by element
+    g = I.heavy_hex(27, 28)
+    gid = ctx.load(g)
+    for p in (I.path(16), I.path(20), I.sub_patch(g, 30, 4)):
+        rows, _, cnt, cs = ctx.plan(gid, p).all()
+        ref = oracle.enumerate(g, p, threads=16)
+        assert cnt == ref.count > 0 and cs == ref.checksum
+        _rows_equal(rows, ref.rows)
+
+
 def test_largest_heavy_hex_p24(ctx):
     g = I.heavy_hex(53, 59)
     gid = ctx.load(g)
