@@ -100,10 +100,14 @@ def test_batch_candidate_plans_with_wide_steps(B):
             B.dm_plan_free(pl)
 
 
-def test_batch_sort_merge_plans(B):
+@pytest.mark.parametrize("shape", [None, 32])  # autotuned, warp walks
+def test_batch_sort_merge_plans(B, shape):
     g = I.heavy_hex(12, 6)
     pats = [I.mixed_pattern(s, 5, 30) for s in range(30)] + [I.cycle(24)]
     with B.Context(0) as ctx:
+        if shape is not None:
+            B.dm_set_tuning(ctx.h, False, 0.5)
+            B.dm_set_batch_shape(ctx.h, shape, 0)
         gid = ctx.load(g)
         counts, sums, single = _run(B, ctx, gid, pats, join_algo=B.DM_JOIN_SORTMERGE)
         _check(g, pats, counts, sums, single)
@@ -145,13 +149,16 @@ def test_c4_full_batch_matches_oracle(B):
             B.dm_plan_free(pl)
 
 
-def test_batch_paths_and_patches(B):
+@pytest.mark.parametrize("shape", [256, 32])  # CTA walks, warp walks
+def test_batch_paths_and_patches(B, shape):
     g = I.heavy_hex(8, 9)
-    pats = [I.path(k) for k in (2, 3, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]
+    pats = [I.path(k) for k in (2, 3, 4, 7, 12, 20, 28)] + [I.sub_patch(g, n, n) for n in (5, 15, 25, 40)]
     pats += [I.from_edges(1, [])]  # single vertex: one-step plan
+    pats += [I.star(3), I.cycle(12)]  # patterns that are motifs themselves: one-step plans
     with B.Context(0) as ctx:
         gid = ctx.load(g)
         B.dm_set_tuning(ctx.h, False, 0.5)
+        B.dm_set_batch_shape(ctx.h, shape, 0)
         counts, sums, single = _run(B, ctx, gid, pats)
         _check(g, pats, counts, sums, single)
         lat = B.dm_batch_latency(ctx.h, len(pats))
@@ -159,17 +166,20 @@ def test_batch_paths_and_patches(B):
         # the heaviest plans step by step, the rest in the persistent launch: same results
         B.dm_set_tuning(ctx.h, False, 0.5, heavy_rows=5000.0)
         counts2, sums2, _ = _run(B, ctx, gid, pats)
-        assert B.dm_batch_config(ctx.h)["stepwise_plans"] > 0
+        cfg = B.dm_batch_config(ctx.h)
+        assert cfg["stepwise_plans"] > 0 and cfg["threads_per_cta"] == shape
         assert np.array_equal(counts, counts2) and np.array_equal(sums, sums2)
 
 
-@pytest.mark.parametrize("lf", [0.25, 0.9])
-def test_batch_two_key_joins_on_grid(B, lf):
+@pytest.mark.parametrize("lf,shape", [(0.25, None), (0.9, None), (0.5, 32), (0.5, 128)])
+def test_batch_two_key_joins_on_grid(B, lf, shape):
     g = I.grid(10, 10)
     pats = [I.cycle(4), I.cycle(6), I.cycle(8), I.grid(2, 3), I.grid(3, 3), I.subdivided_grid(2, 2),
             I.random_tree(7, 1), I.path(6)]
     with B.Context(0) as ctx:
-        B.dm_set_tuning(ctx.h, True, lf)
+        B.dm_set_tuning(ctx.h, shape is None, lf)  # None: autotuned
+        if shape is not None:
+            B.dm_set_batch_shape(ctx.h, shape, 0)
         gid = ctx.load(g)
         counts, sums, single = _run(B, ctx, gid, pats, motifs=[104, 106, 202, 2])
         _check(g, pats, counts, sums, single)
