@@ -1429,9 +1429,10 @@ int batch_build(dm_ctx *c, DevGraph *g, const dm_plan_t *const *plans, int32_t n
   }
   P.n_items = (int64_t)hitems.size();
   const int64_t slices = walk ? dmk::BW_WALK_WARPS : 1;  // scratch slices a CTA holds
+  P.tile_words = 32 * std::min(ws_max, dmk::BW_WALK_TILE_STRIDE);  // >= 6 rows of the widest (132 words)
   if (walk) {
-    if (dmk::walk_smem_bytes(ws_max, max_steps) > 200 * 1024) return DM_E_CAPACITY;
-    b->grid = dmk::walk_grid(ws_max, max_steps, c->num_sms, ctas_per_sm);
+    if (dmk::walk_smem_bytes(P.tile_words, max_steps) > 200 * 1024) return DM_E_CAPACITY;
+    b->grid = dmk::walk_grid(P.tile_words, max_steps, c->num_sms, ctas_per_sm);
   } else {
     b->grid = dmk::batch_grid(TR, ws_max, P.bm_words, c->num_sms, threads, ctas_per_sm);
   }

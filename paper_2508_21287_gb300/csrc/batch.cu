@@ -181,8 +181,40 @@ cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream
 // are read with plain (coherent) loads, never through the read-only cache path.
 
 // 64-entry staging lists: the smaller footprint keeps more walks resident than a longer list
-// would save in flushes (the walks are latency-bound)
+// would save in flushes (the walks are latency-bound). Each walk's shared tile holds
+// tile_words words (BatchParams): a step whose rows take s words (join_row_stride) joins
+// min(32, tile_words / s) rows a tile, so the few wide steps of a batch take shorter tiles
+// instead of every walk reserving 32 rows of the widest.
 constexpr int BW_WARPS = BW_WALK_WARPS, BW_BLK = 32 * BW_WARPS, BW_STAGE = 64;
+
+__host__ __device__ __forceinline__ int walk_tile_rows(int tile_words, int w) {
+  const int r = tile_words / join_row_stride(w);
+  return r < WT ? r : WT;
+}
+
+// The warp's tile, checksum terms, scores and staging list (the layout of warp_smem with a
+// fixed tile of tile_words words).
+__host__ __device__ __forceinline__ size_t walk_head_bytes(int tile_words) {
+  size_t b = (size_t)tile_words * 4 + (size_t)WT * 8 + (size_t)WT * 4;
+  b = (b + 15) / 16 * 16 + (size_t)BW_STAGE * 12 + (size_t)BW_STAGE * STAGE_NV * 4;
+  return (b + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ WarpSmem walk_warp(unsigned char *base, int tile_words) {
+  WarpSmem m;
+  size_t off = (size_t)tile_words * 4;  // a multiple of 16
+  m.rows = (int32_t *)base;
+  m.part = (unsigned long long *)(base + off);
+  off += (size_t)WT * 8;
+  m.rs = (float *)(base + off);
+  off += (size_t)WT * 4;
+  off = (off + 15) / 16 * 16;
+  m.st_r = (int32_t *)(base + off);
+  m.st_m = m.st_r + BW_STAGE;
+  m.st_s = (float *)(m.st_m + BW_STAGE);
+  m.st_nv = (int32_t *)(m.st_s + BW_STAGE);
+  return m;
+}
 
 struct WalkSmem {
   int32_t *tq;           // MAXW: counted step, 1 + output position of each working column
@@ -192,15 +224,15 @@ struct WalkSmem {
   int32_t *n_lvl, *cur;  // per level: rows held, rows already joined into the next level
 };
 
-__host__ __device__ __forceinline__ size_t walk_warp_bytes(int ws_max, int max_steps) {
-  size_t b = warp_smem_bytes<BW_STAGE>(ws_max) + (size_t)MAXW * 4 + MAXM;
+__host__ __device__ __forceinline__ size_t walk_warp_bytes(int tile_words, int max_steps) {
+  size_t b = walk_head_bytes(tile_words) + (size_t)MAXW * 4 + MAXM;
   b = (b + 15) / 16 * 16 + (size_t)max_steps * 8;
   return (b + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ WalkSmem walk_smem(unsigned char *base, int ws_max, int max_steps) {
+__device__ __forceinline__ WalkSmem walk_smem(unsigned char *base, int tile_words, int max_steps) {
   WalkSmem k;
-  size_t off = warp_smem_bytes<BW_STAGE>(ws_max);  // a multiple of 16
+  size_t off = walk_head_bytes(tile_words);  // a multiple of 16
   k.tq = (int32_t *)(base + off);
   k.code = (int16_t *)(base + off);
   off += (size_t)MAXW * 4;
@@ -284,7 +316,7 @@ __device__ __forceinline__ bool wcheck_lazy(const JoinArgs &a, const WarpSmem &W
 }
 
 template <int MAXNEW, int MODE>
-__device__ __forceinline__ void walk_tile(const JoinArgs &a, unsigned char *wbase, const WalkSmem &K,
+__device__ __forceinline__ void walk_tile(const JoinArgs &a, const WarpSmem &W, const WalkSmem &K,
                                           const int32_t *src, int rs_in, int nr, int64_t m0, int32_t *out, int rs_out,
                                           int64_t cap, int64_t &n_out, unsigned long long *ovf,
                                           unsigned long long &acc_rows, unsigned long long &acc_sum) {
@@ -293,7 +325,6 @@ __device__ __forceinline__ void walk_tile(const JoinArgs &a, unsigned char *wbas
   const bool seed = src == nullptr;
   const int w = a.w, wo = a.wo;
   const int wsv = join_row_stride(w);
-  const WarpSmem W = warp_smem<BW_STAGE>(wbase, wsv);
   for (int q = lane; q < wo; q += 32) {  // where this step's columns go
     const int col = a.src_col[q];
     if (MODE == 1) {
@@ -303,7 +334,8 @@ __device__ __forceinline__ void walk_tile(const JoinArgs &a, unsigned char *wbas
       K.code[q] = (int16_t)(col < w ? col : (0x100 | (col - w)));
     }
   }
-  for (int c = w; c < wsv; c++) W.rows[lane * wsv + c] = -1;  // padding words of the 32 tile rows
+  if (lane < nr)  // padding words of the tile rows (row 0 in the first step: read by the padded flush)
+    for (int c = w; c < wsv; c++) W.rows[lane * wsv + c] = -1;
   __syncwarp();
   int C;
   int g_start = 0, g_off = 0;
@@ -389,16 +421,16 @@ __device__ __forceinline__ void walk_tile(const JoinArgs &a, unsigned char *wbas
 }
 
 template <int MODE>
-__device__ __forceinline__ void walk_step_mode(const JoinArgs &a, unsigned char *wbase, const WalkSmem &K,
+__device__ __forceinline__ void walk_step_mode(const JoinArgs &a, const WarpSmem &W, const WalkSmem &K,
                                                const int32_t *src, int rs_in, int nr, int64_t m0, int32_t *out,
                                                int rs_out, int64_t cap, int64_t &n_out, unsigned long long *ovf,
                                                unsigned long long &ar, unsigned long long &as) {
   switch (a.n_new) {
-    case 1: walk_tile<1, MODE>(a, wbase, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
-    case 2: walk_tile<2, MODE>(a, wbase, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
-    case 3: walk_tile<3, MODE>(a, wbase, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
-    case 4: walk_tile<4, MODE>(a, wbase, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
-    default: walk_tile<MAXM, MODE>(a, wbase, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as);
+    case 1: walk_tile<1, MODE>(a, W, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
+    case 2: walk_tile<2, MODE>(a, W, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
+    case 3: walk_tile<3, MODE>(a, W, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
+    case 4: walk_tile<4, MODE>(a, W, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as); break;
+    default: walk_tile<MAXM, MODE>(a, W, K, src, rs_in, nr, m0, out, rs_out, cap, n_out, ovf, ar, as);
   }
 }
 
@@ -408,8 +440,9 @@ __host__ __device__ __forceinline__ int walk_level_stride(const JoinArgs &a) { r
 __global__ void __launch_bounds__(BW_BLK, 14) k_batchw(const __grid_constant__ BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char *wbase = smem + (size_t)wid * walk_warp_bytes(P.ws_max, P.max_steps);
-  const WalkSmem K = walk_smem(wbase, P.ws_max, P.max_steps);
+  unsigned char *wbase = smem + (size_t)wid * walk_warp_bytes(P.tile_words, P.max_steps);
+  const WarpSmem W = walk_warp(wbase, P.tile_words);
+  const WalkSmem K = walk_smem(wbase, P.tile_words, P.max_steps);
   if (blockIdx.x == 0 && threadIdx.x == 0) *P.start_ns = globaltimer_ns();
   unsigned char *mine = P.scratch + ((int64_t)blockIdx.x * BW_WARPS + wid) * P.cta_bytes;
   while (true) {
@@ -429,9 +462,9 @@ __global__ void __launch_bounds__(BW_BLK, 14) k_batchw(const __grid_constant__ B
       for (int64_t lo = item.lo; lo < item.hi; lo += 32) {
         const int nr = (int)imin64(32, item.hi - lo);
         if (S == 1)
-          walk_step_mode<1>(a0, wbase, K, nullptr, 0, nr, lo, nullptr, 0, 0, n_out, P.ovf, ar, as);
+          walk_step_mode<1>(a0, W, K, nullptr, 0, nr, lo, nullptr, 0, 0, n_out, P.ovf, ar, as);
         else
-          walk_step_mode<0>(a0, wbase, K, nullptr, 0, nr, lo, out, a0.rs_out, P.lvl_cap[0], n_out, P.ovf, ar, as);
+          walk_step_mode<0>(a0, W, K, nullptr, 0, nr, lo, out, a0.rs_out, P.lvl_cap[0], n_out, P.ovf, ar, as);
       }
       if (lane == 0) {
         K.n_lvl[0] = (int32_t)imin64(n_out, P.lvl_cap[0]);
@@ -447,15 +480,15 @@ __global__ void __launch_bounds__(BW_BLK, 14) k_batchw(const __grid_constant__ B
         continue;
       }
       const int j = top + 1;
-      const int nr = min(32, have - cur);
+      const int nr = min(walk_tile_rows(P.tile_words, args[j].w), have - cur);
       const int rs_in = walk_level_stride(args[top]);
       const int32_t *src = (const int32_t *)(mine + P.lvl_off[top]) + (int64_t)cur * rs_in;
       const JoinArgs &a = args[j];
       int64_t n_out = 0;
       if (j == S - 1)
-        walk_step_mode<1>(a, wbase, K, src, rs_in, nr, 0, nullptr, 0, 0, n_out, P.ovf, ar, as);
+        walk_step_mode<1>(a, W, K, src, rs_in, nr, 0, nullptr, 0, 0, n_out, P.ovf, ar, as);
       else
-        walk_step_mode<0>(a, wbase, K, src, rs_in, nr, 0, (int32_t *)(mine + P.lvl_off[j]), a.rs_out, P.lvl_cap[j],
+        walk_step_mode<0>(a, W, K, src, rs_in, nr, 0, (int32_t *)(mine + P.lvl_off[j]), a.rs_out, P.lvl_cap[j],
                           n_out, P.ovf, ar, as);
       if (lane == 0) {
         K.cur[top] = cur + nr;
@@ -484,10 +517,12 @@ __global__ void __launch_bounds__(BW_BLK, 14) k_batchw(const __grid_constant__ B
   }
 }
 
-size_t walk_smem_bytes(int ws_max, int max_steps) { return (size_t)BW_WARPS * walk_warp_bytes(ws_max, max_steps); }
+size_t walk_smem_bytes(int tile_words, int max_steps) {
+  return (size_t)BW_WARPS * walk_warp_bytes(tile_words, max_steps);
+}
 
-int walk_grid(int ws_max, int max_steps, int num_sms, int max_per_sm) {
-  const size_t smem = walk_smem_bytes(ws_max, max_steps);
+int walk_grid(int tile_words, int max_steps, int num_sms, int max_per_sm) {
+  const size_t smem = walk_smem_bytes(tile_words, max_steps);
   cudaFuncSetAttribute(k_batchw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batchw, BW_BLK, smem);
@@ -499,7 +534,7 @@ int walk_grid(int ws_max, int max_steps, int num_sms, int max_per_sm) {
 cudaError_t launch_batch_walk(const BatchParams &p, int grid, cudaStream_t s) {
   cudaFuncSetAttribute(k_batchw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   g_launches++;
-  k_batchw<<<grid, BW_BLK, walk_smem_bytes(p.ws_max, p.max_steps), s>>>(p);
+  k_batchw<<<grid, BW_BLK, walk_smem_bytes(p.tile_words, p.max_steps), s>>>(p);
   return cudaGetLastError();
 }
 

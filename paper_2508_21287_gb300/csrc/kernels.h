@@ -176,19 +176,22 @@ struct BatchParams {
   unsigned long long *plan_done;  // GPU global-timer time at which each plan's last item ended
   unsigned long long *start_ns;   // GPU global-timer time at the start of the launch
   int max_steps;                  // warp walks: the most steps of a plan (per-warp level state)
+  int tile_words;                 // warp walks: words of each walk's shared tile (a multiple of 4)
 };
 // threads: 128 or 256 per CTA. batch_grid: SMs x resident CTAs per SM (at most max_per_sm when
 // it is > 0).
 size_t batch_smem_bytes(int tile_rows, int ws_max, int bm_words, int threads);
 int batch_grid(int tile_rows, int ws_max, int bm_words, int num_sms, int threads, int max_per_sm);
 cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream_t s);
-// The same batch with one depth-first walk per warp (k_batchw, 64-thread CTAs): tiles of 32 rows
-// (TR = 32), the levels of each warp in its own cta_bytes slice of scratch, rows of level j of
-// stride args[j].rs_out (padded, working-column order) or args[j].wo. walk_grid: SMs x resident
-// CTAs per SM (at most max_per_sm when it is > 0); BW_WALK_WARPS warps a CTA.
-constexpr int BW_WALK_WARPS = 2;
-size_t walk_smem_bytes(int ws_max, int max_steps);
-int walk_grid(int ws_max, int max_steps, int num_sms, int max_per_sm);
+// The same batch with one depth-first walk per warp (k_batchw, 64-thread CTAs): tiles of up to
+// 32 rows (TR = 32; a step of row stride s takes min(32, tile_words / s)), the levels of each warp
+// in its own cta_bytes slice of scratch, rows of level j of stride args[j].rs_out (padded,
+// working-column order) or args[j].wo. walk_grid: SMs x resident CTAs per SM (at most max_per_sm
+// when it is > 0); BW_WALK_WARPS warps a CTA. BW_WALK_TILE_STRIDE: the row stride (words) that a
+// walk's tile holds 32 rows of.
+constexpr int BW_WALK_WARPS = 2, BW_WALK_TILE_STRIDE = 28;
+size_t walk_smem_bytes(int tile_words, int max_steps);
+int walk_grid(int tile_words, int max_steps, int num_sms, int max_per_sm);
 cudaError_t launch_batch_walk(const BatchParams &p, int grid, cudaStream_t s);
 
 // Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.
