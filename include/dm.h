@@ -41,7 +41,7 @@ extern "C" {
 #define DM_E_DISCONNECTED (-2) /* pattern or data graph not connected (Sec. 3.1 assumes connected graphs) */
 #define DM_E_NOMEM (-3)        /* device or host allocation failed, or the memory budget is too small */
 #define DM_E_CAPACITY (-4)     /* projected work or rows exceed the plan's cap (dm_plan_opts.max_rows) */
-#define DM_E_TIMEOUT (-5)      /* reserved: no kernel of this library waits on another, so no call returns it */
+#define DM_E_TIMEOUT (-5)      /* a bounded wait (about a second) of the model's tensor-core matmul ran out */
 #define DM_E_CUDA (-6)         /* a CUDA runtime call failed */
 #define DM_E_CANCELLED (-7)    /* the chunk callback returned non-zero */
 #define DM_E_NOTFOUND (-8)     /* unknown graph handle or motif id */

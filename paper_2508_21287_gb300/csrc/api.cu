@@ -1591,12 +1591,23 @@ int model_run(dm_ctx *c, const float *x_host, const float *t_host, int32_t n, fl
   CK(dmk::mlp_forward_backward(c->m_params, X, T, rows, n, Y, grads_dev, L, work, c->stream));
   if (y_host) CK(cudaMemcpyAsync(y_host, Y, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
   if (loss_host) CK(cudaMemcpyAsync(loss_host, L, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  // the tensor-core timeout flag, into a pinned counter slot that no other call of this
+  // context uses while the model runs
+  unsigned long long *flag_host = c->h_ctr + CTR_N - 1;
+  *flag_host = 0;
+  CK(cudaMemcpyAsync(flag_host, dmk::mlp_error_flag(work, rows), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                     c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  const unsigned long long timed_out = *flag_host;
   dfree(c, X);
   dfree(c, T);
   dfree(c, Y);
   dfree(c, L);
   dfree(c, work);
+  if (timed_out) {
+    c->last_error = "a tensor-core wait of the cardinality model timed out";
+    return DM_E_TIMEOUT;
+  }
   return DM_OK;
 }
 

@@ -197,6 +197,9 @@ cudaError_t launch_batch_walk(const BatchParams &p, int grid, cudaStream_t s);
 // Cardinality model (mlp.cu): flat FP32 parameters, BF16 tensor-core forward / backward.
 int64_t mlp_param_count();
 int64_t mlp_work_bytes(int rows);
+// Word of the work buffer that the forward/backward pass sets when a tensor-core wait ran out
+// (the pass's outputs are then invalid); zeroed at the start of every pass.
+unsigned *mlp_error_flag(void *work, int rows);
 cudaError_t mlp_forward_backward(const float *params, const float *X, const float *target, int rows, int n_valid,
                                  float *y, float *grads, float *loss, void *work, cudaStream_t s);
 cudaError_t mlp_adam(float *params, const float *grads, float *m, float *v, int64_t n, float lr, int step,
