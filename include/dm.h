@@ -321,8 +321,9 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
 
 /* ------------------------------------------------------------------ learned planner --- */
 /* No counterpart in the paper (which notes that motif choice and ordering matter, Sec. 5.2):
- * a 3-layer MLP (32 -> 128 -> 128 -> 1, ReLU; BF16 tensor-core matmuls with FP32
- * accumulation) predicts, for a candidate join step, the log growth of the intermediate
+ * a 3-layer MLP (32 -> 128 -> 128 -> 1, ReLU; BF16 matmuls on the fifth-generation tensor
+ * cores, tcgen05, with FP32 accumulation in tensor memory) predicts, for a candidate join
+ * step, the log growth of the intermediate
  * table, log(1 + rows after) - log(1 + rows before). DM_ORDER_LEARNED plans are the cheapest,
  * under the model's predicted cardinalities, of several candidate decompositions (the
  * paper's rule and the greedy heuristic order, with the given motif set, with motifs
@@ -331,7 +332,10 @@ int dm_match_topk(dm_ctx *ctx, const dm_plan_t *plan, int mode, dm_chunk_cb cb, 
  * The output set never depends on the order. Feature vectors are DM_MODEL_FEATURES floats
  * (dm_plan_estimates / dm_step_log give them); parameters are FP32, flat, in the order
  * W1[128][32] b1[128] W2[128][128] b2[128] w3[128] b3, followed by the 32 input means and
- * 32 input standard deviations used to standardise the features. */
+ * 32 input standard deviations used to standardise the features. The calls that run the
+ * model (dm_model_train, dm_model_predict, dm_model_grad, and planning in the learned order)
+ * return DM_E_TIMEOUT if a matmul's bounded wait for its tensor-core work ran out (the results
+ * of that call are then discarded). */
 #define DM_MODEL_FEATURES 32
 
 /* Fresh He-uniform weights from a SplitMix64 stream seeded by `seed`; forgets training. */
