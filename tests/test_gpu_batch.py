@@ -185,6 +185,29 @@ def test_batch_two_key_joins_on_grid(B, lf, shape):
         _check(g, pats, counts, sums, single)
 
 
+@pytest.mark.parametrize("shape", [256, 32])  # CTA walks, warp walks
+def test_batch_induced_plans(B, shape):
+    # the literal reading of Sec. 3.1 (induced = 1): every step also rejects rows whose new
+    # vertices are adjacent to columns their pattern vertices are not adjacent to
+    cases = [(I.grid(7, 7), [I.path(k) for k in (3, 4, 6, 9)] + [I.cycle(4), I.cycle(8), I.star(3),
+                                                              I.grid(2, 3), I.random_tree(8, 2)]),
+             (I.heavy_hex(6, 5), [I.path(k) for k in (5, 12, 18)] + [I.sub_patch(I.heavy_hex(6, 5), 14, 1)])]
+    with B.Context(0) as ctx:
+        B.dm_set_tuning(ctx.h, False, 0.5)
+        B.dm_set_batch_shape(ctx.h, shape, 0)
+        for g, pats in cases:
+            gid = ctx.load(g)
+            plans = [B.dm_plan(ctx.h, gid, p.n, p.row_ptr, p.col_idx, induced=True) for p in pats]
+            counts, sums = B.dm_match_batch(ctx.h, plans, B.DM_COUNT)
+            assert B.dm_batch_config(ctx.h)["threads_per_cta"] == shape
+            for p, pl, c, s_ in zip(pats, plans, counts.tolist(), sums.tolist()):
+                ref = oracle.enumerate(g, p, induced=True, rows=False, threads=8)
+                assert (c, s_) == (ref.count, ref.checksum), (p.name, shape)
+                assert B.dm_match(ctx.h, pl, B.DM_COUNT) == (c, s_)
+            for pl in plans:
+                B.dm_plan_free(pl)
+
+
 def test_batch_rejects_mixed_graphs_and_modes(B):
     with B.Context(0) as ctx:
         a = ctx.load(I.grid(3, 3))
