@@ -477,6 +477,8 @@ def dm_batch_config(ctx) -> dict:
 
 
 def dm_set_batch_shape(ctx, threads_per_cta: int = 256, ctas_per_sm: int = 0) -> None:
+    """Block shape of dm_match_batch without autotuning: 128 or 256 threads a CTA (CTA walks),
+    or 32 (one walk per warp, two warps a CTA); ctas_per_sm 0 = as many as fit."""
     _check(_lib.dm_set_batch_shape(ctx, int(threads_per_cta), int(ctas_per_sm)), "dm_set_batch_shape", ctx)
 
 
