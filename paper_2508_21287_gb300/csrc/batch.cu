@@ -174,8 +174,8 @@ cudaError_t launch_batch(const BatchParams &p, int grid, int threads, cudaStream
 // on one data graph; the "warp walk" block shape of dm_match_batch). Every warp takes work
 // items (plan, rows of the motif table of its first slice) from the global counter and runs
 // each one through the plan's steps on its own: level j of the warp's scratch holds step j's
-// output for the current 32-row tile of level j - 1 (at most 32 x the step's largest key group
-// rows), and the last step is counted. A step over one tile is k_joinw's warp tile -- the same
+// output for the current tile (up to 32 rows) of level j - 1, at most 32 x the step's largest
+// key group rows, and the last step is counted. A step over one tile is k_joinw's warp tile -- the same
 // lookup, candidate walk, checks, staging and 16-byte flush -- so no warp waits for another and
 // no block barrier is taken. Level rows are written and read back within the launch, so they
 // are read with plain (coherent) loads, never through the read-only cache path.
