@@ -260,7 +260,8 @@ int dm_batch_latency(dm_ctx *ctx, double *out_ms, int32_t n);
 
 /* Tuning knobs: autotune (1 = on the first dm_match_batch of a new set of plans, time the
  * candidate configurations and keep the fastest: tile rows x root chunk, the split between
- * the persistent launch and step-by-step execution, the block shape, then the two-key hash
+ * the persistent launch and step-by-step execution, the block shape (and the root chunk again
+ * for a changed shape), then the two-key hash
  * load factor among 0.25, 0.5 and 0.75, a coordinate search; the chosen load factor stays
  * the context's for later calls), hash_load_factor (fill of two-key hash indices,
  * 0 < f <= 0.95; changing it drops those indices, which are rebuilt when a plan next runs),

@@ -2380,7 +2380,8 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
         return r;
       };
       // coordinate search: tile rows x root chunk, then the split between the persistent
-      // launch and step-by-step execution, then the block shape, then the hash load factor
+      // launch and step-by-step execution, then the block shape (and the root chunk again when
+      // the shape changed), then the hash load factor
       double best = 1e300, ms = 0;
       for (int tr : {32, 64, 128})
         for (int64_t ch : {4, 16, 64})
@@ -2396,6 +2397,7 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
         }
       const int shapes[5][2] = {{256, 1}, {128, 0}, {128, 2}, {256, 0}, {32, 0}};  // 32: warp walks
       int TR_shape = TR;
+      const int threads0 = threads, ctas0 = ctas;
       for (auto &sh : shapes)
         if (trial(TR, chunk, heavy, sh[0], sh[1], &ms) == DM_OK && ms < best) {
           best = ms;
@@ -2404,6 +2406,12 @@ int dm_match_batch(dm_ctx *c, const dm_plan_t *const *plans, int32_t n_plans, in
           TR_shape = sh[0] == 32 ? 32 : TR;  // warp walks always take 32-row tiles
         }
       TR = TR_shape;
+      if (threads != threads0 || ctas != ctas0)  // the root chunk again, for the shape chosen
+        for (int64_t ch : {4, 16, 64})
+          if (ch != chunk && trial(TR, ch, heavy, threads, ctas, &ms) == DM_OK && ms < best) {
+            best = ms;
+            chunk = ch;
+          }
       const double lf0 = c->hash_lf;
       double lf_best = lf0;
       for (double lf : {0.25, 0.5, 0.75}) {
